@@ -1,0 +1,264 @@
+/*
+ * geneo.h — C ABI of the GenEO two-level overlapping Schwarz library (sm_103a).
+ *
+ * The library builds and applies the two-level additive Schwarz
+ * preconditioner with the GenEO coarse space of Seelinger, Reinarz and
+ * Scheichl, "A High-Performance Implementation of a Robust Preconditioner for
+ * Heterogeneous Problems" (arXiv:1906.10944):
+ *
+ *   M^{-1}_{AS,2} = R_H^T A_H^{-1} R_H + sum_j R_j^T A_j^{-1} R_j   (Section 3,
+ *   Definition 2), with R_H^T = Z, the coarse basis of Definition 4 built from
+ *   the local eigenproblem Atilde_j p = lambda X_j A_j^o X_j p (eq. 5 and
+ *   Section 4.3), and solves A x = b with preconditioned CG (Section 5).
+ *
+ * Every numeric step runs in CUDA kernels of this library on one GPU.  The
+ * signatures use plain pointers and sizes only.
+ *
+ * Conventions shared by all entry points:
+ *  - Errors are returned as geneo_status_t; no call aborts, throws or traps.
+ *  - Streams: every call is ordered on the cudaStream_t it is given (0 = the
+ *    legacy default stream).  geneo_setup, geneo_pcg_solve, geneo_query and
+ *    geneo_get_subdomain synchronise that stream before returning.
+ *    geneo_apply only enqueues work; its device-side status is reported by
+ *    the next synchronising call on the same handle.
+ *  - Ownership: the caller owns every input array and may free it once the
+ *    call that received it returns.  geneo_setup copies what it keeps into
+ *    device memory owned by the handle until geneo_destroy.
+ *  - Indices are 0-based.
+ */
+#ifndef GENEO_H
+#define GENEO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GENEO_OK = 0,
+  GENEO_ERR_ARG = 1,          /* invalid argument or inconsistent sizes */
+  GENEO_ERR_OOM = 2,          /* device allocation failed */
+  GENEO_ERR_NOT_SPD = 3,      /* non-positive pivot in a Cholesky factorisation */
+  GENEO_ERR_EIG_NOCONV = 4,   /* local eigensolver reached eig_maxit */
+  GENEO_ERR_PCG_NOCONV = 5,   /* PCG reached maxit before the tolerance */
+  GENEO_ERR_BREAKDOWN = 6,    /* PCG breakdown: p^T A p <= 0 or r^T z <= 0 */
+  GENEO_ERR_CUDA = 7,         /* a CUDA runtime call failed */
+  GENEO_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+  GENEO_ERR_NONFINITE = 9     /* NaN or Inf met in the data */
+} geneo_status_t;
+
+typedef enum { GENEO_MEM_HOST = 0, GENEO_MEM_DEVICE = 1 } geneo_mem_t;
+
+typedef enum {
+  GENEO_EIG_PAPER = 0,   /* B_j = X_j A_j^o X_j, A_j^o over overlap elements (Section 4.3) */
+  GENEO_EIG_FULL = 1     /* B_j = X_j Atilde_j X_j (all elements of Omega_j) */
+} geneo_eig_form_t;
+
+typedef enum {
+  GENEO_PREC_FP64 = 0,   /* all factors and local solves in FP64 */
+  GENEO_PREC_FP32 = 1    /* subdomain factors in FP32; Rayleigh-Ritz, residuals,
+                            coarse problem and PCG in FP64 */
+} geneo_precision_t;
+
+/*
+ * Problem description (Section 2: a conforming FE discretisation; Section 3:
+ * overlapping subdomains as unions of mesh elements).
+ *
+ * All arrays live where `mem` says (host or device memory of the current
+ * device) and are read-only for the library.
+ *
+ *  n            global number of dofs.
+ *  ndof_node    dofs per mesh node (1 Darcy, 3 elasticity); informational.
+ *  row_ptr[n+1], col[nnz], val[nnz]
+ *               CSR of the global matrix A (FP64), symmetric positive
+ *               definite, column indices sorted within each row.  Rows and
+ *               columns of global Dirichlet dofs are eliminated: their row
+ *               and column are zero except a diagonal 1.  The pattern must
+ *               contain every coupling (k, l) of two dofs of one element
+ *               (explicit zeros allowed).
+ *  dirichlet[n] 1 for a global Dirichlet dof, else 0.
+ *  n_elem, elem_ndof
+ *               number of elements and dofs per element (4 for 2D Q1, 8 for
+ *               3D Q1, 24 for 3D Q1 elasticity).
+ *  elem_dofs[n_elem*elem_ndof]
+ *               global dof of local dof a of element e at [e*elem_ndof + a].
+ *  elem_mats[n_elem*elem_ndof*elem_ndof]
+ *               unconstrained element stiffness matrices, row-major per
+ *               element: K_e[a][b] at [(e*elem_ndof + a)*elem_ndof + b].
+ *               Their sum over all elements equals A off the Dirichlet rows.
+ *  n_sub        number of overlapping subdomains N.
+ *  sub_elem_ptr[N+1], sub_elem[...]
+ *               elements of Omega_j, sorted ascending, at
+ *               sub_elem[sub_elem_ptr[j] .. sub_elem_ptr[j+1]).
+ *  sub_dof_ptr[N+1], sub_dof[...]
+ *               dofs of the closure of Omega_j without global Dirichlet
+ *               dofs, sorted ascending (geneo_grow_partition produces both
+ *               lists from a non-overlapping partition).
+ *  Every subdomain must be non-empty.  Every non-Dirichlet dof must lie in
+ *  the interior of at least one subdomain (overlap >= 1 element layer).
+ */
+typedef struct {
+  int32_t mem;
+  int32_t ndof_node;
+  int64_t n;
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const uint8_t* dirichlet;
+  int64_t n_elem;
+  int32_t elem_ndof;
+  int32_t n_sub;
+  const int32_t* elem_dofs;
+  const double* elem_mats;
+  const int64_t* sub_elem_ptr;
+  const int32_t* sub_elem;
+  const int64_t* sub_dof_ptr;
+  const int32_t* sub_dof;
+} geneo_problem_t;
+
+/*
+ * Options (Theorem 1 and the remark after it for the threshold; Section 4.4
+ * for the shift).
+ *  tau        eigenvectors with lambda < tau are taken (default 0.3).
+ *  nev_max    at most this many per subdomain (default 10); 0 gives the
+ *             one-level method M^{-1}_{AS,1}.
+ *  fixed_nev  1: take exactly nev_max per subdomain regardless of tau.
+ *  sigma      shift of the spectral transformation, nu = 1/(lambda-sigma)
+ *             (default -0.01; must be negative: Atilde_j is singular on
+ *             floating subdomains).
+ *  eig_form   geneo_eig_form_t (default GENEO_EIG_PAPER).
+ *  eig_tol    relative residual ||B x - nu K x|| / (||B x|| + nu ||K x||)
+ *             at which an eigenpair counts as converged (default 1e-6).
+ *  eig_maxit  iteration cap of the block eigensolver (default 100).
+ *  guard      extra block vectors beyond nev_max (default min(5, nev_max)).
+ *  precision  geneo_precision_t (default GENEO_PREC_FP64).
+ *  seed       seed of the counter-based start vectors (SplitMix64).
+ */
+typedef struct {
+  double tau;
+  double sigma;
+  double eig_tol;
+  int32_t nev_max;
+  int32_t fixed_nev;
+  int32_t eig_form;
+  int32_t eig_maxit;
+  int32_t guard;
+  int32_t precision;
+  uint64_t seed;
+} geneo_options_t;
+
+typedef struct geneo_handle_s* geneo_handle_t;
+
+/* Per-solve report (Section 5.3 and 5.4 report iterations and a condition
+ * estimate).  resid_hist may be NULL; otherwise it receives up to
+ * resid_hist_cap relative residuals ||r_k||/||b|| (k = 0, 1, ...). */
+typedef struct {
+  int32_t iterations;
+  int32_t converged;
+  double rel_residual;       /* recursive ||r||/||b|| at exit */
+  double kappa_estimate;     /* Lanczos estimate of kappa(M^{-1} A) */
+  double* resid_hist;
+  int32_t resid_hist_cap;
+  int32_t resid_hist_len;
+} geneo_solve_info_t;
+
+/* Setup summary (host copies). */
+typedef struct {
+  int32_t n_sub;
+  int32_t dim_coarse;        /* dim V_H = sum_j m_j */
+  int32_t coarse_bandwidth;  /* half bandwidth of the banded A_H factor */
+  int32_t eig_iterations;    /* block eigensolver iterations (max over batch) */
+  int32_t block_size;        /* eigensolver block width s */
+  int64_t device_bytes;      /* device memory held by the handle */
+  double setup_ms[8];        /* per phase: structure, assembly, factor,
+                                eigensolve, basis, coarse matrix, coarse
+                                factor, total */
+} geneo_coarse_info_t;
+
+/* Fill *opt with the defaults listed above. */
+void geneo_default_options(geneo_options_t* opt);
+
+/*
+ * Build the preconditioner (Sections 3 and 4): partition of unity, local
+ * Dirichlet matrices A_j, Neumann and overlap matrices, their factorisations,
+ * the local eigenproblems, the coarse basis Z and A_H = Z^T A Z with its
+ * factorisation.  On success *out receives a new handle.  Synchronises
+ * `stream`.  On failure *out is NULL and nothing is leaked.
+ */
+geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* opt,
+                           void* stream, geneo_handle_t* out);
+
+/*
+ * z = M^{-1}_{AS,2} r (Section 3, Definition 2) for nrhs right-hand sides
+ * stored one after another (stride n).  r_dev and z_dev are device arrays of
+ * n*nrhs doubles and must not overlap.  The preconditioner is the identity on
+ * global Dirichlet dofs.  Asynchronous on `stream`.
+ */
+geneo_status_t geneo_apply(geneo_handle_t h, const double* r_dev, double* z_dev, int32_t nrhs,
+                           void* stream);
+
+/*
+ * Solve A x = b by PCG with M^{-1}_{AS,2} (x0 = 0, stop when
+ * ||r_k||_2 <= tol ||b||_2) for nrhs right-hand sides (stride n).  b and x
+ * are device arrays unless `mem` is GENEO_MEM_HOST, in which case they are
+ * host arrays and the copies are part of the call.  info may be NULL; with
+ * nrhs > 1 it reports the last right-hand side.  Synchronises `stream`.
+ */
+geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int32_t nrhs,
+                               double tol, int32_t maxit, int32_t mem,
+                               geneo_solve_info_t* info, void* stream);
+
+/* Setup summary; synchronises the handle's work. */
+geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info);
+
+/*
+ * Host copies of subdomain j's data, for inspection and parity tests.  Any
+ * output pointer may be NULL.  Sizes first: *n_neu = |N_j|, *n_dir = |D_j|,
+ * *m = m_j, *s = block width.  Then, if non-NULL and large enough (caps are
+ * element counts):
+ *   dir_dofs[n_dir]  global dofs of D_j (ascending)
+ *   pu[n_neu]        X_j on N_j
+ *   lambda[s]        Ritz values lambda (ascending; +inf where nu <= 0)
+ *   Z[n_dir*m]       coarse basis block on D_j rows, column-major
+ */
+geneo_status_t geneo_get_subdomain(geneo_handle_t h, int32_t j, int32_t* n_neu, int32_t* n_dir,
+                                   int32_t* m, int32_t* s, int32_t* dir_dofs, int64_t dir_cap,
+                                   double* pu, int64_t pu_cap, double* lambda, int64_t lambda_cap,
+                                   double* Z, int64_t z_cap);
+
+/*
+ * Overlapping subdomains from a non-overlapping element partition (Section 3:
+ * each Omega'_j is grown by `overlap` layers; one layer adds every element
+ * that shares a vertex with the current set).  Host arrays only.
+ *   part[n_elem]       part of each element in [0, n_parts)
+ *   elem_dofs          as in geneo_problem_t; vertices are the dofs
+ *   dirichlet[n]       as in geneo_problem_t
+ * Outputs are malloc'ed host arrays the caller frees with geneo_free_host:
+ * *sub_elem_ptr[n_parts+1], *sub_elem, *sub_dof_ptr[n_parts+1], *sub_dof
+ * (sorted lists, Dirichlet dofs excluded from the dof lists).
+ */
+geneo_status_t geneo_grow_partition(int64_t n, int64_t n_elem, int32_t elem_ndof,
+                                    const int32_t* elem_dofs, const uint8_t* dirichlet,
+                                    const int32_t* part, int32_t n_parts, int32_t overlap,
+                                    int64_t** sub_elem_ptr, int32_t** sub_elem,
+                                    int64_t** sub_dof_ptr, int32_t** sub_dof);
+
+void geneo_free_host(void* p);
+
+/* Release all device memory of the handle (NULL is allowed). */
+void geneo_destroy(geneo_handle_t h);
+
+/* Static string describing a status code. */
+const char* geneo_status_str(geneo_status_t s);
+
+/* Details of the last error on this handle: the device status words
+ * (code, subdomain or matrix id, row or index, extra). */
+geneo_status_t geneo_last_error(geneo_handle_t h, int32_t* code, int32_t* where, int64_t* index);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENEO_H */

@@ -1,0 +1,514 @@
+// Subdomain structure, partition of unity and local matrices.
+//
+// Section 3: Omega_j is a union of elements; R_j restricts to the dofs of
+// V_{h,0}(Omega_j), here D_j = the dofs of N_j (closure of Omega_j without
+// global Dirichlet dofs) all of whose elements lie in Omega_j.
+// Section 4.3: the discrete partition of unity X_j is 1/c_k on D_j, where c_k
+// counts the subdomains whose D contains dof k (the "sum of ones"), and 0 on
+// the subdomain boundary; the Neumann matrix Atilde_j is assembled from all
+// elements of Omega_j, the overlap matrix A_j^o from the elements that belong
+// to more than one subdomain.  Section 4.4: K_j = Atilde_j - sigma B_j with
+// B_j = X_j A_j^o X_j is the operator of the shift-and-invert transformation.
+//
+// All scatter steps are written in gather form (one thread owns one output
+// row and sums its contributions in a fixed order), so the results are
+// bitwise reproducible.  Integer counters use atomics, which is exact.
+#include <algorithm>
+#include <chrono>
+
+#include "handle.cuh"
+
+namespace geneo {
+namespace {
+
+constexpr int kT = 256;
+
+__global__ void k_count_i32(const int32_t* __restrict__ idx, int64_t m, int32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[idx[i]], 1);
+}
+
+__global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// cnt_j[a] = number of elements of Omega_j containing N-row a.
+__global__ void k_sub_elem_counts(const SubDesc* __restrict__ sub, const int32_t* __restrict__ sub_elem,
+                                  const int32_t* __restrict__ elem_dofs, int ke,
+                                  const int32_t* __restrict__ Nlist, int32_t* __restrict__ cnt_j) {
+  const SubDesc d = sub[blockIdx.x];
+  const int32_t* Nj = Nlist + d.offN;
+  const int64_t tot = (int64_t)d.nE * ke;
+  for (int64_t i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int32_t e = sub_elem[d.offE + i / ke];
+    const int32_t k = elem_dofs[(int64_t)e * ke + (i % ke)];
+    const int loc = find_i32(Nj, d.nN, k);
+    if (loc >= 0) atomicAdd(&cnt_j[d.offN + loc], 1);
+  }
+}
+
+// D_j = N-rows whose element count inside Omega_j equals the global count.
+// Ordered compaction with a block scan; writes Dlist, dpos, nToD and nD.
+__global__ void k_dirichlet_set(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                                const int32_t* __restrict__ cnt_j, const int32_t* __restrict__ cnt_all,
+                                int32_t* __restrict__ Dlist, int32_t* __restrict__ dpos,
+                                int32_t* __restrict__ nToD, int32_t* __restrict__ nD_out) {
+  __shared__ int32_t wsum[kT / 32];
+  __shared__ int32_t carry;
+  const SubDesc d = sub[blockIdx.x];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < d.nN; base += blockDim.x) {
+    const int a = base + threadIdx.x;
+    int flag = 0;
+    if (a < d.nN) flag = cnt_j[d.offN + a] == cnt_all[Nlist[d.offN + a]];
+    unsigned ball = __ballot_sync(0xffffffffu, flag);
+    int pre = __popc(ball & ((1u << lane) - 1u));
+    if (lane == 0) wsum[wid] = __popc(ball);
+    __syncthreads();
+    int woff = 0;
+    for (int w2 = 0; w2 < wid; ++w2) woff += wsum[w2];
+    int tot = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += wsum[w2];
+    const int pos = carry + woff + pre;
+    if (a < d.nN) {
+      if (flag) {
+        Dlist[d.offN + pos] = Nlist[d.offN + a];
+        dpos[d.offN + pos] = a;
+        nToD[d.offN + a] = pos;
+      } else {
+        nToD[d.offN + a] = -1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) nD_out[blockIdx.x] = carry;
+}
+
+__global__ void k_count_D(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Dlist,
+                          int32_t* __restrict__ cmul) {
+  const SubDesc d = sub[blockIdx.x];
+  for (int i = threadIdx.x; i < d.nD; i += blockDim.x) atomicAdd(&cmul[Dlist[d.offN + i]], 1);
+}
+
+// Every free dof must lie in some D_j (Section 4.3: the weights sum to one).
+__global__ void k_check_cover(const int32_t* __restrict__ cmul, const uint8_t* __restrict__ dir,
+                              int64_t n, DevStatus* st) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    if (!dir[k] && cmul[k] == 0) record_error(st, GENEO_ERR_ARG, -1, k);
+}
+
+// X_j = 1/c_k on D_j, 0 elsewhere on N_j.
+__global__ void k_pu(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                     const int32_t* __restrict__ nToD, const int32_t* __restrict__ cmul,
+                     double* __restrict__ pu) {
+  const SubDesc d = sub[blockIdx.x];
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const int64_t r = d.offN + a;
+    pu[r] = nToD[r] >= 0 ? 1.0 / (double)cmul[Nlist[r]] : 0.0;
+  }
+}
+
+__global__ void k_fill_inv(const SubDesc* __restrict__ sub, const int32_t* __restrict__ list,
+                           const int32_t* __restrict__ counts_per_sub, int use_nD,
+                           const int64_t* __restrict__ ptr, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ inv_sub, int32_t* __restrict__ inv_loc) {
+  const SubDesc d = sub[blockIdx.x];
+  const int cnt = use_nD ? d.nD : d.nN;
+  (void)counts_per_sub;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int32_t k = list[d.offN + i];
+    const int pos = atomicAdd(&cursor[k], 1);
+    inv_sub[ptr[k] + pos] = blockIdx.x;
+    inv_loc[ptr[k] + pos] = i;
+  }
+}
+
+// Sort each short inverse list by key (insertion sort; lists hold at most a
+// few dozen entries).  Makes every later gather order deterministic.
+__global__ void k_sort_lists(const int64_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ key,
+                             int32_t* __restrict__ val) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = ptr[k], e = ptr[k + 1];
+    for (int64_t i = b + 1; i < e; ++i) {
+      const int32_t kk = key[i];
+      const int32_t vv = val ? val[i] : 0;
+      int64_t j = i - 1;
+      while (j >= b && key[j] > kk) {
+        key[j + 1] = key[j];
+        if (val) val[j + 1] = val[j];
+        --j;
+      }
+      key[j + 1] = kk;
+      if (val) val[j + 1] = vv;
+    }
+  }
+}
+
+__global__ void k_fill_dof_elem(const int32_t* __restrict__ elem_dofs, int64_t n_elem, int ke,
+                                const int64_t* __restrict__ ptr, int32_t* __restrict__ cursor,
+                                int32_t* __restrict__ de) {
+  const int64_t tot = n_elem * ke;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = elem_dofs[i];
+    const int pos = atomicAdd(&cursor[k], 1);
+    de[ptr[k] + pos] = (int32_t)(i / ke);
+  }
+}
+
+// Local CSR pattern: row a of subdomain j holds the columns of global row
+// N_j[a] that are in N_j.  pass 0 counts, pass 1 fills and records the
+// half bandwidth max |a - b|.
+template <int PASS>
+__global__ void k_local_csr(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                            const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, int64_t* __restrict__ lcnt,
+                            const int64_t* __restrict__ lrow, int32_t* __restrict__ lcol,
+                            double* __restrict__ lA, int32_t* __restrict__ wK) {
+  const SubDesc d = sub[blockIdx.x];
+  const int32_t* Nj = Nlist + d.offN;
+  int wmax = 0;
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const int32_t k = Nj[a];
+    int c = 0;
+    int64_t out = PASS ? lrow[d.offN + a] : 0;
+    for (int64_t e = rowptr[k]; e < rowptr[k + 1]; ++e) {
+      const int b = find_i32(Nj, d.nN, col[e]);
+      if (b < 0) continue;
+      if (PASS) {
+        lcol[out] = b;
+        lA[out] = val[e];
+        ++out;
+        wmax = max(wmax, abs(a - b));
+      }
+      ++c;
+    }
+    if (!PASS) lcnt[d.offN + a] = c;
+  }
+  if (PASS) {
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, 16));
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, 8));
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, 4));
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, 2));
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, 1));
+    if ((threadIdx.x & 31) == 0) atomicMax(&wK[blockIdx.x], wmax);
+  }
+}
+
+// Half bandwidth of A_j in D numbering.
+__global__ void k_band_width_A(const SubDesc* __restrict__ sub, const int32_t* __restrict__ dpos,
+                               const int32_t* __restrict__ nToD, const int64_t* __restrict__ lrow,
+                               const int32_t* __restrict__ lcol, int32_t* __restrict__ wA) {
+  const SubDesc d = sub[blockIdx.x];
+  int wmax = 0;
+  for (int i = threadIdx.x; i < d.nD; i += blockDim.x) {
+    const int a = dpos[d.offN + i];
+    for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
+      const int i2 = nToD[d.offN + lcol[e]];
+      if (i2 >= 0) wmax = max(wmax, abs(i - i2));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&wA[blockIdx.x], wmax);
+}
+
+// Element assembly in gather form: row a of Omega_j sums, over the elements
+// of its dof that belong to Omega_j (ascending element id), the element
+// matrix row.  lK receives Atilde_j, lB receives A_j^o (overlap elements).
+__global__ void k_assemble(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                           const int32_t* __restrict__ sub_elem, const int64_t* __restrict__ de_ptr,
+                           const int32_t* __restrict__ de, const int32_t* __restrict__ elem_dofs,
+                           const double* __restrict__ elem_mats, int ke,
+                           const int32_t* __restrict__ e_tau, const int64_t* __restrict__ lrow,
+                           const int32_t* __restrict__ lcol, double* __restrict__ lK,
+                           double* __restrict__ lB) {
+  const SubDesc d = sub[blockIdx.x];
+  const int32_t* Nj = Nlist + d.offN;
+  const int32_t* Ej = sub_elem + d.offE;
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const int32_t k = Nj[a];
+    const int64_t r0 = lrow[d.offN + a], r1 = lrow[d.offN + a + 1];
+    for (int64_t e = r0; e < r1; ++e) {
+      lK[e] = 0.0;
+      lB[e] = 0.0;
+    }
+    for (int64_t t = de_ptr[k]; t < de_ptr[k + 1]; ++t) {
+      const int32_t el = de[t];
+      if (find_i32(Ej, d.nE, el) < 0) continue;
+      const int32_t* ed = elem_dofs + (int64_t)el * ke;
+      int ak = 0;
+      while (ak < ke && ed[ak] != k) ++ak;
+      const double* Krow = elem_mats + ((int64_t)el * ke + ak) * ke;
+      const bool ovl = e_tau[el] > 1;
+      for (int bq = 0; bq < ke; ++bq) {
+        const int bl = find_i32(Nj, d.nN, ed[bq]);
+        if (bl < 0) continue;
+        int64_t slot = r0;
+        while (slot < r1 && lcol[slot] != bl) ++slot;
+        if (slot >= r1) continue;  // cannot happen when A holds every element coupling
+        const double v = Krow[bq];
+        lK[slot] += v;
+        if (ovl) lB[slot] += v;
+      }
+    }
+  }
+}
+
+// B = X M X with M = A^o (paper form) or Atilde (full form); K = Atilde - sigma B.
+__global__ void k_pencil(const SubDesc* __restrict__ sub, const double* __restrict__ pu,
+                         const int64_t* __restrict__ lrow, const int32_t* __restrict__ lcol,
+                         double* __restrict__ lK, double* __restrict__ lB, double sigma, int full) {
+  const SubDesc d = sub[blockIdx.x];
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const double xa = pu[d.offN + a];
+    for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
+      const double at = lK[e];
+      const double m = full ? at : lB[e];
+      const double b = xa * m * pu[d.offN + lcol[e]];
+      lB[e] = b;
+      lK[e] = at - sigma * b;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_band_fill_K(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
+                              const int32_t* __restrict__ lcol, const double* __restrict__ lK,
+                              T* __restrict__ band) {
+  const SubDesc d = sub[blockIdx.x];
+  const int64_t ld = d.wK + 1;
+  T* L = band + d.bandK;
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x)
+    for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
+      const int b = lcol[e];
+      if (b <= a) L[(int64_t)b * ld + (a - b)] = (T)lK[e];
+    }
+}
+
+template <typename T>
+__global__ void k_band_fill_A(const SubDesc* __restrict__ sub, const int32_t* __restrict__ dpos,
+                              const int32_t* __restrict__ nToD, const int64_t* __restrict__ lrow,
+                              const int32_t* __restrict__ lcol, const double* __restrict__ lA,
+                              T* __restrict__ band) {
+  const SubDesc d = sub[blockIdx.x];
+  const int64_t ld = d.wA + 1;
+  T* L = band + d.bandA;
+  for (int i = threadIdx.x; i < d.nD; i += blockDim.x) {
+    const int a = dpos[d.offN + i];
+    for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
+      const int i2 = nToD[d.offN + lcol[e]];
+      if (i2 >= 0 && i2 <= i) L[(int64_t)i2 * ld + (i - i2)] = (T)lA[e];
+    }
+  }
+}
+
+inline int grid_for(int64_t m) { return (int)std::min<int64_t>(std::max<int64_t>(1, (m + kT - 1) / kT), 152 * 16); }
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& a_out,
+                               DevMem& tmp, cudaStream_t s) {
+  const int N = h->N;
+  const int64_t n = h->n;
+  const int ke = p->elem_ndof;
+  DevMem& M = h->mem;
+  GENEO_TRY(M.get(&h->Nlist, (size_t)h->sumN));
+  GENEO_TRY(M.get(&h->Dlist, (size_t)h->sumN));
+  GENEO_TRY(M.get(&h->dpos, (size_t)h->sumN));
+  GENEO_TRY(M.get(&h->nToD, (size_t)h->sumN));
+  GENEO_TRY(M.get(&h->pu, (size_t)h->sumN));
+  GENEO_CUDA(cudaMemcpyAsync(h->Nlist, p->sub_dof, sizeof(int32_t) * h->sumN,
+                             cudaMemcpyDeviceToDevice, s));
+
+  // element multiplicity e_tau (R5) and global element counts per dof
+  GENEO_TRY(tmp.get(&a_out.e_tau, (size_t)p->n_elem));
+  GENEO_TRY(tmp.get(&a_out.cnt_all, (size_t)n));
+  GENEO_CUDA(cudaMemsetAsync(a_out.e_tau, 0, sizeof(int32_t) * p->n_elem, s));
+  GENEO_CUDA(cudaMemsetAsync(a_out.cnt_all, 0, sizeof(int32_t) * n, s));
+  const int64_t n_sub_elem = h->hsub.back().offE + h->hsub.back().nE;
+  k_count_i32<<<grid_for(n_sub_elem), kT, 0, s>>>(p->sub_elem, n_sub_elem, a_out.e_tau);
+  k_count_i32<<<grid_for(p->n_elem * ke), kT, 0, s>>>(p->elem_dofs, p->n_elem * ke, a_out.cnt_all);
+  GENEO_CUDA(cudaGetLastError());
+
+  // D_j (Section 3) from element counts inside / outside Omega_j
+  int32_t* cnt_j = nullptr;
+  int32_t* nD_dev = nullptr;
+  GENEO_TRY(tmp.get(&cnt_j, (size_t)h->sumN));
+  GENEO_TRY(tmp.get(&nD_dev, (size_t)N));
+  GENEO_CUDA(cudaMemsetAsync(cnt_j, 0, sizeof(int32_t) * h->sumN, s));
+  k_sub_elem_counts<<<N, kT, 0, s>>>(h->dsub, p->sub_elem, p->elem_dofs, ke, h->Nlist, cnt_j);
+  k_dirichlet_set<<<N, kT, 0, s>>>(h->dsub, h->Nlist, cnt_j, a_out.cnt_all, h->Dlist, h->dpos,
+                                   h->nToD, nD_dev);
+  GENEO_CUDA(cudaGetLastError());
+  std::vector<int32_t> nD(N);
+  GENEO_CUDA(cudaMemcpyAsync(nD.data(), nD_dev, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < N; ++j) {
+    h->hsub[j].nD = nD[j];
+    if (nD[j] == 0) return GENEO_ERR_ARG;  // a subdomain without interior dofs
+  }
+  GENEO_CUDA(cudaMemcpyAsync(h->dsub, h->hsub.data(), sizeof(SubDesc) * N, cudaMemcpyHostToDevice, s));
+
+  // multiplicity c_k and partition of unity (Section 4.3)
+  int32_t* cmul = nullptr;
+  GENEO_TRY(tmp.get(&cmul, (size_t)n));
+  GENEO_CUDA(cudaMemsetAsync(cmul, 0, sizeof(int32_t) * n, s));
+  k_count_D<<<N, kT, 0, s>>>(h->dsub, h->Dlist, cmul);
+  k_check_cover<<<grid_for(n), kT, 0, s>>>(cmul, h->dir, n, h->dstat);
+  k_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, cmul, h->pu);
+  GENEO_CUDA(cudaGetLastError());
+
+  // inverse map dof -> (j, D index), sorted by j
+  int64_t* cnt64 = nullptr;
+  GENEO_TRY(M.get(&h->invD_ptr, (size_t)n + 1));
+  GENEO_TRY(tmp.get(&cnt64, (size_t)n + 1));
+  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(cmul, cnt64, n);
+  GENEO_CUDA(cudaMemsetAsync(cnt64 + n, 0, sizeof(int64_t), s));
+  int64_t totD = 0;
+  GENEO_TRY(exclusive_scan_i64(cnt64, h->invD_ptr, n + 1, &totD, tmp, s));
+  GENEO_TRY(M.get(&h->invD_sub, (size_t)totD));
+  GENEO_TRY(M.get(&h->invD_loc, (size_t)totD));
+  int32_t* cursor = nullptr;
+  GENEO_TRY(tmp.get(&cursor, (size_t)n));
+  GENEO_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
+  k_fill_inv<<<N, kT, 0, s>>>(h->dsub, h->Dlist, nullptr, 1, h->invD_ptr, cursor, h->invD_sub,
+                              h->invD_loc);
+  k_sort_lists<<<grid_for(n), kT, 0, s>>>(h->invD_ptr, n, h->invD_sub, h->invD_loc);
+  GENEO_CUDA(cudaGetLastError());
+  return check_status(h, s);
+}
+
+geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& out,
+                              DevMem& tmp, cudaStream_t s, double* ms_assembly, double* ms_factor) {
+  AssemblyOut& a_out = out;
+  auto t0 = std::chrono::steady_clock::now();
+  const int N = h->N;
+  const int64_t n = h->n;
+  const int ke = p->elem_ndof;
+
+  // dof -> element lists (ascending element id)
+  int64_t* de_cnt = nullptr;
+  int64_t* de_ptr = nullptr;
+  int32_t* de = nullptr;
+  int32_t* cursor = nullptr;
+  GENEO_TRY(tmp.get(&de_cnt, (size_t)n + 1));
+  GENEO_TRY(tmp.get(&de_ptr, (size_t)n + 1));
+  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(a_out.cnt_all, de_cnt, n);
+  GENEO_CUDA(cudaMemsetAsync(de_cnt + n, 0, sizeof(int64_t), s));
+  int64_t tot = 0;
+  GENEO_TRY(exclusive_scan_i64(de_cnt, de_ptr, n + 1, &tot, tmp, s));
+  GENEO_TRY(tmp.get(&de, (size_t)tot));
+  GENEO_TRY(tmp.get(&cursor, (size_t)n));
+  GENEO_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
+  k_fill_dof_elem<<<grid_for(p->n_elem * ke), kT, 0, s>>>(p->elem_dofs, p->n_elem, ke, de_ptr,
+                                                          cursor, de);
+  k_sort_lists<<<grid_for(n), kT, 0, s>>>(de_ptr, n, de, nullptr);
+  GENEO_CUDA(cudaGetLastError());
+
+  // local CSR pattern over N-rows
+  int64_t* lcnt = nullptr;
+  GENEO_TRY(tmp.get(&lcnt, (size_t)h->sumN + 1));
+  GENEO_TRY(tmp.get(&out.lrow, (size_t)h->sumN + 1));
+  GENEO_CUDA(cudaMemsetAsync(lcnt + h->sumN, 0, sizeof(int64_t), s));
+  k_local_csr<0><<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->rowptr, h->col, h->val, lcnt, nullptr,
+                                  nullptr, nullptr, nullptr);
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_TRY(exclusive_scan_i64(lcnt, out.lrow, h->sumN + 1, &out.lnnz, tmp, s));
+  int32_t *wK = nullptr, *wA = nullptr;
+  GENEO_TRY(tmp.get(&out.lcol, (size_t)out.lnnz));
+  GENEO_TRY(tmp.get(&out.lA, (size_t)out.lnnz));
+  double* lA = out.lA;
+  GENEO_TRY(tmp.get(&wK, (size_t)N));
+  GENEO_TRY(tmp.get(&wA, (size_t)N));
+  GENEO_CUDA(cudaMemsetAsync(wK, 0, sizeof(int32_t) * N, s));
+  GENEO_CUDA(cudaMemsetAsync(wA, 0, sizeof(int32_t) * N, s));
+  k_local_csr<1><<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->rowptr, h->col, h->val, nullptr, out.lrow,
+                                  out.lcol, lA, wK);
+  k_band_width_A<<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, wA);
+  GENEO_CUDA(cudaGetLastError());
+  std::vector<int32_t> hwK(N), hwA(N);
+  GENEO_CUDA(cudaMemcpyAsync(hwK.data(), wK, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaMemcpyAsync(hwA.data(), wA, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  int64_t bandK_tot = 0, bandA_tot = 0;
+  out.maxwK = 0;
+  h->maxwA = 0;
+  for (int j = 0; j < N; ++j) {
+    SubDesc& d = h->hsub[j];
+    d.wK = hwK[j];
+    d.wA = hwA[j];
+    d.bandK = bandK_tot;
+    d.bandA = bandA_tot;
+    bandK_tot += (int64_t)d.nN * (d.wK + 1);
+    bandA_tot += (int64_t)d.nD * (d.wA + 1);
+    out.maxwK = std::max(out.maxwK, d.wK);
+    h->maxwA = std::max(h->maxwA, d.wA);
+  }
+  GENEO_CUDA(cudaMemcpyAsync(h->dsub, h->hsub.data(), sizeof(SubDesc) * N, cudaMemcpyHostToDevice, s));
+
+  // numeric assembly of Atilde_j, A_j^o, then B_j and K_j
+  GENEO_TRY(tmp.get(&out.lK, (size_t)out.lnnz));
+  GENEO_TRY(tmp.get(&out.lB, (size_t)out.lnnz));
+  k_assemble<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, de_ptr, de, p->elem_dofs,
+                              p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB);
+  k_pencil<<<N, kT, 0, s>>>(h->dsub, h->pu, out.lrow, out.lcol, out.lK, out.lB, h->opt.sigma,
+                            h->opt.eig_form == GENEO_EIG_FULL);
+  GENEO_CUDA(cudaGetLastError());
+
+  // band storage, descriptors
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  GENEO_TRY(tmp.alloc(&out.bandK, esz * (size_t)std::max<int64_t>(bandK_tot, 1)));
+  GENEO_TRY(h->mem.alloc(&h->bandA, esz * (size_t)std::max<int64_t>(bandA_tot, 1)));
+  GENEO_CUDA(cudaMemsetAsync(out.bandK, 0, esz * bandK_tot, s));
+  GENEO_CUDA(cudaMemsetAsync(h->bandA, 0, esz * bandA_tot, s));
+  std::vector<BandDesc> bk(N), ba(N);
+  for (int j = 0; j < N; ++j) {
+    const SubDesc& d = h->hsub[j];
+    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, 0};
+    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, 0};
+  }
+  GENEO_TRY(tmp.get(&out.dbandK, (size_t)N));
+  GENEO_TRY(h->mem.get(&h->dbandA, (size_t)N));
+  GENEO_CUDA(cudaMemcpyAsync(out.dbandK, bk.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->dbandA, ba.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
+  if (h->fp32) {
+    k_band_fill_K<float><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (float*)out.bandK);
+    k_band_fill_A<float><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
+                                          (float*)h->bandA);
+  } else {
+    k_band_fill_K<double><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (double*)out.bandK);
+    k_band_fill_A<double><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
+                                           (double*)h->bandA);
+  }
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_TRY(check_status(h, s));
+  *ms_assembly = ms_since(t0);
+
+  // batched Cholesky of A_j and K_j (Sections 3 and 4.4)
+  auto t1 = std::chrono::steady_clock::now();
+  if (h->fp32) {
+    GENEO_TRY(band_potrf<float>((float*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
+    GENEO_TRY(band_potrf<float>((float*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
+  } else {
+    GENEO_TRY(band_potrf<double>((double*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
+    GENEO_TRY(band_potrf<double>((double*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
+  }
+  GENEO_TRY(check_status(h, s));
+  *ms_factor = ms_since(t1);
+  return GENEO_OK;
+}
+
+}  // namespace geneo

@@ -1,0 +1,163 @@
+// Internal declarations shared by the translation units of libgeneo.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "geneo.h"
+
+namespace geneo {
+
+// --------------------------------------------------------------------------
+// Status handling.  Device code records the first error it meets in a small
+// status block (code, where, index); host code returns geneo_status_t.
+// --------------------------------------------------------------------------
+struct DevStatus {
+  int32_t code;    // geneo_status_t, 0 = OK
+  int32_t where;   // subdomain / matrix id
+  int64_t index;   // row, iteration or other index
+};
+
+__device__ __forceinline__ void record_error(DevStatus* st, int code, int where, int64_t index) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->where = where;
+    st->index = index;
+  }
+}
+
+#define GENEO_CUDA(call)                                \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      geneo::set_cuda_error(e_, #call, __FILE__, __LINE__); \
+      return GENEO_ERR_CUDA;                            \
+    }                                                   \
+  } while (0)
+
+#define GENEO_TRY(expr)                      \
+  do {                                       \
+    geneo_status_t s_ = (expr);              \
+    if (s_ != GENEO_OK) return s_;           \
+  } while (0)
+
+void set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+const std::string& last_cuda_error();
+
+// --------------------------------------------------------------------------
+// Per-subdomain descriptor (device and host copies).
+// --------------------------------------------------------------------------
+struct SubDesc {
+  int64_t offN;    // offset of subdomain rows in N-indexed arrays
+  int64_t offE;    // offset into sub_elem
+  int64_t bandA;   // element offset of the Dirichlet band factor
+  int64_t bandK;   // element offset of the shifted Neumann band factor
+  int64_t offZ;    // element offset of Z_j (nD x m, column-major)
+  int64_t offY;    // element offset of Y_j = A Z_j (nN x m, column-major)
+  int32_t nN, nD, nE;
+  int32_t wA, wK;  // half bandwidths
+  int32_t s;       // eigensolver block width actually used
+  int32_t m;       // coarse vectors taken
+  int32_t offH;    // first coarse index of this subdomain
+};
+
+// Band matrix descriptor for the batched Cholesky / triangular solves.
+// Lower band stored column-major: entry (r, c), 0 <= r - c <= w, at
+// base[c * ld + (r - c)], ld = w + 1.
+struct BandDesc {
+  int64_t off;     // element offset of the band
+  int32_t n, w;
+  int32_t id;      // reported in errors
+  int32_t pad;
+};
+
+// --------------------------------------------------------------------------
+// Device helpers.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// index of key in sorted a[0..n) or -1
+__device__ __forceinline__ int find_i32(const int32_t* a, int n, int32_t key) {
+  int p = lower_bound_i32(a, n, key);
+  return (p < n && a[p] == key) ? p : -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (deterministic: fixed tree).  `red` needs blockDim/32 slots.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? red[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): counter -> 64 random bits.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// --------------------------------------------------------------------------
+// Simple owning device buffer.
+// --------------------------------------------------------------------------
+struct DevMem {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  geneo_status_t alloc(void** p, size_t n);
+  template <typename T>
+  geneo_status_t get(T** p, size_t count) {
+    return alloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  void release(void* p);
+  void free_all();
+};
+
+// --------------------------------------------------------------------------
+// Kernel launchers implemented in the .cu files.
+// --------------------------------------------------------------------------
+// scan.cu: exclusive prefix sum of n int64 (out may alias in); returns total.
+geneo_status_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
+                                  DevMem& tmp, cudaStream_t st);
+
+// band.cu
+template <typename T>
+geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
+                          DevStatus* st, cudaStream_t s);
+// Solve L L^T X = X in place for `nrhs` columns per matrix (column-major,
+// leading dimension = matrix n, column stride = n); X for matrix i starts
+// at xbase + xoff[i]; nrhs_dev (may be NULL) gives per-matrix column counts
+// capped by nrhs; skip_dev (may be NULL) skips matrices with a non-zero flag.
+template <typename T>
+geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
+                          double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
+                          const int32_t* skip_dev, cudaStream_t s);
+
+}  // namespace geneo

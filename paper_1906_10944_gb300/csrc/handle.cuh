@@ -1,0 +1,105 @@
+// The device state owned by a geneo handle, and the phase entry points the
+// setup orchestration calls.
+#pragma once
+
+#include "common.cuh"
+
+struct geneo_handle_s {
+  geneo::DevMem mem;        // everything the handle keeps
+  cudaStream_t stream = 0;  // stream of the last synchronising call
+  geneo_options_t opt{};
+  bool fp32 = false;
+
+  // global problem (device copies)
+  int64_t n = 0, nnz = 0;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  uint8_t* dir = nullptr;
+
+  // subdomains
+  int N = 0;
+  int64_t sumN = 0;                // total rows of all N_j
+  std::vector<geneo::SubDesc> hsub;
+  geneo::SubDesc* dsub = nullptr;
+  int32_t* Nlist = nullptr;        // [sumN] global dof of each N-row
+  int32_t* Dlist = nullptr;        // [sumN] D_j stored at offN (first nD entries)
+  int32_t* dpos = nullptr;         // [sumN] position in N_j of D entry
+  int32_t* nToD = nullptr;         // [sumN] D index of an N-row or -1
+  double* pu = nullptr;            // [sumN] X_j on N_j
+
+  // inverse map global dof -> (subdomain, D index), sorted by subdomain
+  int64_t* invD_ptr = nullptr;     // [n+1]
+  int32_t* invD_sub = nullptr;
+  int32_t* invD_loc = nullptr;
+
+  // Dirichlet band factors
+  void* bandA = nullptr;           // double or float
+  geneo::BandDesc* dbandA = nullptr;
+  int maxwA = 0;
+
+  // coarse space
+  int dimH = 0, wH = 0;
+  int maxm = 0;
+  double* Z = nullptr;             // per subdomain nD x m, column-major
+  double* bandH = nullptr;         // band factor of A_H
+  geneo::BandDesc* dbandH = nullptr;
+  int64_t* xoffH = nullptr;        // {0}
+  std::vector<double> lambda_host; // [N * s] ascending lambda per subdomain
+  int s_block = 0;
+  int eig_iters = 0;
+
+  // apply / PCG work
+  double* u = nullptr;             // [sumD] local solutions
+  int64_t* uoff = nullptr;         // [N] offsets into u (= offN)
+  double* cH = nullptr;            // [dimH] coarse vector
+  double *r = nullptr, *zv = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;
+  double* red = nullptr;           // reduction scratch
+  double* scal = nullptr;          // device scalars
+  double* hpin = nullptr;          // pinned host scalars
+  int red_blocks = 0;
+
+  geneo::DevStatus* dstat = nullptr;
+  geneo::DevStatus hstat{};
+  double setup_ms[8] = {0};
+};
+
+namespace geneo {
+geneo_status_t check_status(geneo_handle_s* h, cudaStream_t s);
+
+// assembly.cu
+struct AssemblyOut {
+  // local CSR over N-rows (pattern of A restricted to N_j x N_j)
+  int64_t* lrow = nullptr;  // [sumN+1]
+  int32_t* lcol = nullptr;
+  double* lK = nullptr;     // K = Atilde - sigma B
+  double* lB = nullptr;     // B = X A^o X  (or X Atilde X)
+  double* lA = nullptr;     // A on the local pattern
+  int64_t lnnz = 0;
+  int32_t* e_tau = nullptr;    // element multiplicity (number of subdomains)
+  int32_t* cnt_all = nullptr;  // elements per dof
+  void* bandK = nullptr;
+  BandDesc* dbandK = nullptr;
+  int maxwK = 0;
+};
+geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& a,
+                               DevMem& tmp, cudaStream_t s);
+geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& out,
+                              DevMem& tmp, cudaStream_t s, double* ms_assembly,
+                              double* ms_factor);
+
+// lobpcg.cu
+geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& a, DevMem& tmp, cudaStream_t s,
+                                double** X_out, int64_t* ld_unused);
+
+// coarse.cu
+geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& a, const double* X,
+                            DevMem& tmp, cudaStream_t s, double* ms_basis, double* ms_matrix,
+                            double* ms_factor);
+
+// solve.cu
+geneo_status_t alloc_solver(geneo_handle_s* h);
+geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStream_t s);
+geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
+                   geneo_solve_info_t* info, cudaStream_t s);
+}  // namespace geneo

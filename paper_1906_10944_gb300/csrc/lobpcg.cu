@@ -1,0 +1,733 @@
+// Batched shift-and-invert block eigensolver for the GenEO local problems.
+//
+// Section 3, eq. 5 and Section 4.3: Atilde_j p = lambda X_j A_j^o X_j p.
+// Section 4.4: with K_j = Atilde_j - sigma B_j (B_j = X_j A_j^o X_j) the
+// transformed problem B_j x = nu K_j x, nu = 1/(lambda - sigma), has the
+// same eigenvectors and the wanted (smallest) lambda become the largest nu.
+//
+// The paper solves each transformed problem with ARPACK.  Here all
+// subdomains are solved at once by a locally optimal block preconditioned
+// conjugate-gradient iteration (LOBPCG) on the pencil (B_j, K_j), with the
+// exact shift-invert operator K_j^{-1} (banded Cholesky factor) as the
+// preconditioner.  Per iteration and subdomain:
+//   R = B X - K X diag(nu)            residuals, relative norms rn_i
+//   W = K^{-1} R[:, active]           active = columns with rn_i > tol
+//   Q = [W, P], K-orthogonalised against X twice, K-orthonormalised by SVQB
+//   Rayleigh-Ritz on S = [X, Q] (S^T K S = I): eig(S^T B S), top s
+//   P = Q U_Q, X = S U
+// Stop when every Ritz pair below the threshold tau is converged and the
+// first one at or above tau is converged too (or all nev_max in fixed-count
+// mode).  Rayleigh-Ritz, residuals and orthogonalisation are FP64; the
+// K^{-1} solves use the factor's precision.
+//
+// Dense small problems (at most kMaxW = 104 columns) are solved by parallel
+// cyclic Jacobi in shared memory, one thread block per subdomain.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+
+#include "handle.cuh"
+
+namespace geneo {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxW = 104;      // largest [X, Q] width handled by the dense kernels
+constexpr int kRS = 4;          // row splits of the Gram kernel
+constexpr int kRB = 24;         // rows per shared-memory chunk in the Gram kernel
+constexpr int kMaxSweeps = 40;  // bound of the Jacobi sweep loop
+
+// A multivector operand: columns [c0 + c0d[j], + width) of a buffer holding W
+// columns per subdomain (rows = nN_j, column-major, ld = nN_j).
+struct ColRef {
+  double* base;
+  int W;
+  int c0;
+  const int32_t* c0d;
+  int w;
+  const int32_t* wd;
+  const int32_t* wd2;  // width = w + wd[j] + wd2[j] (NULL terms are 0)
+};
+
+__device__ __forceinline__ int cr_c0(const ColRef& r, int j) { return r.c0 + (r.c0d ? r.c0d[j] : 0); }
+__device__ __forceinline__ int cr_w(const ColRef& r, int j) {
+  return r.w + (r.wd ? r.wd[j] : 0) + (r.wd2 ? r.wd2[j] : 0);
+}
+__device__ __forceinline__ double* cr_ptr(const ColRef& r, const SubDesc& d, int j) {
+  return r.base + d.offN * (int64_t)r.W + (int64_t)cr_c0(r, j) * d.nN;
+}
+
+ColRef cref(double* base, int W, int c0, const int32_t* c0d, int w, const int32_t* wd,
+            const int32_t* wd2 = nullptr) {
+  return ColRef{base, W, c0, c0d, w, wd, wd2};
+}
+
+// ---------------------------------------------------------------------------
+// Multivector kernels (grid: x = row blocks, y = subdomain).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kT)
+k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
+       const int32_t* __restrict__ lcol, const double* __restrict__ v1, const double* __restrict__ v2,
+       ColRef X, ColRef Y1, ColRef Y2, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int w = cr_w(X, j);
+  const double* x = cr_ptr(X, d, j);
+  double* y1 = cr_ptr(Y1, d, j);
+  double* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
+  const int64_t e0 = lrow[d.offN + a], e1 = lrow[d.offN + a + 1];
+  for (int c = 0; c < w; ++c) {
+    const double* xc = x + (int64_t)c * d.nN;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const double xv = xc[lcol[e]];
+      s1 += v1[e] * xv;
+      if (v2) s2 += v2[e] * xv;
+    }
+    y1[(int64_t)c * d.nN + a] = s1;
+    if (v2) y2[(int64_t)c * d.nN + a] = s2;
+  }
+}
+
+// Y = X columnwise copy
+__global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef Dst,
+                            const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int w = cr_w(Src, j);
+  const double* s = cr_ptr(Src, d, j);
+  double* t = cr_ptr(Dst, d, j);
+  for (int c = 0; c < w; ++c) t[(int64_t)c * d.nN + a] = s[(int64_t)c * d.nN + a];
+}
+
+// Partial Gram matrices G = A^T B over a row split; ld of G is ldg.
+// Each thread owns up to 3 register tiles of 4x4; sym computes the lower
+// triangle only (A == B).
+__global__ void __launch_bounds__(kT)
+k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double* __restrict__ Gp,
+            int ldg, int nsub, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y, rs = blockIdx.x;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(B, j);
+  double* G = Gp + ((int64_t)rs * nsub + j) * ldg * ldg;
+  if (p <= 0 || q <= 0) return;
+  const double* a = cr_ptr(A, d, j);
+  const double* b = cr_ptr(B, d, j);
+  __shared__ double As[kRB][kMaxW + 1];
+  __shared__ double Bs[kRB][kMaxW + 1];
+  const int tp = (p + 3) >> 2, tq = (q + 3) >> 2;
+  const int ntiles = tp * tq;
+  double acc[3][16];
+  int own[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int t = threadIdx.x + u * kT;
+    own[u] = -1;
+    if (t < ntiles) {
+      const int ti = t % tp, tj = t / tp;
+      if (!sym || tj <= ti) own[u] = t;
+    }
+#pragma unroll
+    for (int z = 0; z < 16; ++z) acc[u][z] = 0.0;
+  }
+  const int r0 = (int)((int64_t)rs * d.nN / kRS), r1 = (int)((int64_t)(rs + 1) * d.nN / kRS);
+  for (int rb = r0; rb < r1; rb += kRB) {
+    const int nr = min(kRB, r1 - rb);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kRB * p; idx += kT) {
+      const int r = idx % kRB, c = idx / kRB;
+      As[r][c] = r < nr ? a[(int64_t)c * d.nN + rb + r] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < kRB * q; idx += kT) {
+      const int r = idx % kRB, c = idx / kRB;
+      Bs[r][c] = r < nr ? b[(int64_t)c * d.nN + rb + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (own[u] < 0) continue;
+      const int ti = own[u] % tp, tj = own[u] / tp;
+      for (int r = 0; r < nr; ++r) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+          av[z] = (4 * ti + z < p) ? As[r][4 * ti + z] : 0.0;
+          bv[z] = (4 * tj + z < q) ? Bs[r][4 * tj + z] : 0.0;
+        }
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[u][z * 4 + y] += av[z] * bv[y];
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    if (own[u] < 0) continue;
+    const int ti = own[u] % tp, tj = own[u] / tp;
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int r = 4 * ti + z, c = 4 * tj + y;
+        if (r < p && c < q) G[(int64_t)c * ldg + r] = acc[u][z * 4 + y];
+      }
+  }
+}
+
+// G = sum of the row-split partials (fixed order); sym mirrors the lower part.
+__global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym,
+                              const double* __restrict__ Gp, double* __restrict__ G, int ldg,
+                              int nsub, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.x;
+  if (skip && skip[j]) return;
+  const int p = cr_w(A, j), q = cr_w(B, j);
+  for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
+    int r = idx % p, c = idx / p;
+    int rr = r, cc = c;
+    if (sym && c > r) { rr = c; cc = r; }
+    double s = 0.0;
+    for (int rs = 0; rs < kRS; ++rs) s += Gp[((int64_t)rs * nsub + j) * ldg * ldg + (int64_t)cc * ldg + rr];
+    G[(int64_t)j * ldg * ldg + (int64_t)c * ldg + r] = s;
+  }
+}
+
+// C = beta*C + alpha * A * T, T = rows [t0 + t0d[j], ...) of a per-subdomain
+// ldg x ldg matrix (column-major).  p = width(A), q = width(C).
+__global__ void __launch_bounds__(kT)
+k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
+          int t0, const int32_t* __restrict__ t0d, ColRef C, double alpha, double beta,
+          const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(C, j);
+  if (q <= 0) return;
+  extern __shared__ double Ts[];  // p x q, Ts[i*q + c]
+  const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
+  for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
+    const int i = idx % p, c = idx / p;
+    Ts[i * q + c] = T[(int64_t)c * ldg + i];
+  }
+  __syncthreads();
+  const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a_row >= d.nN) return;
+  const double* a = cr_ptr(A, d, j);
+  double* cm = cr_ptr(C, d, j);
+  constexpr int CB = 8;
+  for (int c0 = 0; c0 < q; c0 += CB) {
+    double acc[CB];
+#pragma unroll
+    for (int z = 0; z < CB; ++z) acc[z] = 0.0;
+    for (int i = 0; i < p; ++i) {
+      const double av = a[(int64_t)i * d.nN + a_row];
+#pragma unroll
+      for (int z = 0; z < CB; ++z)
+        if (c0 + z < q) acc[z] += av * Ts[i * q + c0 + z];
+    }
+#pragma unroll
+    for (int z = 0; z < CB; ++z) {
+      const int c = c0 + z;
+      if (c < q) {
+        double* o = cm + (int64_t)c * d.nN + a_row;
+        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc[z];
+      }
+    }
+  }
+}
+
+// Counter-based start block: uniform(-1, 1) from SplitMix64.
+__global__ void k_init_random(const SubDesc* __restrict__ sub, ColRef X, uint64_t seed) {
+  const int j = blockIdx.y;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int w = cr_w(X, j);
+  double* x = cr_ptr(X, d, j);
+  for (int c = 0; c < w; ++c) {
+    const uint64_t ctr = ((uint64_t)j << 40) ^ ((uint64_t)c << 28) ^ (uint64_t)a;
+    const uint64_t u = splitmix64(seed ^ splitmix64(ctr));
+    x[(int64_t)c * d.nN + a] = (double)(u >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense symmetric eigensolver: parallel cyclic Jacobi (round-robin pairs).
+// A (m x m, row stride lda) is overwritten by its diagonal form, V receives
+// the eigenvectors (columns).  Whole block participates.
+// ---------------------------------------------------------------------------
+__device__ void jacobi_eig(double* A, int lda, double* V, int ldv, int m, double* cs, double* sn,
+                           double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int M = m + (m & 1);
+  for (int idx = tid; idx < m * m; idx += nt) {
+    const int r = idx % m, c = idx / m;
+    V[r * ldv + c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (m <= 1) return;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    // convergence test: off-diagonal mass relative to the whole
+    double off = 0.0, all = 0.0;
+    for (int idx = tid; idx < m * m; idx += nt) {
+      const int r = idx % m, c = idx / m;
+      const double v = A[r * lda + c];
+      all += v * v;
+      if (r != c) off += v * v;
+    }
+    off = block_sum(off, red);
+    all = block_sum(all, red);
+    if (off <= 1e-30 * all || all == 0.0) break;
+    for (int round = 0; round < M - 1; ++round) {
+      // pair k: (M-1, round) for k = 0; ((round+k)%(M-1), (round-k+M-1)%(M-1)) otherwise
+      for (int k = tid; k < M / 2; k += nt) {
+        int pi, qi;
+        if (k == 0) { pi = M - 1; qi = round; }
+        else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
+        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+        double c = 1.0, s = 0.0;
+        if (qi < m) {
+          const double apq = A[pi * lda + qi];
+          const double app = A[pi * lda + pi], aqq = A[qi * lda + qi];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            const double theta = (aqq - app) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = s;
+      }
+      __syncthreads();
+      // rows: new_p = c p - s q, new_q = s p + c q
+      for (int idx = tid; idx < (M / 2) * m; idx += nt) {
+        const int k = idx / m, col = idx % m;
+        int pi, qi;
+        if (k == 0) { pi = M - 1; qi = round; }
+        else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
+        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+        if (qi >= m || sn[k] == 0.0) continue;
+        const double c = cs[k], s = sn[k];
+        const double ap = A[pi * lda + col], aq = A[qi * lda + col];
+        A[pi * lda + col] = c * ap - s * aq;
+        A[qi * lda + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns of A and of V
+      for (int idx = tid; idx < (M / 2) * m; idx += nt) {
+        const int k = idx / m, row = idx % m;
+        int pi, qi;
+        if (k == 0) { pi = M - 1; qi = round; }
+        else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
+        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+        if (qi >= m || sn[k] == 0.0) continue;
+        const double c = cs[k], s = sn[k];
+        const double ap = A[row * lda + pi], aq = A[row * lda + qi];
+        A[row * lda + pi] = c * ap - s * aq;
+        A[row * lda + qi] = s * ap + c * aq;
+        const double vp = V[row * ldv + pi], vq = V[row * ldv + qi];
+        V[row * ldv + pi] = c * vp - s * vq;
+        V[row * ldv + qi] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// SVQB: columns whose Gram matrix is G (q x q) -> T (q x r) with
+// (M T)^T K (M T) = I; directions with eigenvalue below drop * max are
+// removed.  Writes T into Tout (ldg) and r into r_out[j].
+__global__ void __launch_bounds__(kT)
+k_svqb(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
+       const int32_t* __restrict__ wq, const int32_t* __restrict__ wq2, int32_t* __restrict__ r_out,
+       double drop, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.x;
+  if (skip && skip[j]) return;
+  const int q = (wq ? wq[j] : 0) + (wq2 ? wq2[j] : 0);
+  extern __shared__ double sm[];
+  constexpr int LD = kMaxW + 1;
+  double* A = sm;
+  double* V = A + kMaxW * LD;
+  double* dsc = V + kMaxW * LD;
+  double* ev = dsc + kMaxW;
+  double* cs = ev + kMaxW;
+  double* sn = cs + kMaxW;
+  double* red = sn + kMaxW;
+  __shared__ int keep[kMaxW];
+  __shared__ int nkeep;
+  if (q <= 0) {
+    if (threadIdx.x == 0) r_out[j] = 0;
+    return;
+  }
+  const double* G = Gall + (int64_t)j * ldg * ldg;
+  for (int i = threadIdx.x; i < q; i += blockDim.x) {
+    const double g = G[(int64_t)i * ldg + i];
+    dsc[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    const int r = idx % q, c = idx / q;
+    const double g = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
+    A[r * LD + c] = dsc[r] * g * dsc[c];
+  }
+  __syncthreads();
+  jacobi_eig(A, LD, V, LD, q, cs, sn, red);
+  for (int i = threadIdx.x; i < q; i += blockDim.x) ev[i] = A[i * LD + i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < q; ++i) mx = fmax(mx, ev[i]);
+    int r = 0;
+    for (int i = 0; i < q; ++i)
+      if (mx > 0.0 && ev[i] > drop * mx) keep[r++] = i;
+    nkeep = r;
+    r_out[j] = r;
+  }
+  __syncthreads();
+  double* T = Tout + (int64_t)j * ldg * ldg;
+  for (int idx = threadIdx.x; idx < q * nkeep; idx += blockDim.x) {
+    const int r = idx % q, k = idx / q;
+    const int i = keep[k];
+    T[(int64_t)k * ldg + r] = dsc[r] * V[r * LD + i] / sqrt(ev[i]);
+  }
+}
+
+// Rayleigh-Ritz: eig of G (m x m, m = s_j + q_j), keep the s_j largest in
+// descending order: nu[0..s_j), U (m x s_j) into Tout.
+__global__ void __launch_bounds__(kT)
+k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
+     const int32_t* __restrict__ sj, const int32_t* __restrict__ qj, double* __restrict__ nu_out,
+     int ldnu, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.x;
+  if (skip && skip[j]) return;
+  const int s = sj[j];
+  const int m = s + (qj ? qj[j] : 0);
+  extern __shared__ double sm[];
+  constexpr int LD = kMaxW + 1;
+  double* A = sm;
+  double* V = A + kMaxW * LD;
+  double* ev = V + kMaxW * LD;
+  double* cs = ev + kMaxW;
+  double* sn = cs + kMaxW;
+  double* red = sn + kMaxW;
+  __shared__ int order[kMaxW];
+  if (m <= 0) return;
+  const double* G = Gall + (int64_t)j * ldg * ldg;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int r = idx % m, c = idx / m;
+    A[r * LD + c] = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
+  }
+  __syncthreads();
+  jacobi_eig(A, LD, V, LD, m, cs, sn, red);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ev[i] = A[i * LD + i];
+  __syncthreads();
+  // rank in descending order (ties by index)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    int rk = 0;
+    for (int k = 0; k < m; ++k) rk += (ev[k] > ev[i]) || (ev[k] == ev[i] && k < i);
+    order[rk] = i;
+  }
+  __syncthreads();
+  double* U = Tout + (int64_t)j * ldg * ldg;
+  for (int idx = threadIdx.x; idx < m * s; idx += blockDim.x) {
+    const int r = idx % m, k = idx / m;
+    U[(int64_t)k * ldg + r] = V[r * LD + order[k]];
+  }
+  for (int k = threadIdx.x; k < s; k += blockDim.x) nu_out[(int64_t)j * ldnu + k] = ev[order[k]];
+}
+
+// Residuals, convergence and the next search block.  One block per
+// subdomain.  R = BX - KX diag(nu) is written (active columns only,
+// compacted) to S after X, then the s_p columns of P follow.
+__global__ void __launch_bounds__(kT)
+k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef P,
+        const double* __restrict__ nu_all, int ldnu, const int32_t* __restrict__ sj,
+        const int32_t* __restrict__ spj, int32_t* __restrict__ aj, int32_t* __restrict__ qj,
+        int32_t* __restrict__ done, int32_t* __restrict__ iters, int32_t* __restrict__ notdone,
+        double* __restrict__ rn_out, double tol, double tau, double sigma, int nev, int fixed,
+        int it) {
+  const int j = blockIdx.x;
+  if (done[j]) return;
+  const SubDesc d = sub[j];
+  const int s = sj[j];
+  const double* nu = nu_all + (int64_t)j * ldnu;
+  const double* bx = cr_ptr(BX, d, j);
+  const double* kx = cr_ptr(KX, d, j);
+  __shared__ double rn[kMaxW];
+  __shared__ int act[kMaxW];
+  __shared__ int na, fin;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < s; c += nw) {
+    double r2 = 0.0, b2 = 0.0, k2 = 0.0;
+    const double* bc = bx + (int64_t)c * d.nN;
+    const double* kc = kx + (int64_t)c * d.nN;
+    const double nc = nu[c];
+    for (int a = lane; a < d.nN; a += 32) {
+      const double bv = bc[a], kv = kc[a];
+      const double rv = bv - nc * kv;
+      r2 += rv * rv;
+      b2 += bv * bv;
+      k2 += kv * kv;
+    }
+    r2 = warp_sum(r2);
+    b2 = warp_sum(b2);
+    k2 = warp_sum(k2);
+    if (lane == 0) {
+      const double den = sqrt(b2) + fabs(nc) * sqrt(k2);
+      rn[c] = den > 0.0 ? sqrt(r2) / den : 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    if (fixed) {
+      for (int i = 0; i < min(nev, s); ++i) ok = ok && rn[i] <= tol;
+    } else {
+      for (int i = 0; i < min(nev, s); ++i) {
+        if (rn[i] > tol) { ok = false; break; }
+        const double lam = nu[i] > 0.0 ? sigma + 1.0 / nu[i] : INFINITY;
+        if (lam >= tau) break;
+      }
+    }
+    int k = 0;
+    for (int i = 0; i < s; ++i)
+      if (rn[i] > tol) act[k++] = i;
+    na = k;
+    fin = ok || k == 0;
+    if (fin) {
+      done[j] = 1;
+    } else {
+      atomicAdd(notdone, 1);
+    }
+    iters[j] = it;
+    aj[j] = fin ? 0 : k;
+    qj[j] = fin ? 0 : k + spj[j];
+    for (int i = 0; i < s; ++i) rn_out[(int64_t)j * ldnu + i] = rn[i];
+  }
+  __syncthreads();
+  if (fin) return;
+  double* sbase = cr_ptr(S, d, j);
+  double* w0 = sbase + (int64_t)s * d.nN;
+  const int k = na;
+  for (int t = 0; t < k; ++t) {
+    const int c = act[t];
+    const double nc = nu[c];
+    const double* bc = bx + (int64_t)c * d.nN;
+    const double* kc = kx + (int64_t)c * d.nN;
+    double* o = w0 + (int64_t)t * d.nN;
+    for (int a = threadIdx.x; a < d.nN; a += blockDim.x) o[a] = bc[a] - nc * kc[a];
+  }
+  const int sp = spj[j];
+  const double* pc = cr_ptr(P, d, j);
+  for (int t = 0; t < sp; ++t) {
+    double* o = w0 + (int64_t)(k + t) * d.nN;
+    const double* src = pc + (int64_t)t * d.nN;
+    for (int a = threadIdx.x; a < d.nN; a += blockDim.x) o[a] = src[a];
+  }
+}
+
+__global__ void k_set_i32(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int n,
+                          const int32_t* __restrict__ skip) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && !(skip && skip[j])) dst[j] = src[j];
+}
+
+inline double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tmp, cudaStream_t st,
+                                double** X_out, int64_t* ld_unused) {
+  (void)ld_unused;
+  const int N = h->N;
+  const geneo_options_t& o = h->opt;
+  const int nev = o.nev_max;
+  const int s = h->s_block;
+  const int W3 = 3 * s;
+  const int ldg = W3;
+  if (W3 > kMaxW) return GENEO_ERR_ARG;
+  const int64_t rows = h->sumN;
+  double *S, *KS, *BS, *P, *Tmp, *G, *Gp, *Tm, *nu, *rn;
+  GENEO_TRY(tmp.get(&S, (size_t)rows * W3));
+  GENEO_TRY(tmp.get(&KS, (size_t)rows * W3));
+  GENEO_TRY(tmp.get(&BS, (size_t)rows * W3));
+  GENEO_TRY(tmp.get(&Tmp, (size_t)rows * W3));
+  GENEO_TRY(tmp.get(&P, (size_t)rows * s));
+  GENEO_TRY(tmp.get(&G, (size_t)N * ldg * ldg));
+  GENEO_TRY(tmp.get(&Gp, (size_t)kRS * N * ldg * ldg));
+  GENEO_TRY(tmp.get(&Tm, (size_t)N * ldg * ldg));
+  GENEO_TRY(tmp.get(&nu, (size_t)N * s));
+  GENEO_TRY(tmp.get(&rn, (size_t)N * s));
+  int32_t *sj, *aj, *qj, *rj, *spj, *done, *iters, *notdone;
+  GENEO_TRY(tmp.get(&sj, (size_t)N));
+  GENEO_TRY(tmp.get(&aj, (size_t)N));
+  GENEO_TRY(tmp.get(&qj, (size_t)N));
+  GENEO_TRY(tmp.get(&rj, (size_t)N));
+  GENEO_TRY(tmp.get(&spj, (size_t)N));
+  GENEO_TRY(tmp.get(&done, (size_t)N));
+  GENEO_TRY(tmp.get(&iters, (size_t)N));
+  GENEO_TRY(tmp.get(&notdone, 1));
+  GENEO_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * rows * W3, st));
+  GENEO_CUDA(cudaMemsetAsync(P, 0, sizeof(double) * rows * s, st));
+  GENEO_CUDA(cudaMemsetAsync(nu, 0, sizeof(double) * N * s, st));
+  GENEO_CUDA(cudaMemsetAsync(spj, 0, sizeof(int32_t) * N, st));
+  GENEO_CUDA(cudaMemsetAsync(done, 0, sizeof(int32_t) * N, st));
+  GENEO_CUDA(cudaMemsetAsync(iters, 0, sizeof(int32_t) * N, st));
+  std::vector<int32_t> hs(N);
+  int maxn = 0;
+  for (int j = 0; j < N; ++j) {
+    hs[j] = std::min(s, h->hsub[j].nN);
+    maxn = std::max(maxn, h->hsub[j].nN);
+  }
+  GENEO_CUDA(cudaMemcpyAsync(sj, hs.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+  const dim3 gridR(ceil_div(maxn, kT), N);
+  const size_t dense_smem = sizeof(double) * (2 * kMaxW * (kMaxW + 1) + 6 * kMaxW + kT / 32 + 8);
+  GENEO_CUDA(cudaFuncSetAttribute(k_svqb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  const size_t nn_smem = sizeof(double) * kMaxW * kMaxW;
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+
+  const bool f32 = h->fp32;
+  std::vector<int64_t> hxoff(N);
+  for (int j = 0; j < N; ++j) hxoff[j] = h->hsub[j].offN * (int64_t)W3;
+  int64_t *xoffX, *xoffQ;
+  GENEO_TRY(tmp.get(&xoffX, (size_t)N));
+  GENEO_TRY(tmp.get(&xoffQ, (size_t)N));
+  GENEO_CUDA(cudaMemcpyAsync(xoffX, hxoff.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
+
+  auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
+    if (f32)
+      return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, s * 2,
+                               ncols, skip, st);
+    return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
+                              s * 2, ncols, skip, st);
+  };
+  auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip) -> geneo_status_t {
+    k_gram_part<<<dim3(kRS, N), kT, 0, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
+    k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip);
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  };
+  auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
+                  double beta, const int32_t* skip) -> geneo_status_t {
+    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  };
+  auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip) {
+    if (withK && withB)
+      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
+    else if (withK)
+      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, nullptr, X, YK, YK, skip);
+    else
+      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
+  };
+  // Column references
+  const ColRef Xr = cref(S, W3, 0, nullptr, 0, sj);
+  const ColRef KXr = cref(KS, W3, 0, nullptr, 0, sj);
+  const ColRef BXr = cref(BS, W3, 0, nullptr, 0, sj);
+  const ColRef Qr = cref(S, W3, 0, sj, 0, qj);        // Q after X
+  const ColRef KQr = cref(KS, W3, 0, sj, 0, qj);
+  const ColRef Pr = cref(P, W3 / 3, 0, nullptr, 0, spj);
+  const ColRef Sr = cref(S, W3, 0, nullptr, 0, sj, qj);  // [X, Q]
+  const ColRef BSr = cref(BS, W3, 0, nullptr, 0, sj, qj);
+
+  auto t0 = std::chrono::steady_clock::now();
+  // ---- start block: X = K^{-1} B R, K-orthonormalised, Rayleigh-Ritz
+  k_init_random<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), o.seed);
+  spmm(false, true, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, Xr, nullptr);   // S[:, 0:s] = B R
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_TRY(solveK(xoffX, sj, nullptr));
+  spmm(true, false, Xr, KXr, KXr, nullptr);
+  GENEO_TRY(gram(Xr, KXr, 1, nullptr));
+  k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, nullptr);
+  GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, nullptr));
+  k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, nullptr);
+  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr);
+  spmm(false, true, Xr, BXr, BXr, nullptr);
+  GENEO_TRY(gram(Xr, BXr, 1, nullptr));
+  k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, nullptr);
+  GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, nullptr));
+  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr);
+  GENEO_CUDA(cudaGetLastError());
+
+  // ---- iterations
+  std::vector<int64_t> hq(N);
+  for (int j = 0; j < N; ++j) hq[j] = hxoff[j];  // Q offset depends on s_j: computed per iteration
+  int it = 0;
+  int remaining = N;
+  for (it = 0; it < o.eig_maxit; ++it) {
+    spmm(true, true, Xr, KXr, BXr, done);
+    GENEO_CUDA(cudaMemsetAsync(notdone, 0, sizeof(int32_t), st));
+    k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
+                              spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nev,
+                              o.fixed_nev, it);
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_CUDA(cudaMemcpyAsync(&remaining, notdone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    if (remaining == 0) break;
+    // W = K^{-1} R (active columns start at column s_j)
+    std::vector<int32_t> hsj(N);
+    GENEO_CUDA(cudaMemcpyAsync(hsj.data(), sj, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < N; ++j) hq[j] = hxoff[j] + (int64_t)hsj[j] * h->hsub[j].nN;
+    GENEO_CUDA(cudaMemcpyAsync(xoffQ, hq.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
+    GENEO_TRY(solveK(xoffQ, aj, done));
+    // K-orthogonalise Q against X (twice), SVQB, once more each
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int rep = 0; rep < (pass == 0 ? 2 : 1); ++rep) {
+        spmm(true, false, Qr, KQr, KQr, done);
+        GENEO_TRY(gram(Xr, KQr, 0, done));
+        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
+      }
+      spmm(true, false, Qr, KQr, KQr, done);
+      GENEO_TRY(gram(Qr, KQr, 1, done));
+      k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done);
+      GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
+      k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done);
+      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done);
+      GENEO_CUDA(cudaGetLastError());
+    }
+    // Rayleigh-Ritz on S = [X, Q]
+    spmm(false, true, Sr, BSr, BSr, done);
+    GENEO_TRY(gram(Sr, BSr, 1, done));
+    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done);
+    // P = Q U[s_j:, :], X = S U
+    GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
+    k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done);
+    GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
+    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done);
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_TRY(check_status(h, st));
+  }
+  h->eig_iters = it;
+  h->setup_ms[3] = ms_since(t0);
+  // eigenvalues lambda = sigma + 1/nu (ascending in lambda = descending nu)
+  std::vector<double> hnu((size_t)N * s);
+  std::vector<int32_t> hsj(N);
+  GENEO_CUDA(cudaMemcpyAsync(hnu.data(), nu, sizeof(double) * N * s, cudaMemcpyDeviceToHost, st));
+  GENEO_CUDA(cudaMemcpyAsync(hsj.data(), sj, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+  GENEO_CUDA(cudaStreamSynchronize(st));
+  h->lambda_host.assign((size_t)N * s, INFINITY);
+  for (int j = 0; j < N; ++j) {
+    h->hsub[j].s = hsj[j];
+    for (int i = 0; i < hsj[j]; ++i) {
+      const double v = hnu[(size_t)j * s + i];
+      h->lambda_host[(size_t)j * s + i] = v > 0.0 ? o.sigma + 1.0 / v : INFINITY;
+    }
+  }
+  *X_out = S;  // X occupies columns [0, s_j) of S (buffer width 3s)
+  return check_status(h, st);
+}
+
+}  // namespace geneo

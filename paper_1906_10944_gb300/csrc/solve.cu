@@ -1,0 +1,323 @@
+// Two-level additive Schwarz application and preconditioned CG.
+//
+// Section 3, Definition 2:
+//   z = sum_j R_j^T A_j^{-1} R_j r + R_H^T A_H^{-1} R_H r,
+// Section 4.5: (R_H r)_i = phi_i . r and R_H^T y = sum_i phi_i y_i.
+// Steps on the device:
+//   1. per subdomain: u_j = r[D_j] (restriction) and c_j = Z_j^T r[D_j]
+//   2. batched banded solves L_j L_j^T u_j = u_j
+//   3. banded solve of the coarse system A_H y = c
+//   4. per global dof k (gather form over the subdomains whose D contains k):
+//      z_k = sum_j (u_j[k] + Z_j[k, :] y_j); z_k = r_k on global Dirichlet dofs.
+// PCG (Section 5): x0 = 0, stop when ||r||_2 <= tol ||b||_2; all dot
+// products are two-stage fixed-order reductions, so iterates are bitwise
+// reproducible run to run.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace geneo {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kRedBlocks = 1024;
+
+__global__ void __launch_bounds__(kT)
+k_restrict(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Dlist, const double* __restrict__ r,
+           const double* __restrict__ Z, double* __restrict__ u, double* __restrict__ c) {
+  const int j = blockIdx.x;
+  const SubDesc d = sub[j];
+  __shared__ double red[kT / 32];
+  const int32_t* Dj = Dlist + d.offN;
+  double* uj = u + d.offN;
+  for (int i = threadIdx.x; i < d.nD; i += blockDim.x) uj[i] = r[Dj[i]];
+  const double* zj = Z + d.offZ;
+  for (int k = 0; k < d.m; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < d.nD; i += blockDim.x) s += zj[(int64_t)k * d.nD + i] * r[Dj[i]];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) c[d.offH + k] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kT)
+k_prolong(int64_t n, const uint8_t* __restrict__ dir, const double* __restrict__ r,
+          const int64_t* __restrict__ invD_ptr, const int32_t* __restrict__ invD_sub,
+          const int32_t* __restrict__ invD_loc, const SubDesc* __restrict__ sub,
+          const double* __restrict__ u, const double* __restrict__ Z, const double* __restrict__ y,
+          double* __restrict__ z) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (dir[k]) {
+      z[k] = r[k];
+      continue;
+    }
+    double acc = 0.0;
+    for (int64_t t = invD_ptr[k]; t < invD_ptr[k + 1]; ++t) {
+      const int j = invD_sub[t], i = invD_loc[t];
+      const SubDesc& d = sub[j];
+      double v = u[d.offN + i];
+      const double* zr = Z + d.offZ + i;
+      for (int c = 0; c < d.m; ++c) v += zr[(int64_t)c * d.nD] * y[d.offH + c];
+      acc += v;
+    }
+    z[k] = acc;
+  }
+}
+
+// q = A p with one warp per row; partial sums of p.q per block.
+__global__ void __launch_bounds__(kT)
+k_spmv_dot(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+           const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
+           double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double dsum = 0.0;
+  for (int64_t row = warp; row < n; row += nwarps) {
+    double s = 0.0;
+    for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) s += val[e] * p[col[e]];
+    s = warp_sum(s);
+    if (lane == 0) {
+      q[row] = s;
+      dsum += s * p[row];
+    }
+  }
+  dsum = block_sum(dsum, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = dsum;
+}
+
+__global__ void __launch_bounds__(kT)
+k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// scalars: 0 rz, 1 alpha, 2 beta, 3 rr, 4 pq, 5 bb, 6 flag
+__global__ void k_finish(const double* __restrict__ part, int nb, double* __restrict__ scal, int what,
+                         double* __restrict__ hist_a, double* __restrict__ hist_b, int it) {
+  __shared__ double red[kT / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x != 0) return;
+  if (what == 0) {            // rz0
+    scal[0] = s;
+    if (!(s > 0.0)) scal[6] = 1.0;
+  } else if (what == 1) {     // alpha = rz / pq
+    scal[4] = s;
+    if (!(s > 0.0)) { scal[6] = 1.0; scal[1] = 0.0; }
+    else scal[1] = scal[0] / s;
+    hist_a[it] = scal[1];
+  } else if (what == 2) {     // rr
+    scal[3] = s;
+  } else if (what == 3) {     // beta = rz_new / rz
+    if (!(s > 0.0)) scal[6] = 1.0;
+    scal[2] = scal[0] > 0.0 ? s / scal[0] : 0.0;
+    scal[0] = s;
+    hist_b[it] = scal[2];
+  } else if (what == 4) {     // bb
+    scal[5] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kT)
+k_update_xr(int64_t n, const double* __restrict__ scal, const double* __restrict__ p,
+            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+            double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  const double alpha = scal[1];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_update_p(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
+                           double* __restrict__ p) {
+  const double beta = scal[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// extreme eigenvalues of a symmetric tridiagonal matrix by bisection on the
+// Sturm sequence count
+double sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (q < 0) ++cnt;
+  for (size_t i = 1; i < d.size(); ++i) {
+    const double qq = (q == 0.0) ? 1e-300 : q;
+    q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, int k) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < d.size() ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(d, e, mid) > k) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+double condition_estimate(const std::vector<double>& a, const std::vector<double>& b, int m) {
+  if (m <= 0) return 1.0;
+  std::vector<double> d(m), e(std::max(m - 1, 0));
+  for (int i = 0; i < m; ++i) {
+    d[i] = 1.0 / a[i] + (i > 0 ? b[i - 1] / a[i - 1] : 0.0);
+    if (i < m - 1) e[i] = std::sqrt(std::max(b[i], 0.0)) / a[i];
+  }
+  const double lmin = tridiag_eig(d, e, 0), lmax = tridiag_eig(d, e, m - 1);
+  return lmax / lmin;
+}
+
+}  // namespace
+
+geneo_status_t alloc_solver(geneo_handle_s* h) {
+  DevMem& M = h->mem;
+  const int64_t n = h->n;
+  GENEO_TRY(M.get(&h->u, (size_t)h->sumN));
+  GENEO_TRY(M.get(&h->cH, (size_t)std::max(h->dimH, 1)));
+  GENEO_TRY(M.get(&h->r, (size_t)n));
+  GENEO_TRY(M.get(&h->zv, (size_t)n));
+  GENEO_TRY(M.get(&h->p, (size_t)n));
+  GENEO_TRY(M.get(&h->q, (size_t)n));
+  GENEO_TRY(M.get(&h->red, (size_t)kRedBlocks));
+  GENEO_TRY(M.get(&h->scal, 16));
+  GENEO_TRY(M.get(&h->uoff, (size_t)h->N));
+  std::vector<int64_t> off(h->N);
+  for (int j = 0; j < h->N; ++j) off[j] = h->hsub[j].offN;
+  GENEO_CUDA(cudaMemcpy(h->uoff, off.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice));
+  GENEO_TRY(M.get(&h->xoffH, 1));
+  GENEO_CUDA(cudaMemset(h->xoffH, 0, sizeof(int64_t)));
+  if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
+  h->red_blocks = kRedBlocks;
+  return GENEO_OK;
+}
+
+geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStream_t s) {
+  const int N = h->N;
+  k_restrict<<<N, kT, 0, s>>>(h->dsub, h->Dlist, r, h->Z, h->u, h->cH);
+  GENEO_CUDA(cudaGetLastError());
+  if (h->fp32)
+    GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
+                                nullptr, nullptr, s));
+  else
+    GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
+                                 nullptr, nullptr, s));
+  if (h->dimH > 0)
+    GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr, s));
+  const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
+  k_prolong<<<grid, kT, 0, s>>>(h->n, h->dir, r, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
+                                h->u, h->Z, h->cH, z);
+  GENEO_CUDA(cudaGetLastError());
+  return GENEO_OK;
+}
+
+geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
+                   geneo_solve_info_t* info, cudaStream_t s) {
+  const int64_t n = h->n;
+  const int nb = h->red_blocks;
+  const int gridv = nb;
+  std::vector<double> ha(std::max(maxit, 1) + 1), hb(std::max(maxit, 1) + 1);
+  double *da = nullptr, *db = nullptr;
+  DevMem tmp;
+  GENEO_TRY(tmp.get(&da, ha.size()));
+  GENEO_TRY(tmp.get(&db, hb.size()));
+  // x = 0, r = b, ||b||
+  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GENEO_CUDA(cudaMemsetAsync(h->scal, 0, sizeof(double) * 16, s));
+  k_dot<<<gridv, kT, 0, s>>>(n, b, b, h->red);
+  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 4, da, db, 0);
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(h->hpin[5]);
+  int hist_len = 0;
+  auto push_hist = [&](double v) {
+    if (info && info->resid_hist && hist_len < info->resid_hist_cap) info->resid_hist[hist_len] = v;
+    ++hist_len;
+  };
+  if (bnorm == 0.0) {
+    if (info) {
+      info->iterations = 0;
+      info->converged = 1;
+      info->rel_residual = 0.0;
+      info->kappa_estimate = 1.0;
+      info->resid_hist_len = 0;
+    }
+    return GENEO_OK;
+  }
+  push_hist(1.0);
+  GENEO_TRY(apply_prec(h, h->r, h->zv, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red);
+  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 0, da, db, 0);
+  GENEO_CUDA(cudaGetLastError());
+  int it = 0;
+  double rel = 1.0;
+  bool breakdown = false;
+  while (rel > tol && it < maxit) {
+    k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red);
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 1, da, db, it);
+    k_update_xr<<<gridv, kT, 0, s>>>(n, h->scal, h->p, h->q, x, h->r, h->red);
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 2, da, db, it);
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    ++it;
+    if (h->hpin[6] != 0.0) {
+      breakdown = true;
+      break;
+    }
+    rel = std::sqrt(h->hpin[3]) / bnorm;
+    push_hist(rel);
+    if (rel <= tol) break;
+    GENEO_TRY(apply_prec(h, h->r, h->zv, s));
+    k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red);
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 3, da, db, it - 1);
+    k_update_p<<<gridv, kT, 0, s>>>(n, h->scal, h->zv, h->p);
+    GENEO_CUDA(cudaGetLastError());
+  }
+  GENEO_CUDA(cudaMemcpyAsync(ha.data(), da, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaMemcpyAsync(hb.data(), db, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  const int nalpha = breakdown ? std::max(it - 1, 0) : it;
+  if (info) {
+    info->iterations = it;
+    info->converged = rel <= tol;
+    info->rel_residual = rel;
+    info->kappa_estimate = condition_estimate(ha, hb, nalpha);
+    info->resid_hist_len = std::min(hist_len, info->resid_hist ? info->resid_hist_cap : 0);
+  }
+  GENEO_TRY(check_status(h, s));
+  if (breakdown) return GENEO_ERR_BREAKDOWN;
+  if (rel > tol) return GENEO_ERR_PCG_NOCONV;
+  return GENEO_OK;
+}
+
+}  // namespace geneo

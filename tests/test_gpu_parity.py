@@ -1,0 +1,161 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP64 path): eigenvalues |lambda - lambda*| <= 1e-6 max(|lambda*|,
+1e-3 tau); partition of unity and D_j bit-exact; PCG iterations within +-2 of
+the oracle; final relative residual <= 1e-8; relative error <= 1e-7 against
+a direct solve, or the oracle's own error at the same tolerance times 10 when
+that is larger (the error a residual of 1e-8 implies depends on kappa(A)).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_helpers import compare_setup, gpu_solve, oracle_reference_solution, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _c1(contrast=1e6, seed=0):
+    k = gen.kappa_channels_2d((64, 64), seed=seed, contrast=contrast)
+    return gen.darcy_problem((64, 64), k, (4, 4), 1)
+
+
+def _full_check(prob, tau=0.3, nev=10, fixed=False, form="paper", tol=1e-8):
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(tau=tau, nev_max=nev, fixed_nev=fixed,
+                                                        eig_form=form))
+    sol, torch = run_gpu(prob, tau=tau, nev_max=nev, fixed_nev=int(fixed),
+                         eig_form=0 if form == "paper" else 1)
+    try:
+        q = sol.query()
+        compare_setup(prob, sol, orc, tau, nev, fixed)
+        assert q["dim_coarse"] == orc.dim_H or not fixed
+        x, info = gpu_solve(sol, prob, tol=tol)
+        xo, ito, _, kapo = orc.solve(tol=tol)
+        xs = oracle_reference_solution(prob)
+        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
+        assert info["converged"] and res <= 1.01 * tol
+        assert abs(info["iterations"] - ito) <= 2, (info["iterations"], ito)
+        err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+        err_o = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
+        assert err <= max(1e-7, 10 * err_o), (err, err_o)
+        assert abs(info["kappa_estimate"] - kapo) <= 0.05 * kapo
+        return sol, orc, info
+    finally:
+        sol.close()
+
+
+def test_c1_darcy_2d_high_contrast():
+    """2D Darcy 64x64, 4x4 subdomains, overlap 1, channels at contrast 1e6."""
+    _full_check(_c1())
+
+
+def test_c1_full_eigen_form():
+    _full_check(_c1(), form="full")
+
+
+def test_fixed_nev_mode():
+    _full_check(_c1(contrast=1e4, seed=3), nev=4, fixed=True)
+
+
+def test_one_level_apply_exact():
+    """nev_max = 0: the apply equals sum_j R_j^T A_j^{-1} R_j (one-level method,
+    banded FP64 Cholesky against sparse LU) to rounding."""
+    import torch
+    prob = _c1()
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=0))
+    sol, _ = run_gpu(prob, nev_max=0)
+    try:
+        rng = np.random.default_rng(1)
+        for _ in range(3):
+            r = rng.standard_normal(prob.n)
+            z = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            sol.apply(torch.from_numpy(r).cuda(), z)
+            zg = z.cpu().numpy()
+            zo = orc.apply(r)
+            assert np.linalg.norm(zg - zo) <= 1e-10 * np.linalg.norm(zo)
+    finally:
+        sol.close()
+
+
+def test_two_level_apply_matches_oracle():
+    """Two-level apply vs the oracle's; the coarse vectors come from an
+    iterative eigensolve (residual 1e-6), hence the looser tolerance."""
+    import torch
+    prob = _c1(contrast=1e3, seed=5)
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=6))
+    sol, _ = run_gpu(prob, nev_max=6, eig_tol=1e-9)
+    try:
+        rng = np.random.default_rng(2)
+        r = rng.standard_normal(prob.n)
+        z = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        sol.apply(torch.from_numpy(r).cuda(), z)
+        zo = orc.apply(r)
+        assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-6 * np.linalg.norm(zo)
+    finally:
+        sol.close()
+
+
+def test_darcy_3d_ragged():
+    """3D Darcy 18x14x12 with uneven boxes (3x2x2 parts, overlap 2): several
+    block columns of the banded kernels and ragged last blocks."""
+    nel = (18, 14, 12)
+    kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
+                                  slab_z=(30, 80), slab_thickness=1)
+    prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
+    _full_check(prob, nev=8)
+
+
+def test_elasticity_3d_small():
+    """3D laminate elasticity (3 dofs per node), floating subdomains carry six
+    rigid-body modes."""
+    prob = gen.elasticity_problem((12, 6, 6), (3, 1, 1), 1, layer_thickness=1)
+    _full_check(prob, nev=10)
+
+
+def test_single_subdomain_is_direct_solve():
+    """One subdomain covering the domain: no overlap, B = 0, no coarse space;
+    M^{-1} = A^{-1} and PCG converges in one iteration."""
+    prob = gen.darcy_problem((20, 16), np.ones((16, 20)), (1, 1), 0)
+    sol, _ = run_gpu(prob, nev_max=5)
+    try:
+        assert sol.query()["dim_coarse"] == 0
+        x, info = gpu_solve(sol, prob)
+        assert info["iterations"] <= 1
+        xs = oracle_reference_solution(prob)
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    finally:
+        sol.close()
+
+
+def test_deterministic():
+    """Two setups and solves give bitwise identical results."""
+    prob = _c1()
+    outs = []
+    for _ in range(2):
+        sol, _ = run_gpu(prob, nev_max=10)
+        try:
+            x, info = gpu_solve(sol, prob)
+            lam = np.concatenate([sol.subdomain(j)["lambda"] for j in range(prob.n_sub)])
+            outs.append((x, lam, info["iterations"]))
+        finally:
+            sol.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
+def test_host_memory_path():
+    """The same setup and solve with host arrays (copies inside the calls)."""
+    from paper_1906_10944_gb300 import geneo as G
+    prob = _c1()
+    arrs = G.problem_arrays(prob)
+    p = G.make_problem(arrs, prob.n, prob.n_sub, 4, 1, G.GENEO_MEM_HOST)
+    h = G.geneo_setup(p, G.geneo_default_options())
+    try:
+        x = np.zeros(prob.n)
+        info = G.geneo_pcg_solve(h, np.ascontiguousarray(prob.b), x, tol=1e-8, mem=G.GENEO_MEM_HOST)
+        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
+        assert info["converged"] and res <= 1.01e-8
+    finally:
+        G.geneo_destroy(h)
