@@ -176,6 +176,17 @@ typedef struct {
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse
                                 factor, total */
+  double factor_flops;       /* algorithmic flops of the batched Cholesky of
+                                all A_j and K_j: sum over columns (h_c + 1)^2,
+                                h_c = entries below the diagonal in column c */
+  double factor_event_ms;    /* CUDA-event time of those launches */
+  double eigsolve_flops;     /* algorithmic flops of the K_j^{-1} block solves
+                                of the eigensolver: 2 (2 h_c + 1) per column
+                                and right-hand side */
+  double eigsolve_event_ms;  /* CUDA-event time of those launches */
+  double apply_flops;        /* algorithmic flops of one geneo_apply */
+  double apply_bytes;        /* algorithmic bytes of one geneo_apply: factors,
+                                Z, the coarse factor and the vectors once */
 } geneo_coarse_info_t;
 
 /* Fill *opt with the defaults listed above. */
@@ -247,6 +258,10 @@ geneo_status_t geneo_grow_partition(int64_t n, int64_t n_elem, int32_t elem_ndof
                                     int64_t** sub_dof_ptr, int32_t** sub_dof);
 
 void geneo_free_host(void* p);
+
+/* Number of CUDA kernel launches this library has made in this process
+ * (all handles, all threads). */
+int64_t geneo_launch_count(void);
 
 /* Release all device memory of the handle (NULL is allowed). */
 void geneo_destroy(geneo_handle_t h);

@@ -232,8 +232,16 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->block_size = h->s_block;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
+  info->factor_flops = h->factor_flops;
+  info->factor_event_ms = h->factor_ms;
+  info->eigsolve_flops = h->eig_flops;
+  info->eigsolve_event_ms = h->eig_ms;
+  info->apply_flops = h->apply_flops;
+  info->apply_bytes = h->apply_bytes;
   return GENEO_OK;
 }
+
+int64_t geneo_launch_count(void) { return geneo::launch_count(); }
 
 geneo_status_t geneo_get_subdomain(geneo_handle_t h, int32_t j, int32_t* n_neu, int32_t* n_dir,
                                    int32_t* m, int32_t* s, int32_t* dir_dofs, int64_t dir_cap,

@@ -339,8 +339,8 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   GENEO_CUDA(cudaMemsetAsync(a_out.e_tau, 0, sizeof(int32_t) * p->n_elem, s));
   GENEO_CUDA(cudaMemsetAsync(a_out.cnt_all, 0, sizeof(int32_t) * n, s));
   const int64_t n_sub_elem = h->hsub.back().offE + h->hsub.back().nE;
-  k_count_i32<<<grid_for(n_sub_elem), kT, 0, s>>>(p->sub_elem, n_sub_elem, a_out.e_tau);
-  k_count_i32<<<grid_for(p->n_elem * ke), kT, 0, s>>>(p->elem_dofs, p->n_elem * ke, a_out.cnt_all);
+  k_count_i32<<<grid_for(n_sub_elem), kT, 0, s>>>(p->sub_elem, n_sub_elem, a_out.e_tau); note_launch();
+  k_count_i32<<<grid_for(p->n_elem * ke), kT, 0, s>>>(p->elem_dofs, p->n_elem * ke, a_out.cnt_all); note_launch();
   GENEO_CUDA(cudaGetLastError());
 
   // D_j (Section 3) from element counts inside / outside Omega_j
@@ -349,9 +349,9 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   GENEO_TRY(tmp.get(&cnt_j, (size_t)h->sumN));
   GENEO_TRY(tmp.get(&nD_dev, (size_t)N));
   GENEO_CUDA(cudaMemsetAsync(cnt_j, 0, sizeof(int32_t) * h->sumN, s));
-  k_sub_elem_counts<<<N, kT, 0, s>>>(h->dsub, p->sub_elem, p->elem_dofs, ke, h->Nlist, cnt_j);
+  k_sub_elem_counts<<<N, kT, 0, s>>>(h->dsub, p->sub_elem, p->elem_dofs, ke, h->Nlist, cnt_j); note_launch();
   k_dirichlet_set<<<N, kT, 0, s>>>(h->dsub, h->Nlist, cnt_j, a_out.cnt_all, h->Dlist, h->dpos,
-                                   h->nToD, nD_dev);
+                                   h->nToD, nD_dev); note_launch();
   GENEO_CUDA(cudaGetLastError());
   std::vector<int32_t> nD(N);
   GENEO_CUDA(cudaMemcpyAsync(nD.data(), nD_dev, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
@@ -366,16 +366,16 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   int32_t* cmul = nullptr;
   GENEO_TRY(tmp.get(&cmul, (size_t)n));
   GENEO_CUDA(cudaMemsetAsync(cmul, 0, sizeof(int32_t) * n, s));
-  k_count_D<<<N, kT, 0, s>>>(h->dsub, h->Dlist, cmul);
-  k_check_cover<<<grid_for(n), kT, 0, s>>>(cmul, h->dir, n, h->dstat);
-  k_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, cmul, h->pu);
+  k_count_D<<<N, kT, 0, s>>>(h->dsub, h->Dlist, cmul); note_launch();
+  k_check_cover<<<grid_for(n), kT, 0, s>>>(cmul, h->dir, n, h->dstat); note_launch();
+  k_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, cmul, h->pu); note_launch();
   GENEO_CUDA(cudaGetLastError());
 
   // inverse map dof -> (j, D index), sorted by j
   int64_t* cnt64 = nullptr;
   GENEO_TRY(M.get(&h->invD_ptr, (size_t)n + 1));
   GENEO_TRY(tmp.get(&cnt64, (size_t)n + 1));
-  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(cmul, cnt64, n);
+  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(cmul, cnt64, n); note_launch();
   GENEO_CUDA(cudaMemsetAsync(cnt64 + n, 0, sizeof(int64_t), s));
   int64_t totD = 0;
   GENEO_TRY(exclusive_scan_i64(cnt64, h->invD_ptr, n + 1, &totD, tmp, s));
@@ -385,8 +385,8 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   GENEO_TRY(tmp.get(&cursor, (size_t)n));
   GENEO_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
   k_fill_inv<<<N, kT, 0, s>>>(h->dsub, h->Dlist, nullptr, 1, h->invD_ptr, cursor, h->invD_sub,
-                              h->invD_loc);
-  k_sort_lists<<<grid_for(n), kT, 0, s>>>(h->invD_ptr, n, h->invD_sub, h->invD_loc);
+                              h->invD_loc); note_launch();
+  k_sort_lists<<<grid_for(n), kT, 0, s>>>(h->invD_ptr, n, h->invD_sub, h->invD_loc); note_launch();
   GENEO_CUDA(cudaGetLastError());
   return check_status(h, s);
 }
@@ -406,7 +406,7 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   int32_t* cursor = nullptr;
   GENEO_TRY(tmp.get(&de_cnt, (size_t)n + 1));
   GENEO_TRY(tmp.get(&de_ptr, (size_t)n + 1));
-  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(a_out.cnt_all, de_cnt, n);
+  k_i32_to_i64<<<grid_for(n), kT, 0, s>>>(a_out.cnt_all, de_cnt, n); note_launch();
   GENEO_CUDA(cudaMemsetAsync(de_cnt + n, 0, sizeof(int64_t), s));
   int64_t tot = 0;
   GENEO_TRY(exclusive_scan_i64(de_cnt, de_ptr, n + 1, &tot, tmp, s));
@@ -414,8 +414,8 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_TRY(tmp.get(&cursor, (size_t)n));
   GENEO_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
   k_fill_dof_elem<<<grid_for(p->n_elem * ke), kT, 0, s>>>(p->elem_dofs, p->n_elem, ke, de_ptr,
-                                                          cursor, de);
-  k_sort_lists<<<grid_for(n), kT, 0, s>>>(de_ptr, n, de, nullptr);
+                                                          cursor, de); note_launch();
+  k_sort_lists<<<grid_for(n), kT, 0, s>>>(de_ptr, n, de, nullptr); note_launch();
   GENEO_CUDA(cudaGetLastError());
 
   // local CSR pattern over N-rows
@@ -424,7 +424,7 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_TRY(tmp.get(&out.lrow, (size_t)h->sumN + 1));
   GENEO_CUDA(cudaMemsetAsync(lcnt + h->sumN, 0, sizeof(int64_t), s));
   k_local_csr<0><<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->rowptr, h->col, h->val, lcnt, nullptr,
-                                  nullptr, nullptr, nullptr);
+                                  nullptr, nullptr, nullptr); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_TRY(exclusive_scan_i64(lcnt, out.lrow, h->sumN + 1, &out.lnnz, tmp, s));
   int32_t *wK = nullptr, *wA = nullptr;
@@ -436,8 +436,8 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_CUDA(cudaMemsetAsync(wK, 0, sizeof(int32_t) * N, s));
   GENEO_CUDA(cudaMemsetAsync(wA, 0, sizeof(int32_t) * N, s));
   k_local_csr<1><<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->rowptr, h->col, h->val, nullptr, out.lrow,
-                                  out.lcol, lA, wK);
-  k_band_width_A<<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, wA);
+                                  out.lcol, lA, wK); note_launch();
+  k_band_width_A<<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, wA); note_launch();
   GENEO_CUDA(cudaGetLastError());
   std::vector<int32_t> hwK(N), hwA(N);
   GENEO_CUDA(cudaMemcpyAsync(hwK.data(), wK, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
@@ -463,9 +463,9 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_TRY(tmp.get(&out.lK, (size_t)out.lnnz));
   GENEO_TRY(tmp.get(&out.lB, (size_t)out.lnnz));
   k_assemble<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, de_ptr, de, p->elem_dofs,
-                              p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB);
+                              p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB); note_launch();
   k_pencil<<<N, kT, 0, s>>>(h->dsub, h->pu, out.lrow, out.lcol, out.lK, out.lB, h->opt.sigma,
-                            h->opt.eig_form == GENEO_EIG_FULL);
+                            h->opt.eig_form == GENEO_EIG_FULL); note_launch();
   GENEO_CUDA(cudaGetLastError());
 
   // band storage, descriptors
@@ -485,13 +485,13 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_CUDA(cudaMemcpyAsync(out.dbandK, bk.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandA, ba.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
   if (h->fp32) {
-    k_band_fill_K<float><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (float*)out.bandK);
+    k_band_fill_K<float><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (float*)out.bandK); note_launch();
     k_band_fill_A<float><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
-                                          (float*)h->bandA);
+                                          (float*)h->bandA); note_launch();
   } else {
-    k_band_fill_K<double><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (double*)out.bandK);
+    k_band_fill_K<double><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (double*)out.bandK); note_launch();
     k_band_fill_A<double><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
-                                           (double*)h->bandA);
+                                           (double*)h->bandA); note_launch();
   }
   GENEO_CUDA(cudaGetLastError());
   GENEO_TRY(check_status(h, s));
@@ -499,6 +499,8 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
 
   // batched Cholesky of A_j and K_j (Sections 3 and 4.4)
   auto t1 = std::chrono::steady_clock::now();
+  EventTimer ev;
+  ev.start(s);
   if (h->fp32) {
     GENEO_TRY(band_potrf<float>((float*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
     GENEO_TRY(band_potrf<float>((float*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
@@ -506,6 +508,11 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     GENEO_TRY(band_potrf<double>((double*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
     GENEO_TRY(band_potrf<double>((double*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
   }
+  ev.stop();
+  h->factor_ms = ev.ms;
+  h->factor_flops = 0.0;
+  for (const SubDesc& d : h->hsub)
+    h->factor_flops += band_factor_flops(d.nD, d.wA) + band_factor_flops(d.nN, d.wK);
   GENEO_TRY(check_status(h, s));
   *ms_factor = ms_since(t1);
   return GENEO_OK;

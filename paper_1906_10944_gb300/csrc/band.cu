@@ -304,10 +304,10 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
     auto kern = k_band_potrf<T, kNB, true>;
     GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(diag + panel)));
-    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, max_w, st);
+    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, max_w, st); note_launch();
   } else {
     auto kern = k_band_potrf<T, kNB, false>;
-    kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st);
+    kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st); note_launch();
   }
   GENEO_CUDA(cudaGetLastError());
   return GENEO_OK;
@@ -325,7 +325,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
   GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int c0 = 0; c0 < nrhs; c0 += kSolveKmax) {
     const int kc = std::min(kSolveKmax, nrhs - c0);
-    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev);
+    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev); note_launch();
     GENEO_CUDA(cudaGetLastError());
   }
   return GENEO_OK;

@@ -213,7 +213,7 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
     *ms_basis = ms_since(t0);
     return GENEO_OK;
   }
-  k_basis<<<N, kT, 0, s>>>(h->dsub, X, 3 * h->s_block, h->pu, h->dpos, h->Z);
+  k_basis<<<N, kT, 0, s>>>(h->dsub, X, 3 * h->s_block, h->pu, h->dpos, h->Z); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_TRY(check_status(h, s));
   *ms_basis = ms_since(t0);
@@ -222,11 +222,11 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   double* Y = nullptr;
   GENEO_TRY(tmp.get(&Y, (size_t)yoff));
   k_AZ<<<dim3(ceil_div(maxn, kT), N), kT, 0, s>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lA, h->nToD,
-                                                   h->Z, Y);
+                                                   h->Z, Y); note_launch();
   uint8_t* mark = nullptr;
   GENEO_TRY(tmp.get(&mark, (size_t)N * N));
   GENEO_CUDA(cudaMemsetAsync(mark, 0, (size_t)N * N, s));
-  k_pairs<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->invD_ptr, h->invD_sub, N, mark);
+  k_pairs<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->invD_ptr, h->invD_sub, N, mark); note_launch();
   GENEO_CUDA(cudaGetLastError());
   std::vector<uint8_t> hmark((size_t)N * N);
   GENEO_CUDA(cudaMemcpyAsync(hmark.data(), mark, (size_t)N * N, cudaMemcpyDeviceToHost, s));
@@ -250,7 +250,7 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   GENEO_TRY(tmp.get(&dpairs, pairs.size()));
   GENEO_CUDA(cudaMemcpyAsync(dpairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, s));
   k_coarse_block<<<(unsigned)pairs.size(), kT, 0, s>>>(h->dsub, dpairs, h->Nlist, h->invD_ptr,
-                                                       h->invD_sub, h->invD_loc, h->Z, Y, h->bandH, wH);
+                                                       h->invD_sub, h->invD_loc, h->Z, Y, h->bandH, wH); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_TRY(check_status(h, s));
   *ms_matrix = ms_since(t1);

@@ -45,6 +45,32 @@ __device__ __forceinline__ void record_error(DevStatus* st, int code, int where,
   } while (0)
 
 void set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// process-wide count of kernel launches made by this library
+void note_launch();
+int64_t launch_count();
+
+// Accumulates CUDA-event time of selected launches on one stream.
+struct EventTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double ms = 0.0;
+  cudaStream_t s = 0;
+  void start(cudaStream_t st) {
+    s = st;
+    if (!a) { cudaEventCreate(&a); cudaEventCreate(&b); }
+    cudaEventRecord(a, s);
+  }
+  void stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    ms += t;
+  }
+  ~EventTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
 const std::string& last_cuda_error();
 
 // --------------------------------------------------------------------------
@@ -124,6 +150,29 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Algorithmic work of the banded kernels for an n x n band of half width w:
+// column c has h_c = min(w, n-1-c) entries below the diagonal.
+// Cholesky: 1 sqrt, h_c divisions, h_c (h_c + 1)/2 fused multiply-adds of
+// the trailing update -> sum_c (h_c + 1)^2 flops.
+inline double band_factor_flops(double n, double w) {
+  if (n <= 0) return 0.0;
+  if (w >= n) w = n - 1;
+  return (n - w) * (w + 1) * (w + 1) + w * (w + 1) * (2 * w + 1) / 6.0;
+}
+// Forward plus backward substitution, one right-hand side: 2 sum_c (2 h_c + 1).
+inline double band_solve_flops(double n, double w) {
+  if (n <= 0) return 0.0;
+  if (w >= n) w = n - 1;
+  const double sum_h = (n - w) * w + w * (w - 1) / 2.0;
+  return 2.0 * (2.0 * sum_h + n);
+}
+// Stored entries of the band, sum_c (h_c + 1).
+inline double band_entries(double n, double w) {
+  if (n <= 0) return 0.0;
+  if (w >= n) w = n - 1;
+  return (n - w) * (w + 1) + w * (w + 1) / 2.0;
+}
 
 // --------------------------------------------------------------------------
 // Simple owning device buffer.

@@ -59,6 +59,11 @@ struct geneo_handle_s {
   double* hpin = nullptr;          // pinned host scalars
   int red_blocks = 0;
 
+  double factor_flops = 0, factor_ms = 0, eig_flops = 0, eig_ms = 0;
+  double apply_flops = 0, apply_bytes = 0;
+  double* hist = nullptr;          // PCG alpha/beta history (2 * hist_cap)
+  int hist_cap = 0;
+
   geneo::DevStatus* dstat = nullptr;
   geneo::DevStatus hstat{};
   double setup_ms[8] = {0};

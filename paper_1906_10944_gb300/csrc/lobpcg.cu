@@ -605,33 +605,54 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_TRY(tmp.get(&xoffQ, (size_t)N));
   GENEO_CUDA(cudaMemcpyAsync(xoffX, hxoff.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
 
-  auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
+  EventTimer evs;
+  std::vector<double> kflops(N);
+  for (int j = 0; j < N; ++j) kflops[j] = band_solve_flops(h->hsub[j].nN, h->hsub[j].wK);
+  h->eig_flops = 0.0;
+  auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
     if (f32)
       return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, s * 2,
                                ncols, skip, st);
     return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
                               s * 2, ncols, skip, st);
   };
+  // timed with CUDA events; flops from the per-subdomain column counts
+  auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
+    std::vector<int32_t> hc(N), hk(N, 0);
+    GENEO_CUDA(cudaMemcpyAsync(hc.data(), ncols, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    if (skip) GENEO_CUDA(cudaMemcpyAsync(hk.data(), skip, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < N; ++j)
+      if (!hk[j]) h->eig_flops += kflops[j] * hc[j];
+    evs.start(st);
+    geneo_status_t r = solveK_raw(xoff, ncols, skip);
+    evs.stop();
+    h->eig_ms = evs.ms;
+    return r;
+  };
   auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip) -> geneo_status_t {
-    k_gram_part<<<dim3(kRS, N), kT, 0, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
-    k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip);
+    k_gram_part<<<dim3(kRS, N), kT, 0, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
   auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
                   double beta, const int32_t* skip) -> geneo_status_t {
-    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
   auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip) {
-    if (withK && withB)
+    if (withK && withB) {
       k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
-    else if (withK)
+    } else if (withK) {
       k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, nullptr, X, YK, YK, skip);
-    else
+    } else {
       k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
+    }
+    note_launch();
   };
+
   // Column references
   const ColRef Xr = cref(S, W3, 0, nullptr, 0, sj);
   const ColRef KXr = cref(KS, W3, 0, nullptr, 0, sj);
@@ -644,21 +665,21 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
 
   auto t0 = std::chrono::steady_clock::now();
   // ---- start block: X = K^{-1} B R, K-orthonormalised, Rayleigh-Ritz
-  k_init_random<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), o.seed);
+  k_init_random<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), o.seed); note_launch();
   spmm(false, true, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, Xr, nullptr);   // S[:, 0:s] = B R
   GENEO_CUDA(cudaGetLastError());
   GENEO_TRY(solveK(xoffX, sj, nullptr));
   spmm(true, false, Xr, KXr, KXr, nullptr);
   GENEO_TRY(gram(Xr, KXr, 1, nullptr));
-  k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, nullptr);
+  k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, nullptr); note_launch();
   GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, nullptr));
-  k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, nullptr);
-  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr);
+  k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, nullptr); note_launch();
+  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr); note_launch();
   spmm(false, true, Xr, BXr, BXr, nullptr);
   GENEO_TRY(gram(Xr, BXr, 1, nullptr));
-  k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, nullptr);
+  k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, nullptr); note_launch();
   GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, nullptr));
-  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr);
+  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr); note_launch();
   GENEO_CUDA(cudaGetLastError());
 
   // ---- iterations
@@ -671,7 +692,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaMemsetAsync(notdone, 0, sizeof(int32_t), st));
     k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
                               spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nev,
-                              o.fixed_nev, it);
+                              o.fixed_nev, it); note_launch();
     GENEO_CUDA(cudaGetLastError());
     GENEO_CUDA(cudaMemcpyAsync(&remaining, notdone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     GENEO_CUDA(cudaStreamSynchronize(st));
@@ -692,21 +713,21 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       }
       spmm(true, false, Qr, KQr, KQr, done);
       GENEO_TRY(gram(Qr, KQr, 1, done));
-      k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done);
+      k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch();
       GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
-      k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done);
-      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done);
+      k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
+      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
       GENEO_CUDA(cudaGetLastError());
     }
     // Rayleigh-Ritz on S = [X, Q]
     spmm(false, true, Sr, BSr, BSr, done);
     GENEO_TRY(gram(Sr, BSr, 1, done));
-    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done);
+    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch();
     // P = Q U[s_j:, :], X = S U
     GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
-    k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done);
+    k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
     GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
-    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done);
+    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
     GENEO_CUDA(cudaGetLastError());
     GENEO_TRY(check_status(h, st));
   }

@@ -215,12 +215,25 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   GENEO_CUDA(cudaMemset(h->xoffH, 0, sizeof(int64_t)));
   if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
   h->red_blocks = kRedBlocks;
+  // algorithmic work of one apply
+  const double esz = h->fp32 ? 4.0 : 8.0;
+  double fl = 0.0, by = 0.0, sumD = 0.0;
+  for (const SubDesc& d : h->hsub) {
+    fl += band_solve_flops(d.nD, d.wA) + 4.0 * (double)d.nD * d.m;
+    by += 2.0 * esz * band_entries(d.nD, d.wA) + 2.0 * 8.0 * (double)d.nD * d.m;
+    sumD += d.nD;
+  }
+  fl += band_solve_flops(h->dimH, h->wH);
+  by += 2.0 * 8.0 * band_entries(h->dimH, h->wH);
+  by += 8.0 * (2.0 * (double)n + 3.0 * sumD);  // r, z, gathered r, u written and read
+  h->apply_flops = fl;
+  h->apply_bytes = by;
   return GENEO_OK;
 }
 
 geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStream_t s) {
   const int N = h->N;
-  k_restrict<<<N, kT, 0, s>>>(h->dsub, h->Dlist, r, h->Z, h->u, h->cH);
+  k_restrict<<<N, kT, 0, s>>>(h->dsub, h->Dlist, r, h->Z, h->u, h->cH); note_launch();
   GENEO_CUDA(cudaGetLastError());
   if (h->fp32)
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
@@ -232,7 +245,7 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
     GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr, s));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
   k_prolong<<<grid, kT, 0, s>>>(h->n, h->dir, r, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
-                                h->u, h->Z, h->cH, z);
+                                h->u, h->Z, h->cH, z); note_launch();
   GENEO_CUDA(cudaGetLastError());
   return GENEO_OK;
 }
@@ -243,16 +256,20 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
   const int nb = h->red_blocks;
   const int gridv = nb;
   std::vector<double> ha(std::max(maxit, 1) + 1), hb(std::max(maxit, 1) + 1);
-  double *da = nullptr, *db = nullptr;
-  DevMem tmp;
-  GENEO_TRY(tmp.get(&da, ha.size()));
-  GENEO_TRY(tmp.get(&db, hb.size()));
+  if (h->hist_cap < (int)ha.size()) {
+    if (h->hist) h->mem.release(h->hist);
+    h->hist = nullptr;
+    GENEO_TRY(h->mem.get(&h->hist, 2 * ha.size()));
+    h->hist_cap = (int)ha.size();
+  }
+  double* da = h->hist;
+  double* db = h->hist + h->hist_cap;
   // x = 0, r = b, ||b||
   GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   GENEO_CUDA(cudaMemcpyAsync(h->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GENEO_CUDA(cudaMemsetAsync(h->scal, 0, sizeof(double) * 16, s));
-  k_dot<<<gridv, kT, 0, s>>>(n, b, b, h->red);
-  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 4, da, db, 0);
+  k_dot<<<gridv, kT, 0, s>>>(n, b, b, h->red); note_launch();
+  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 4, da, db, 0); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
   GENEO_CUDA(cudaStreamSynchronize(s));
@@ -275,17 +292,17 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
   push_hist(1.0);
   GENEO_TRY(apply_prec(h, h->r, h->zv, s));
   GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red);
-  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 0, da, db, 0);
+  k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red); note_launch();
+  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 0, da, db, 0); note_launch();
   GENEO_CUDA(cudaGetLastError());
   int it = 0;
   double rel = 1.0;
   bool breakdown = false;
   while (rel > tol && it < maxit) {
-    k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red);
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 1, da, db, it);
-    k_update_xr<<<gridv, kT, 0, s>>>(n, h->scal, h->p, h->q, x, h->r, h->red);
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 2, da, db, it);
+    k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 1, da, db, it); note_launch();
+    k_update_xr<<<gridv, kT, 0, s>>>(n, h->scal, h->p, h->q, x, h->r, h->red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 2, da, db, it); note_launch();
     GENEO_CUDA(cudaGetLastError());
     GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
     GENEO_CUDA(cudaStreamSynchronize(s));
@@ -298,9 +315,9 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
     push_hist(rel);
     if (rel <= tol) break;
     GENEO_TRY(apply_prec(h, h->r, h->zv, s));
-    k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red);
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 3, da, db, it - 1);
-    k_update_p<<<gridv, kT, 0, s>>>(n, h->scal, h->zv, h->p);
+    k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 3, da, db, it - 1); note_launch();
+    k_update_p<<<gridv, kT, 0, s>>>(n, h->scal, h->zv, h->p); note_launch();
     GENEO_CUDA(cudaGetLastError());
   }
   GENEO_CUDA(cudaMemcpyAsync(ha.data(), da, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));

@@ -1,9 +1,14 @@
 // Device memory bookkeeping, error strings and a device-wide exclusive scan.
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
 
 namespace geneo {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(); }
 
 static thread_local std::string g_last_cuda_error;
 
@@ -113,14 +118,14 @@ geneo_status_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, in
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   int64_t* sums = nullptr;
   GENEO_TRY(tmp.get(&sums, (size_t)tiles + 1));
-  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, sums);
+  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, sums); note_launch();
   GENEO_CUDA(cudaGetLastError());
   if (tiles > 1) {
     int64_t* offs = nullptr;
     GENEO_TRY(tmp.get(&offs, (size_t)tiles + 1));
     int64_t t2 = 0;
     GENEO_TRY(exclusive_scan_i64(sums, offs, tiles, &t2, tmp, st));
-    k_add_offsets<<<(unsigned)tiles, kScanThreads, 0, st>>>(out, n, offs);
+    k_add_offsets<<<(unsigned)tiles, kScanThreads, 0, st>>>(out, n, offs); note_launch();
     GENEO_CUDA(cudaGetLastError());
     if (total) *total = t2;
   } else if (total) {

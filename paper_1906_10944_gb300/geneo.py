@@ -32,7 +32,7 @@ STATUS = {
 EXPORTED = [
     "geneo_default_options", "geneo_setup", "geneo_apply", "geneo_pcg_solve", "geneo_query",
     "geneo_get_subdomain", "geneo_grow_partition", "geneo_free_host", "geneo_destroy",
-    "geneo_status_str", "geneo_last_error",
+    "geneo_status_str", "geneo_last_error", "geneo_launch_count",
 ]
 
 
@@ -67,7 +67,9 @@ class geneo_coarse_info_t(C.Structure):
     _fields_ = [
         ("n_sub", C.c_int32), ("dim_coarse", C.c_int32), ("coarse_bandwidth", C.c_int32),
         ("eig_iterations", C.c_int32), ("block_size", C.c_int32), ("device_bytes", C.c_int64),
-        ("setup_ms", C.c_double * 8),
+        ("setup_ms", C.c_double * 8), ("factor_flops", C.c_double), ("factor_event_ms", C.c_double),
+        ("eigsolve_flops", C.c_double), ("eigsolve_event_ms", C.c_double),
+        ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
     ]
 
 
@@ -113,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     lib.geneo_status_str.restype = C.c_char_p
     lib.geneo_last_error.argtypes = [VP, P(I32), P(I32), P(I64)]
     lib.geneo_last_error.restype = I32
+    lib.geneo_launch_count.argtypes = []
+    lib.geneo_launch_count.restype = I64
     _lib = lib
     return lib
 
@@ -190,7 +194,10 @@ def geneo_query(h):
     _check(lib.geneo_query(h, C.byref(q)), "geneo_query")
     return {"n_sub": q.n_sub, "dim_coarse": q.dim_coarse, "coarse_bandwidth": q.coarse_bandwidth,
             "eig_iterations": q.eig_iterations, "block_size": q.block_size,
-            "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms)}
+            "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms),
+            "factor_flops": q.factor_flops, "factor_event_ms": q.factor_event_ms,
+            "eigsolve_flops": q.eigsolve_flops, "eigsolve_event_ms": q.eigsolve_event_ms,
+            "apply_flops": q.apply_flops, "apply_bytes": q.apply_bytes}
 
 
 def geneo_get_subdomain(h, j):
@@ -237,6 +244,10 @@ def geneo_destroy(h):
 
 def geneo_status_str(code):
     return load_library().geneo_status_str(code).decode()
+
+
+def geneo_launch_count():
+    return int(load_library().geneo_launch_count())
 
 
 def geneo_last_error(h):
