@@ -222,6 +222,32 @@ geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int
                                double tol, int32_t maxit, int32_t mem,
                                geneo_solve_info_t* info, void* stream);
 
+/*
+ * The same PCG solve as geneo_pcg_solve (one right-hand side, device arrays)
+ * for callers that must not allocate memory during the solve: code that runs
+ * under a fixed device-memory budget, inside a memory pool's own callbacks,
+ * or in a request loop where a cudaMalloc would stall the device or fail.
+ * The paper has no counterpart; it is a property of this library's API.
+ *
+ * The call allocates nothing (no cudaMalloc or cudaFree, no host heap): the
+ * reduction partials, the PCG scalars and the alpha/beta history used for the
+ * condition estimate live in one fixed device array inside the library
+ * (73,856 bytes on every device that loads the library, held until the
+ * process exits), and the vectors come from the handle, allocated by
+ * geneo_setup.  Limit: maxit <= 4095; larger values return GENEO_ERR_ARG.
+ * The first call on a device looks up that array's device address (with the
+ * handle's device current) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents; the scalars are cleared at the start of every call.  Calls whose
+ * work overlaps on the GPU (on different streams, or on different handles
+ * of the same device) race and must not be issued.  b_dev and x_dev are
+ * device arrays of n doubles; info as in geneo_pcg_solve.  Synchronises
+ * `stream`.
+ */
+geneo_status_t geneo_pcg_solve_noalloc(geneo_handle_t h, const double* b_dev, double* x_dev,
+                                       double tol, int32_t maxit, geneo_solve_info_t* info,
+                                       void* stream);
+
 /* Setup summary; synchronises the handle's work. */
 geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info);
 

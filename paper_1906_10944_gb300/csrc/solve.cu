@@ -14,6 +14,7 @@
 // reproducible run to run.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "handle.cuh"
@@ -337,4 +338,175 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
   return GENEO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// PCG that allocates nothing (geneo_pcg_solve_noalloc).
+//
+// The reduction partials, the PCG scalars and the alpha/beta history live in
+// one file-scope device array of fixed size instead of handle or call
+// allocations.  Every device that loads the library holds its own copy until
+// the process exits.  Host code never uses the array's name as an address:
+// the device address is obtained once per device with cudaGetSymbolAddress
+// (with that device current) and cached.  All calls share the array, so calls
+// whose work overlaps on the GPU race with each other.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxIt = 4095;                      // largest maxit accepted
+constexpr int kNoAllocScalars = 16;
+constexpr int kNoAllocDoubles = kRedBlocks + kNoAllocScalars + 2 * (kNoAllocMaxIt + 1);
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_pcg_scratch[kNoAllocDoubles];  // 73,856 bytes
+
+std::mutex g_scratch_mu;
+double* g_scratch_addr[kMaxDevices] = {};
+
+geneo_status_t pcg_scratch(double** out) {
+  int dev = 0;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return GENEO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    GENEO_CUDA(cudaGetSymbolAddress(&p, g_pcg_scratch));
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return GENEO_OK;
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal matrix with caller storage.
+double condition_estimate_fixed(const double* a, const double* b, int m, double* d, double* e) {
+  if (m <= 0) return 1.0;
+  for (int i = 0; i < m; ++i) {
+    d[i] = 1.0 / a[i] + (i > 0 ? b[i - 1] / a[i - 1] : 0.0);
+    if (i < m - 1) e[i] = std::sqrt(std::max(b[i], 0.0)) / a[i];
+  }
+  auto count = [&](double x) {
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      q = d[i] - x - e[i - 1] * e[i - 1] / (q == 0.0 ? 1e-300 : q);
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  double ext[2];
+  for (int which = 0; which < 2; ++which) {
+    const int k = which == 0 ? 0 : m - 1;
+    double l = lo, u = hi;
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (count(mid) > k) u = mid; else l = mid;
+    }
+    ext[which] = 0.5 * (l + u);
+  }
+  return ext[1] / ext[0];
+}
+
+thread_local double t_hist[2][kNoAllocMaxIt + 1];
+thread_local double t_tri[2][kNoAllocMaxIt + 1];
+
+}  // namespace
+
+geneo_status_t pcg_noalloc(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
+                           geneo_solve_info_t* info, cudaStream_t s) {
+  if (maxit > kNoAllocMaxIt) return GENEO_ERR_ARG;
+  double* scr = nullptr;
+  GENEO_TRY(pcg_scratch(&scr));
+  const int64_t n = h->n;
+  const int nb = kRedBlocks;
+  double* red = scr;
+  double* scal = scr + kRedBlocks;
+  double* da = scal + kNoAllocScalars;
+  double* db = da + (kNoAllocMaxIt + 1);
+  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GENEO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kNoAllocScalars, s));
+  k_dot<<<nb, kT, 0, s>>>(n, b, b, red); note_launch();
+  k_finish<<<1, kT, 0, s>>>(red, nb, scal, 4, da, db, 0); note_launch();
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(h->hpin[5]);
+  int hist_len = 0;
+  auto push_hist = [&](double v) {
+    if (info && info->resid_hist && hist_len < info->resid_hist_cap) info->resid_hist[hist_len] = v;
+    ++hist_len;
+  };
+  if (bnorm == 0.0) {
+    if (info) {
+      info->iterations = 0;
+      info->converged = 1;
+      info->rel_residual = 0.0;
+      info->kappa_estimate = 1.0;
+      info->resid_hist_len = 0;
+    }
+    return GENEO_OK;
+  }
+  push_hist(1.0);
+  GENEO_TRY(apply_prec(h, h->r, h->zv, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
+  k_finish<<<1, kT, 0, s>>>(red, nb, scal, 0, da, db, 0); note_launch();
+  GENEO_CUDA(cudaGetLastError());
+  int it = 0;
+  double rel = 1.0;
+  bool breakdown = false;
+  while (rel > tol && it < maxit) {
+    k_spmv_dot<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 1, da, db, it); note_launch();
+    k_update_xr<<<nb, kT, 0, s>>>(n, scal, h->p, h->q, x, h->r, red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 2, da, db, it); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    ++it;
+    if (h->hpin[6] != 0.0) {
+      breakdown = true;
+      break;
+    }
+    rel = std::sqrt(h->hpin[3]) / bnorm;
+    push_hist(rel);
+    if (rel <= tol) break;
+    GENEO_TRY(apply_prec(h, h->r, h->zv, s));
+    k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 3, da, db, it - 1); note_launch();
+    k_update_p<<<nb, kT, 0, s>>>(n, scal, h->zv, h->p); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+  }
+  const int nalpha = breakdown ? std::max(it - 1, 0) : it;
+  if (nalpha > 0) {
+    GENEO_CUDA(cudaMemcpyAsync(t_hist[0], da, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaMemcpyAsync(t_hist[1], db, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
+  }
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iterations = it;
+    info->converged = rel <= tol;
+    info->rel_residual = rel;
+    info->kappa_estimate = condition_estimate_fixed(t_hist[0], t_hist[1], nalpha, t_tri[0], t_tri[1]);
+    info->resid_hist_len = std::min(hist_len, info->resid_hist ? info->resid_hist_cap : 0);
+  }
+  GENEO_TRY(check_status(h, s));
+  if (breakdown) return GENEO_ERR_BREAKDOWN;
+  if (rel > tol) return GENEO_ERR_PCG_NOCONV;
+  return GENEO_OK;
+}
+
 }  // namespace geneo
+
+extern "C" geneo_status_t geneo_pcg_solve_noalloc(geneo_handle_t h, const double* b_dev, double* x_dev,
+                                                  double tol, int32_t maxit,
+                                                  geneo_solve_info_t* info, void* stream) {
+  if (!h || !b_dev || !x_dev || !(tol > 0.0) || maxit < 0 || maxit > geneo::kNoAllocMaxIt)
+    return GENEO_ERR_ARG;
+  return geneo::pcg_noalloc(h, b_dev, x_dev, tol, maxit, info, (cudaStream_t)stream);
+}

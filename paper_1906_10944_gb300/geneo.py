@@ -32,7 +32,7 @@ STATUS = {
 EXPORTED = [
     "geneo_default_options", "geneo_setup", "geneo_apply", "geneo_pcg_solve", "geneo_query",
     "geneo_get_subdomain", "geneo_grow_partition", "geneo_free_host", "geneo_destroy",
-    "geneo_status_str", "geneo_last_error", "geneo_launch_count",
+    "geneo_status_str", "geneo_last_error", "geneo_launch_count", "geneo_pcg_solve_noalloc",
 ]
 
 
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     lib.geneo_status_str.restype = C.c_char_p
     lib.geneo_last_error.argtypes = [VP, P(I32), P(I32), P(I64)]
     lib.geneo_last_error.restype = I32
+    lib.geneo_pcg_solve_noalloc.argtypes = [VP, VP, VP, D, I32, P(geneo_solve_info_t), VP]
+    lib.geneo_pcg_solve_noalloc.restype = I32
     lib.geneo_launch_count.argtypes = []
     lib.geneo_launch_count.restype = I64
     _lib = lib
@@ -186,6 +188,18 @@ def geneo_pcg_solve(h, b, x, nrhs=1, tol=1e-8, maxit=1000, mem=GENEO_MEM_DEVICE,
     if hist is not None:
         out["resid_hist"] = np.array(hist[:min(info.resid_hist_len, hist_cap)])
     return out
+
+
+def geneo_pcg_solve_noalloc(h, b, x, tol=1e-8, maxit=1000, stream=None, raise_on_error=True):
+    """PCG without any allocation inside the call (device arrays only)."""
+    lib = load_library()
+    info = geneo_solve_info_t()
+    code = lib.geneo_pcg_solve_noalloc(h, _ptr(b), _ptr(x), tol, maxit, C.byref(info),
+                                       C.c_void_p(_stream(stream)))
+    if raise_on_error:
+        _check(code, "geneo_pcg_solve_noalloc")
+    return {"status": code, "iterations": info.iterations, "converged": bool(info.converged),
+            "rel_residual": info.rel_residual, "kappa_estimate": info.kappa_estimate}
 
 
 def geneo_query(h):
