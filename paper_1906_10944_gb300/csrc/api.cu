@@ -169,6 +169,13 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   const int guard = o.guard >= 0 ? o.guard : std::min(5, o.nev_max);
   h->s_block = std::min(o.nev_max + guard, 34);
   h->stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    geneo_destroy(h);
+    return GENEO_ERR_CUDA;
+  }
   geneo_status_t st = setup_impl(h, prob, h->stream);
   if (st != GENEO_OK) {
     cudaStreamSynchronize(h->stream);
@@ -267,7 +274,11 @@ geneo_status_t geneo_get_subdomain(geneo_handle_t h, int32_t j, int32_t* n_neu, 
 
 void geneo_destroy(geneo_handle_t h) {
   if (!h) return;
+  if (h->aux) cudaStreamSynchronize(h->aux);
   h->mem.free_all();
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->aux) cudaStreamDestroy(h->aux);
   if (h->hpin) cudaFreeHost(h->hpin);
   delete h;
 }

@@ -285,12 +285,12 @@ __global__ void k_band_fill_K(const SubDesc* __restrict__ sub, const int64_t* __
                               const int32_t* __restrict__ lcol, const double* __restrict__ lK,
                               T* __restrict__ band) {
   const SubDesc d = sub[blockIdx.x];
-  const int64_t ld = d.wK + 1;
+  const int64_t ld = band_ld(d.wK);
   T* L = band + d.bandK;
   for (int a = threadIdx.x; a < d.nN; a += blockDim.x)
     for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
       const int b = lcol[e];
-      if (b <= a) L[(int64_t)b * ld + (a - b)] = (T)lK[e];
+      if (b <= a) L[(int64_t)a * ld + (b - a + d.wK)] = (T)lK[e];
     }
 }
 
@@ -300,13 +300,13 @@ __global__ void k_band_fill_A(const SubDesc* __restrict__ sub, const int32_t* __
                               const int32_t* __restrict__ lcol, const double* __restrict__ lA,
                               T* __restrict__ band) {
   const SubDesc d = sub[blockIdx.x];
-  const int64_t ld = d.wA + 1;
+  const int64_t ld = band_ld(d.wA);
   T* L = band + d.bandA;
   for (int i = threadIdx.x; i < d.nD; i += blockDim.x) {
     const int a = dpos[d.offN + i];
     for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
       const int i2 = nToD[d.offN + lcol[e]];
-      if (i2 >= 0 && i2 <= i) L[(int64_t)i2 * ld + (i - i2)] = (T)lA[e];
+      if (i2 >= 0 && i2 <= i) L[(int64_t)i * ld + (i2 - i + d.wA)] = (T)lA[e];
     }
   }
 }
@@ -452,8 +452,8 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     d.wA = hwA[j];
     d.bandK = bandK_tot;
     d.bandA = bandA_tot;
-    bandK_tot += (int64_t)d.nN * (d.wK + 1);
-    bandA_tot += (int64_t)d.nD * (d.wA + 1);
+    bandK_tot += (int64_t)d.nN * band_ld(d.wK);
+    bandA_tot += (int64_t)d.nD * band_ld(d.wA);
     out.maxwK = std::max(out.maxwK, d.wK);
     h->maxwA = std::max(h->maxwA, d.wA);
   }
@@ -477,9 +477,23 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   std::vector<BandDesc> bk(N), ba(N);
   for (int j = 0; j < N; ++j) {
     const SubDesc& d = h->hsub[j];
-    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, 0};
-    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, 0};
+    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, band_ld(d.wK)};
+    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, band_ld(d.wA)};
   }
+  // largest factorisations first: blocks are dispatched in index order, so
+  // this shortens the tail of the last wave (descriptors carry their id)
+  auto by_cost = [](const BandDesc& x, const BandDesc& y) {
+    const double cx = band_factor_flops(x.n, x.w), cy = band_factor_flops(y.n, y.w);
+    return cx > cy || (cx == cy && x.id < y.id);
+  };
+  std::vector<BandDesc> bkf = bk, baf = ba;
+  std::sort(bkf.begin(), bkf.end(), by_cost);
+  std::sort(baf.begin(), baf.end(), by_cost);
+  BandDesc *fdK = nullptr, *fdA = nullptr;
+  GENEO_TRY(tmp.get(&fdK, (size_t)N));
+  GENEO_TRY(tmp.get(&fdA, (size_t)N));
+  GENEO_CUDA(cudaMemcpyAsync(fdK, bkf.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
+  GENEO_CUDA(cudaMemcpyAsync(fdA, baf.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
   GENEO_TRY(tmp.get(&out.dbandK, (size_t)N));
   GENEO_TRY(h->mem.get(&h->dbandA, (size_t)N));
   GENEO_CUDA(cudaMemcpyAsync(out.dbandK, bk.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
@@ -501,13 +515,18 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   auto t1 = std::chrono::steady_clock::now();
   EventTimer ev;
   ev.start(s);
+  // K_j on the main stream, A_j concurrently on the auxiliary stream
+  GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
+  GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
   if (h->fp32) {
-    GENEO_TRY(band_potrf<float>((float*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
-    GENEO_TRY(band_potrf<float>((float*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
+    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
+    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
   } else {
-    GENEO_TRY(band_potrf<double>((double*)h->bandA, h->dbandA, N, h->maxwA, h->dstat, s));
-    GENEO_TRY(band_potrf<double>((double*)out.bandK, out.dbandK, N, out.maxwK, h->dstat, s));
+    GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
+    GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
   }
+  GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
+  GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   ev.stop();
   h->factor_ms = ev.ms;
   h->factor_flops = 0.0;

@@ -5,8 +5,7 @@
 // (Section 4.4) and the coarse matrix A_H (Section 4.5) are all banded in the
 // natural (lexicographic) dof order of a box subdomain, so one banded kernel
 // family serves all three.  One thread block owns one matrix; the batch is
-// the grid.  Storage: lower band, column-major, entry (r, c) with
-// 0 <= r - c <= w at L[c*(w+1) + (r - c)].
+// the grid.  Storage: lower band by rows (BandDesc in common.cuh).
 //
 // Factorisation (right-looking, block width NB): per step the NB x NB
 // diagonal block is factored by one warp, the panel rows below are solved
@@ -14,6 +13,14 @@
 // triangle receives the rank-NB update in 4x4 register tiles.  Pivots that
 // are not positive are reported (GENEO_ERR_NOT_SPD) and replaced by 1 so the
 // kernel always finishes.
+//
+// Solves (L L^T x = b, in place): the factor is streamed block row by block
+// row (SNB rows, one contiguous chunk) into shared memory by bulk copies on
+// an mbarrier pipeline.  The forward sweep is left-looking (each new row is
+// a dot product with the last w solved rows, kept in a shared ring), the
+// backward sweep right-looking (the rows above the current block are
+// updated in the shared ring); diagonal blocks are solved by warp shuffles.
+// The factor is read once per sweep; b and x once each.
 #include "common.cuh"
 
 namespace geneo {
@@ -21,10 +28,13 @@ namespace geneo {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSolveKmax = 64;   // right-hand sides handled per launch
 
 template <typename T>
 __device__ __forceinline__ bool finite_pos(T v) { return v > T(0) && isfinite(v); }
+
+__device__ __forceinline__ int64_t bidx(int r, int c, int w, int64_t ld) {
+  return (int64_t)r * ld + (c - r + w);
+}
 
 template <typename T, int NB, bool SMEMP>
 __global__ void __launch_bounds__(kThreads)
@@ -32,7 +42,7 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
              DevStatus* st) {
   const BandDesc d = descs[blockIdx.x];
   const int n = d.n, w = d.w;
-  const int64_t ld = (int64_t)w + 1;
+  const int64_t ld = d.ld;
   T* L = base + d.off;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Dk = reinterpret_cast<T*>(smem_raw);   // [NB][NB+1]
@@ -45,9 +55,9 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
     const int h = min(w, n - kb - b);
     // 1. diagonal block
     for (int idx = tid; idx < NB * NB; idx += nt) {
-      const int r = idx % NB, c = idx / NB;
+      const int r = idx / NB, c = idx % NB;
       T v = T(0);
-      if (r < b && c < b && r >= c && r - c <= w) v = L[(int64_t)(kb + c) * ld + (r - c)];
+      if (r < b && c < b && r >= c && r - c <= w) v = L[bidx(kb + r, kb + c, w, ld)];
       Dk[r * DS + c] = v;
     }
     __syncthreads();
@@ -77,8 +87,8 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
     __syncthreads();
     // 3. store the factored diagonal block
     for (int idx = tid; idx < NB * NB; idx += nt) {
-      const int r = idx % NB, c = idx / NB;
-      if (r < b && c < b && r >= c && r - c <= w) L[(int64_t)(kb + c) * ld + (r - c)] = Dk[r * DS + c];
+      const int r = idx / NB, c = idx % NB;
+      if (r < b && c < b && r >= c && r - c <= w) L[bidx(kb + r, kb + c, w, ld)] = Dk[r * DS + c];
     }
     // 4. panel: rows kb+b+i solve x L_kk^T = a
     for (int i = tid; i < h; i += nt) {
@@ -87,10 +97,7 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         T v = T(0);
-        if (t < b) {
-          const int dd = rr - (kb + t);
-          if (dd <= w) v = L[(int64_t)(kb + t) * ld + dd];
-        }
+        if (t < b && rr - (kb + t) <= w) v = L[bidx(rr, kb + t, w, ld)];
         x[t] = v;
       }
 #pragma unroll
@@ -105,17 +112,18 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
 #pragma unroll
       for (int t = 0; t < NB; ++t) {
         if (t < b) {
-          const int dd = rr - (kb + t);
-          if (dd <= w) L[(int64_t)(kb + t) * ld + dd] = x[t];
-          if (SMEMP) Ps[t * phmax + i] = (dd <= w) ? x[t] : T(0);
+          const bool inb = rr - (kb + t) <= w;
+          if (inb) L[bidx(rr, kb + t, w, ld)] = x[t];
+          if (SMEMP) Ps[t * phmax + i] = inb ? x[t] : T(0);
         }
       }
     }
     __syncthreads();
     // 5. trailing update of the h x h window, 4x4 register tiles
+    //    (consecutive threads take consecutive column tiles of one row tile)
     const int T4 = (h + 3) >> 2;
     for (int idx = tid; idx < T4 * T4; idx += nt) {
-      const int ti = idx % T4, tj = idx / T4;
+      const int ti = idx / T4, tj = idx % T4;
       if (tj > ti) continue;
       T acc[4][4];
 #pragma unroll
@@ -131,9 +139,8 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
             pr[q] = (i < h) ? Ps[t * phmax + i] : T(0);
             pc[q] = (j < h) ? Ps[t * phmax + j] : T(0);
           } else {
-            const int di = b + i - t, dj = b + j - t;
-            pr[q] = (i < h && di <= w) ? L[(int64_t)(kb + t) * ld + di] : T(0);
-            pc[q] = (j < h && dj <= w) ? L[(int64_t)(kb + t) * ld + dj] : T(0);
+            pr[q] = (i < h && b + i - t <= w) ? L[bidx(kb + b + i, kb + t, w, ld)] : T(0);
+            pc[q] = (j < h && b + j - t <= w) ? L[bidx(kb + b + j, kb + t, w, ld)] : T(0);
           }
         }
 #pragma unroll
@@ -142,14 +149,13 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
           for (int p = 0; p < 4; ++p) acc[q][p] += pr[q] * pc[p];
       }
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int j = 4 * tj + p;
-        if (j >= h) continue;
-        const int64_t colbase = (int64_t)(kb + b + j) * ld;
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * ti + q;
+        if (i >= h) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = 4 * ti + q;
-          if (i < h && i >= j) L[colbase + (i - j)] -= acc[q][p];
+        for (int p = 0; p < 4; ++p) {
+          const int j = 4 * tj + p;
+          if (j < h && i >= j) L[bidx(kb + b + i, kb + b + j, w, ld)] -= acc[q][p];
         }
       }
     }
@@ -157,12 +163,66 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
   }
 }
 
-// Forward then backward substitution with L and L^T, in place on X.
-template <typename T, int NB>
+// ---------------------------------------------------------------------------
+// Bulk-copy pipeline helpers (cp.async.bulk + mbarrier, sm_90 and later).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (seconds), reports
+// GENEO_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, DevStatus* st, int id,
+                                                  int64_t where) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  record_error(st, GENEO_ERR_TIMEOUT, id, where);
+  return false;
+}
+
+// rows per streamed block: 16, or 4 for bands too wide for 16-row stages
+// pipeline depth: three stages for FP32 factors, two for FP64 (room for the
+// right-hand-side ring)
+template <typename T> struct Stages { static constexpr int v = 3; };
+template <> struct Stages<double> { static constexpr int v = 2; };
+
+// Block v of the visit order 0..nb-1 (forward), nb-1..0 (backward).
+__device__ __forceinline__ int visit_block(int v, int nb) { return v < nb ? v : 2 * nb - 1 - v; }
+
+template <typename T, int kSNB>
 __global__ void __launch_bounds__(kThreads)
 k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
              double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
-             const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip) {
+             const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
+             DevStatus* st) {
   const int mi = blockIdx.x;
   if (skip && skip[mi]) return;
   int k = kcap;
@@ -171,119 +231,163 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   const BandDesc d = descs[mi];
   const int n = d.n, w = d.w;
   if (n <= 0) return;
-  const int64_t ld = (int64_t)w + 1;
+  const int ld = d.ld;
   const T* L = base + d.off;
   double* X = xbase + xoff[mi] + (int64_t)col0 * n;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int DS = NB + 1;
-  T* Dk = reinterpret_cast<T*>(smem_raw);   // [NB][NB+1]
-  T* Yb = Dk + NB * DS;                     // [NB][k]
-  T* Red = Yb + NB * kSolveKmax;            // partial sums
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int rmask = ring - 1;  // ring is a power of two >= w + 2 SNB
+  constexpr int kStages = Stages<T>::v;
 
-  auto load_diag = [&](int kb, int b) {
-    for (int idx = tid; idx < NB * NB; idx += nt) {
-      const int r = idx % NB, c = idx / NB;
-      T v = T(0);
-      if (r < b && c < b && r >= c && r - c <= w) v = L[(int64_t)(kb + c) * ld + (r - c)];
-      Dk[r * DS + c] = v;
-    }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                      // kStages
+  T* stage = reinterpret_cast<T*>(smem_raw + 128);                             // kStages * SNB * ld
+  T* win = stage + (size_t)kStages * kSNB * ld;                                // k columns of ring rows
+  T* blk = win + (size_t)ring * k;                                             // SNB * k
+  T* red = blk + (size_t)kSNB * k;                                             // 4 * kThreads
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kThreads >> 5;
+  const int nb = (n + kSNB - 1) / kSNB;
+  const int nvis = 2 * nb;
+
+  for (int idx = tid; idx < ring * k; idx += kThreads) win[idx] = T(0);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int v) {
+    const int kb = visit_block(v, nb) * kSNB;
+    const int b = min(kSNB, n - kb);
+    const int s = v % kStages;
+    const uint32_t bytes = (uint32_t)((size_t)b * ld * sizeof(T));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    bulk_load(stage + (size_t)s * kSNB * ld, L + (int64_t)kb * ld, bytes, &bars[s]);
   };
+  if (tid == 0)
+    for (int v = 0; v < min(kStages - 1, nvis); ++v) issue(v);
+  bool ok = true;
+  int lo = n;  // lowest row held in the ring during the backward sweep
 
-  // ---- forward: L y = x (right-looking, panel columns are contiguous)
-  for (int kb = 0; kb < n; kb += NB) {
-    const int b = min(NB, n - kb);
-    const int h = min(w, n - kb - b);
-    load_diag(kb, b);
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int t = idx % b, c = idx / b;
-      Yb[t * k + c] = (T)X[(int64_t)c * n + kb + t];
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt) {
-      for (int t = 0; t < b; ++t) {
-        T v = Yb[t * k + c];
-        for (int u = 0; u < t; ++u) v -= Dk[t * DS + u] * Yb[u * k + c];
-        Yb[t * k + c] = v / Dk[t * DS + t];
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int t = idx % b, c = idx / b;
-      X[(int64_t)c * n + kb + t] = (double)Yb[t * k + c];
-    }
-    constexpr int CB = 4;
-    const int ncg = (k + CB - 1) / CB;
-    for (int idx = tid; idx < h * ncg; idx += nt) {
-      const int i = idx % h, cg = idx / h;
-      const int r = kb + b + i;
-      T acc[CB];
-#pragma unroll
-      for (int q = 0; q < CB; ++q) acc[q] = T(0);
-      const int t0 = max(0, b + i - w);
-      for (int t = t0; t < b; ++t) {
-        const T l = L[(int64_t)(kb + t) * ld + (b + i - t)];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) {
-          const int c = cg * CB + q;
-          if (c < k) acc[q] += l * Yb[t * k + c];
+  for (int v = 0; v < nvis; ++v) {
+    const int s = v % kStages;
+    const uint32_t parity = (uint32_t)((v / kStages) & 1);
+    if (tid == 0 && v + kStages - 1 < nvis) issue(v + kStages - 1);
+    if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+    const T* S = stage + (size_t)s * kSNB * ld;
+    const int kb = visit_block(v, nb) * kSNB;
+    const int b = min(kSNB, n - kb);
+    if (v < nb) {
+      // ---------------- forward, rows kb..kb+b-1 (left-looking)
+      // dot products with the solved rows [kb + i - w, kb) held in the ring:
+      // a (b x w) x (w x k) product; a thread owns one row and CT right-hand
+      // sides over one segment of the band, partials reduced in shared memory
+      {
+        const int ct = k == 1 ? 1 : 4;
+        const int ntc = (k + ct - 1) / ct;
+        const int ntiles = b * ntc;
+        const int nseg = max(1, min(32, kThreads / ntiles));
+        for (int task = tid; task < ntiles * nseg; task += kThreads) {
+          const int tile = task % ntiles, seg = task / ntiles;
+          const int i = tile % b, c0 = (tile / b) * ct;
+          const int r = kb + i;
+          const int olo = max(0, w - r), ohi = w - i;  // columns r - w + oo in [0, kb)
+          const int len = max(0, ohi - olo);
+          const int s0 = olo + (int)((int64_t)len * seg / nseg);
+          const int s1 = olo + (int)((int64_t)len * (seg + 1) / nseg);
+          const T* srow = S + (size_t)i * ld;
+          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+          if (ct == 1) {
+            const T* wc = win + (size_t)c0 * ring;
+            for (int oo = s0; oo < s1; ++oo) a0 += srow[oo] * wc[(r - w + oo) & rmask];
+          } else {
+            const T* w0 = win + (size_t)c0 * ring;
+            const bool h1 = c0 + 1 < k, h2 = c0 + 2 < k, h3 = c0 + 3 < k;
+            const T* w1 = h1 ? w0 + ring : w0;
+            const T* w2 = h2 ? w0 + 2 * ring : w0;
+            const T* w3 = h3 ? w0 + 3 * ring : w0;
+            for (int oo = s0; oo < s1; ++oo) {
+              const T sv = srow[oo];
+              const int q = (r - w + oo) & rmask;
+              a0 += sv * w0[q];
+              a1 += sv * w1[q];
+              a2 += sv * w2[q];
+              a3 += sv * w3[q];
+            }
+          }
+          T* rd = red + (size_t)(seg * ntiles + tile) * 4;
+          rd[0] = a0;
+          rd[1] = a1;
+          rd[2] = a2;
+          rd[3] = a3;
+        }
+        __syncthreads();
+        for (int o = tid; o < b * k; o += kThreads) {
+          const int i = o % b, c = o / b;
+          const int tile = i + (c / ct) * b, q = c % ct;
+          T acc = T(0);
+          for (int seg = 0; seg < nseg; ++seg) acc += red[(size_t)(seg * ntiles + tile) * 4 + q];
+          blk[i * k + c] = (T)X[(int64_t)c * n + kb + i] - acc;
         }
       }
-#pragma unroll
-      for (int q = 0; q < CB; ++q) {
-        const int c = cg * CB + q;
-        if (c < k) X[(int64_t)c * n + r] -= (double)acc[q];
+      __syncthreads();
+      // diagonal block: one warp per right-hand side, shuffles
+      for (int c = wid; c < k; c += nw) {
+        T y = lane < b ? blk[lane * k + c] : T(0);
+        for (int t = 0; t < b; ++t) {
+          if (lane == t) y = y / S[t * ld + w];
+          const T yt = __shfl_sync(0xffffffffu, y, t);
+          if (lane > t && lane < b && lane - t <= w) y -= S[lane * ld + (w - lane + t)] * yt;
+        }
+        if (lane < b) {
+          win[(size_t)c * ring + ((kb + lane) & rmask)] = y;
+          X[(int64_t)c * n + kb + lane] = (double)y;
+        }
       }
-    }
-    __syncthreads();
-  }
-
-  // ---- backward: L^T x = y (left-looking: dot products with panel columns)
-  const int nblk = (n + NB - 1) / NB;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int kb = bi * NB;
-    const int b = min(NB, n - kb);
-    const int h = min(w, n - kb - b);
-    load_diag(kb, b);
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int t = idx % b, c = idx / b;
-      Yb[t * k + c] = (T)X[(int64_t)c * n + kb + t];
-    }
-    __syncthreads();
-    if (h > 0) {
-      const int nout = b * k;
-      const int S = max(1, min(8, nt / nout));
-      for (int o = tid; o < S * nout; o += nt) {
-        const int seg = o / nout, rem = o % nout;
-        const int t = rem % b, c = rem / b;
-        const int i0 = (int)((int64_t)seg * h / S), i1 = (int)((int64_t)(seg + 1) * h / S);
-        const int iend = min(i1, w - b + t + 1);   // band limit: b + i - t <= w
-        T acc = T(0);
-        const T* lc = L + (int64_t)(kb + t) * ld + (b - t);
-        const double* xc = X + (int64_t)c * n + kb + b;
-        for (int i = i0; i < iend; ++i) acc += lc[i] * (T)xc[i];
-        Red[o] = acc;
+    } else {
+      // ---------------- backward, block kb (right-looking on L^T)
+      const int newlo = max(0, kb - w);
+      if (newlo < lo) {
+        const int cnt = lo - newlo;
+        for (int idx = tid; idx < cnt * k; idx += kThreads) {
+          const int rr = newlo + idx % cnt, c = idx / cnt;
+          win[(size_t)c * ring + (rr & rmask)] = (T)X[(int64_t)c * n + rr];
+        }
+        lo = newlo;
       }
       __syncthreads();
-      for (int rem = tid; rem < nout; rem += nt) {
-        T s = T(0);
-        for (int seg = 0; seg < S; ++seg) s += Red[seg * nout + rem];
-        const int t = rem % b, c = rem / b;
-        Yb[t * k + c] -= s;
+      for (int c = wid; c < k; c += nw) {
+        T y = lane < b ? win[(size_t)c * ring + ((kb + lane) & rmask)] : T(0);
+        for (int t = b - 1; t >= 0; --t) {
+          if (lane == t) y = y / S[t * ld + w];
+          const T xt = __shfl_sync(0xffffffffu, y, t);
+          if (lane < t && t - lane <= w) y -= S[t * ld + (w - t + lane)] * xt;
+        }
+        if (lane < b) {
+          blk[lane * k + c] = y;
+          X[(int64_t)c * n + kb + lane] = (double)y;
+        }
       }
       __syncthreads();
-    }
-    for (int c = tid; c < k; c += nt) {
-      for (int t = b - 1; t >= 0; --t) {
-        T v = Yb[t * k + c];
-        for (int u = t + 1; u < b; ++u) v -= Dk[u * DS + t] * Yb[u * k + c];
-        Yb[t * k + c] = v / Dk[t * DS + t];
+      // rows [lo, kb) of the ring: y -= sum_t L(kb + t, row) x_t
+      const int cnt = kb - lo;
+      const int ncg = (k + 3) / 4;
+      for (int idx = tid; idx < cnt * ncg; idx += kThreads) {
+        const int rr = lo + idx % cnt, c0 = (idx / cnt) * 4;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        const int tmax = min(b - 1, rr - kb + w);
+        for (int t = 0; t <= tmax; ++t) {
+          const T sv = S[t * ld + (rr - kb - t + w)];
+          const T* bt = blk + t * k + c0;
+          a0 += sv * bt[0];
+          if (c0 + 1 < k) a1 += sv * bt[1];
+          if (c0 + 2 < k) a2 += sv * bt[2];
+          if (c0 + 3 < k) a3 += sv * bt[3];
+        }
+        const int q = rr & rmask;
+        win[(size_t)c0 * ring + q] -= a0;
+        if (c0 + 1 < k) win[(size_t)(c0 + 1) * ring + q] -= a1;
+        if (c0 + 2 < k) win[(size_t)(c0 + 2) * ring + q] -= a2;
+        if (c0 + 3 < k) win[(size_t)(c0 + 3) * ring + q] -= a3;
       }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int t = idx % b, c = idx / b;
-      X[(int64_t)c * n + kb + t] = (double)Yb[t * k + c];
     }
     __syncthreads();
   }
@@ -291,6 +395,12 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
 
 constexpr int kNB = 32;
 constexpr size_t kSmemCap = 200 * 1024;
+
+inline int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
 
 }  // namespace
 
@@ -313,19 +423,33 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
   return GENEO_OK;
 }
 
+// Shared memory of one solve launch with k right-hand sides.
+template <typename T>
+size_t solve_smem(int max_w, int k, int ring, int snb) {
+  const int ld = band_ld(max_w);
+  return 128 + sizeof(T) * ((size_t)Stages<T>::v * snb * ld + (size_t)ring * k + (size_t)snb * k + 4 * kThreads);
+}
+
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, cudaStream_t s) {
-  (void)max_w;
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
-  const size_t smem = (size_t)kNB * (kNB + 1) * sizeof(T) + (size_t)kNB * kSolveKmax * sizeof(T) +
-                      (size_t)std::max(kThreads, kNB * kSolveKmax) * sizeof(T);
-  auto kern = k_band_solve<T, kNB>;
+  int snb = 16;
+  if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16) > kSmemCap) snb = 4;
+  const int ring = next_pow2(max_w + 2 * snb);
+  // right-hand sides per launch: as many as fit in shared memory
+  // at most 64 per launch: the forward partial-sum buffer holds 4 * kThreads
+  // values for b * ceil(k / 4) <= kThreads tiles
+  int kmax = std::min(nrhs, 64);
+  while (kmax > 1 && solve_smem<T>(max_w, kmax, ring, snb) > kSmemCap) kmax = (kmax + 1) / 2;
+  const size_t smem = solve_smem<T>(max_w, kmax, ring, snb);
+  if (smem > 227 * 1024) return GENEO_ERR_ARG;  // band too wide for the streamed solve
+  auto kern = snb == 16 ? k_band_solve<T, 16> : k_band_solve<T, 4>;
   GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  for (int c0 = 0; c0 < nrhs; c0 += kSolveKmax) {
-    const int kc = std::min(kSolveKmax, nrhs - c0);
-    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev); note_launch();
+  for (int c0 = 0; c0 < nrhs; c0 += kmax) {
+    const int kc = std::min(kmax, nrhs - c0);
+    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
   }
   return GENEO_OK;
@@ -337,9 +461,9 @@ template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, Dev
                                           cudaStream_t);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
-                                           cudaStream_t);
+                                           DevStatus*, cudaStream_t);
 template geneo_status_t band_solve<float>(const float*, const BandDesc*, int, int, double*,
                                           const int64_t*, int, const int32_t*, const int32_t*,
-                                          cudaStream_t);
+                                          DevStatus*, cudaStream_t);
 
 }  // namespace geneo

@@ -159,14 +159,14 @@ k_coarse_block(const SubDesc* __restrict__ sub, const int2* __restrict__ pairs,
       acc[u] = s;
     }
   }
-  const int64_t ld = (int64_t)wH + 1;
+  const int64_t ld = band_ld(wH);
 #pragma unroll
   for (int u = 0; u < kOut; ++u) {
     const int o = threadIdx.x + u * kT;
     if (o >= mi * mj) continue;
     const int a = o % mi, b = o / mi;
     const int r = di.offH + a, c = dj.offH + b;
-    if (r >= c && r - c <= wH) band[(int64_t)c * ld + (r - c)] = acc[u];
+    if (r >= c && r - c <= wH) band[(int64_t)r * ld + (c - r + wH)] = acc[u];
   }
 }
 
@@ -244,8 +244,8 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
     }
   }
   h->wH = wH;
-  GENEO_TRY(h->mem.get(&h->bandH, (size_t)h->dimH * (wH + 1)));
-  GENEO_CUDA(cudaMemsetAsync(h->bandH, 0, sizeof(double) * h->dimH * (wH + 1), s));
+  GENEO_TRY(h->mem.get(&h->bandH, (size_t)h->dimH * band_ld(wH)));
+  GENEO_CUDA(cudaMemsetAsync(h->bandH, 0, sizeof(double) * h->dimH * band_ld(wH), s));
   int2* dpairs = nullptr;
   GENEO_TRY(tmp.get(&dpairs, pairs.size()));
   GENEO_CUDA(cudaMemcpyAsync(dpairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, s));
@@ -256,7 +256,7 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   *ms_matrix = ms_since(t1);
 
   auto t2 = std::chrono::steady_clock::now();
-  BandDesc bh{0, h->dimH, wH, -2, 0};
+  BandDesc bh{0, h->dimH, wH, -2, band_ld(wH)};
   GENEO_TRY(h->mem.get(&h->dbandH, 1));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandH, &bh, sizeof(BandDesc), cudaMemcpyHostToDevice, s));
   GENEO_TRY(band_potrf<double>(h->bandH, h->dbandH, 1, wH, h->dstat, s));

@@ -91,14 +91,18 @@ struct SubDesc {
 };
 
 // Band matrix descriptor for the batched Cholesky / triangular solves.
-// Lower band stored column-major: entry (r, c), 0 <= r - c <= w, at
-// base[c * ld + (r - c)], ld = w + 1.
+// Lower band stored by rows: entry (r, c), 0 <= r - c <= w, at
+// base[r * ld + (c - r + w)]; ld = w + 1 rounded up to a multiple of 4, so
+// every row (and every block of rows) starts on a 16-byte boundary (32 for
+// FP64) and can be moved by one bulk copy.  Slots with c < 0 are zero.
 struct BandDesc {
-  int64_t off;     // element offset of the band
+  int64_t off;     // element offset of the band (a multiple of 4)
   int32_t n, w;
   int32_t id;      // reported in errors
-  int32_t pad;
+  int32_t ld;      // row stride
 };
+
+__host__ __device__ __forceinline__ int band_ld(int w) { return (w + 4) & ~3; }
 
 // --------------------------------------------------------------------------
 // Device helpers.
@@ -207,6 +211,6 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, cudaStream_t s);
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s);
 
 }  // namespace geneo

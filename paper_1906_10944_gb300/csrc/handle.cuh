@@ -7,6 +7,8 @@
 struct geneo_handle_s {
   geneo::DevMem mem;        // everything the handle keeps
   cudaStream_t stream = 0;  // stream of the last synchronising call
+  cudaStream_t aux = nullptr;       // second stream (coarse solve, concurrent factorisations)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   geneo_options_t opt{};
   bool fp32 = false;
 

@@ -612,9 +612,9 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
     if (f32)
       return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, s * 2,
-                               ncols, skip, st);
+                               ncols, skip, h->dstat, st);
     return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
-                              s * 2, ncols, skip, st);
+                              s * 2, ncols, skip, h->dstat, st);
   };
   // timed with CUDA events; flops from the per-subdomain column counts
   auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {

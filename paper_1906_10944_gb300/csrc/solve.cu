@@ -236,14 +236,21 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
   const int N = h->N;
   k_restrict<<<N, kT, 0, s>>>(h->dsub, h->Dlist, r, h->Z, h->u, h->cH); note_launch();
   GENEO_CUDA(cudaGetLastError());
+  // the coarse solve (one block) runs beside the batched local solves
+  if (h->dimH > 0) {
+    GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
+    GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr,
+                                 h->dstat, h->aux));
+    GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
+  }
   if (h->fp32)
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                nullptr, nullptr, s));
+                                nullptr, nullptr, h->dstat, s));
   else
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                 nullptr, nullptr, s));
-  if (h->dimH > 0)
-    GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr, s));
+                                 nullptr, nullptr, h->dstat, s));
+  if (h->dimH > 0) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
   k_prolong<<<grid, kT, 0, s>>>(h->n, h->dir, r, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
                                 h->u, h->Z, h->cH, z); note_launch();
