@@ -266,100 +266,126 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
     for (int v = 0; v < min(kStages - 1, nvis); ++v) issue(v);
   bool ok = true;
   int lo = n;  // lowest row held in the ring during the backward sweep
+  constexpr int kMaxRhsPerWarp = 8;
 
   for (int v = 0; v < nvis; ++v) {
     const int s = v % kStages;
     const uint32_t parity = (uint32_t)((v / kStages) & 1);
     if (tid == 0 && v + kStages - 1 < nvis) issue(v + kStages - 1);
-    if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
-    const T* S = stage + (size_t)s * kSNB * ld;
     const int kb = visit_block(v, nb) * kSNB;
     const int b = min(kSNB, n - kb);
     if (v < nb) {
       // ---------------- forward, rows kb..kb+b-1 (left-looking)
+      // right-hand sides of this block, fetched before the wait (lane i of
+      // the warp owning right-hand side c holds b[kb + i][c])
+      T xb[kMaxRhsPerWarp];
+#pragma unroll
+      for (int u = 0; u < kMaxRhsPerWarp; ++u) {
+        const int c = wid + u * nw;
+        xb[u] = (c < k && lane < b) ? (T)X[(int64_t)c * n + kb + lane] : T(0);
+      }
+      if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+      const T* S = stage + (size_t)s * kSNB * ld;
       // dot products with the solved rows [kb + i - w, kb) held in the ring:
       // a (b x w) x (w x k) product; a thread owns one row and CT right-hand
-      // sides over one segment of the band, partials reduced in shared memory
-      {
-        const int ct = k == 1 ? 1 : 4;
-        const int ntc = (k + ct - 1) / ct;
-        const int ntiles = b * ntc;
-        const int nseg = max(1, min(32, kThreads / ntiles));
-        for (int task = tid; task < ntiles * nseg; task += kThreads) {
-          const int tile = task % ntiles, seg = task / ntiles;
-          const int i = tile % b, c0 = (tile / b) * ct;
-          const int r = kb + i;
-          const int olo = max(0, w - r), ohi = w - i;  // columns r - w + oo in [0, kb)
-          const int len = max(0, ohi - olo);
-          const int s0 = olo + (int)((int64_t)len * seg / nseg);
-          const int s1 = olo + (int)((int64_t)len * (seg + 1) / nseg);
-          const T* srow = S + (size_t)i * ld;
-          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-          if (ct == 1) {
-            const T* wc = win + (size_t)c0 * ring;
-            for (int oo = s0; oo < s1; ++oo) a0 += srow[oo] * wc[(r - w + oo) & rmask];
-          } else {
-            const T* w0 = win + (size_t)c0 * ring;
-            const bool h1 = c0 + 1 < k, h2 = c0 + 2 < k, h3 = c0 + 3 < k;
-            const T* w1 = h1 ? w0 + ring : w0;
-            const T* w2 = h2 ? w0 + 2 * ring : w0;
-            const T* w3 = h3 ? w0 + 3 * ring : w0;
-            for (int oo = s0; oo < s1; ++oo) {
-              const T sv = srow[oo];
-              const int q = (r - w + oo) & rmask;
-              a0 += sv * w0[q];
-              a1 += sv * w1[q];
-              a2 += sv * w2[q];
-              a3 += sv * w3[q];
-            }
+      // sides over one segment of the band, partials summed by the warp that
+      // owns the right-hand side
+      const int ct = k == 1 ? 1 : 4;
+      const int ntc = (k + ct - 1) / ct;
+      const int ntiles = b * ntc;
+      const int nseg = max(1, min(32, kThreads / ntiles));
+      for (int task = tid; task < ntiles * nseg; task += kThreads) {
+        const int tile = task % ntiles, seg = task / ntiles;
+        const int i = tile % b, c0 = (tile / b) * ct;
+        const int r = kb + i;
+        const int olo = max(0, w - r), ohi = w - i;  // columns r - w + oo in [0, kb)
+        const int len = max(0, ohi - olo);
+        const int s0 = olo + (int)((int64_t)len * seg / nseg);
+        const int s1 = olo + (int)((int64_t)len * (seg + 1) / nseg);
+        const T* srow = S + (size_t)i * ld;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        if (ct == 1) {
+          const T* wc = win + (size_t)c0 * ring;
+          int oo = s0;
+          for (; oo + 1 < s1; oo += 2) {
+            a0 += srow[oo] * wc[(r - w + oo) & rmask];
+            a1 += srow[oo + 1] * wc[(r - w + oo + 1) & rmask];
           }
-          T* rd = red + (size_t)(seg * ntiles + tile) * 4;
-          rd[0] = a0;
-          rd[1] = a1;
-          rd[2] = a2;
-          rd[3] = a3;
+          if (oo < s1) a0 += srow[oo] * wc[(r - w + oo) & rmask];
+          a0 += a1;
+          a1 = T(0);
+        } else {
+          const T* w0 = win + (size_t)c0 * ring;
+          const bool h1 = c0 + 1 < k, h2 = c0 + 2 < k, h3 = c0 + 3 < k;
+          const T* w1 = h1 ? w0 + ring : w0;
+          const T* w2 = h2 ? w0 + 2 * ring : w0;
+          const T* w3 = h3 ? w0 + 3 * ring : w0;
+          for (int oo = s0; oo < s1; ++oo) {
+            const T sv = srow[oo];
+            const int q = (r - w + oo) & rmask;
+            a0 += sv * w0[q];
+            a1 += sv * w1[q];
+            a2 += sv * w2[q];
+            a3 += sv * w3[q];
+          }
         }
-        __syncthreads();
-        for (int o = tid; o < b * k; o += kThreads) {
-          const int i = o % b, c = o / b;
-          const int tile = i + (c / ct) * b, q = c % ct;
-          T acc = T(0);
-          for (int seg = 0; seg < nseg; ++seg) acc += red[(size_t)(seg * ntiles + tile) * 4 + q];
-          blk[i * k + c] = (T)X[(int64_t)c * n + kb + i] - acc;
-        }
+        T* rd = red + (size_t)(seg * ntiles + tile) * 4;
+        rd[0] = a0;
+        rd[1] = a1;
+        rd[2] = a2;
+        rd[3] = a3;
       }
       __syncthreads();
-      // diagonal block: one warp per right-hand side, shuffles
-      for (int c = wid; c < k; c += nw) {
-        T y = lane < b ? blk[lane * k + c] : T(0);
-        for (int t = 0; t < b; ++t) {
-          if (lane == t) y = y / S[t * ld + w];
-          const T yt = __shfl_sync(0xffffffffu, y, t);
-          if (lane > t && lane < b && lane - t <= w) y -= S[lane * ld + (w - lane + t)] * yt;
+      // diagonal block by the warp owning each right-hand side: row of L and
+      // the reciprocal pivot in registers, substitution by shuffles
+      T lrow[kSNB];
+#pragma unroll
+      for (int t = 0; t < kSNB; ++t)
+        lrow[t] = (lane < b && t < lane && lane - t <= w) ? S[lane * ld + (w - lane + t)] : T(0);
+      const T dinv = lane < b ? T(1) / S[lane * ld + w] : T(0);
+#pragma unroll
+      for (int u = 0; u < kMaxRhsPerWarp; ++u) {
+        const int c = wid + u * nw;
+        if (c >= k) break;
+        T y = T(0);
+        if (lane < b) {
+          const int tile = lane + (c / ct) * b, q = c % ct;
+          T acc = T(0);
+          for (int seg = 0; seg < nseg; ++seg) acc += red[(size_t)(seg * ntiles + tile) * 4 + q];
+          y = xb[u] - acc;
+        }
+#pragma unroll
+        for (int t = 0; t < kSNB; ++t) {
+          if (t < b) {
+            if (lane == t) y *= dinv;
+            const T yt = __shfl_sync(0xffffffffu, y, t);
+            if (lane > t) y -= lrow[t] * yt;
+          }
         }
         if (lane < b) {
           win[(size_t)c * ring + ((kb + lane) & rmask)] = y;
           X[(int64_t)c * n + kb + lane] = (double)y;
         }
       }
+      if (v == nb - 1) lo = max(0, kb - w);  // the ring holds rows [lo, n) for the backward sweep
     } else {
       // ---------------- backward, block kb (right-looking on L^T)
-      const int newlo = max(0, kb - w);
-      if (newlo < lo) {
-        const int cnt = lo - newlo;
-        for (int idx = tid; idx < cnt * k; idx += kThreads) {
-          const int rr = newlo + idx % cnt, c = idx / cnt;
-          win[(size_t)c * ring + (rr & rmask)] = (T)X[(int64_t)c * n + rr];
-        }
-        lo = newlo;
-      }
-      __syncthreads();
+      if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+      const T* S = stage + (size_t)s * kSNB * ld;
+      T lcol[kSNB];
+#pragma unroll
+      for (int t = 0; t < kSNB; ++t)
+        lcol[t] = (t < b && lane < t && t - lane <= w) ? S[t * ld + (w - t + lane)] : T(0);
+      const T dinv = lane < b ? T(1) / S[lane * ld + w] : T(0);
       for (int c = wid; c < k; c += nw) {
         T y = lane < b ? win[(size_t)c * ring + ((kb + lane) & rmask)] : T(0);
-        for (int t = b - 1; t >= 0; --t) {
-          if (lane == t) y = y / S[t * ld + w];
-          const T xt = __shfl_sync(0xffffffffu, y, t);
-          if (lane < t && t - lane <= w) y -= S[t * ld + (w - t + lane)] * xt;
+#pragma unroll
+        for (int t = kSNB - 1; t >= 0; --t) {
+          if (t < b) {
+            if (lane == t) y *= dinv;
+            const T xt = __shfl_sync(0xffffffffu, y, t);
+            if (lane < t) y -= lcol[t] * xt;
+          }
         }
         if (lane < b) {
           blk[lane * k + c] = y;
@@ -367,7 +393,9 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         }
       }
       __syncthreads();
-      // rows [lo, kb) of the ring: y -= sum_t L(kb + t, row) x_t
+      // rows [lo, kb) of the ring: y -= sum_t L(kb + t, row) x_t; at the same
+      // time the rows the next block adds to the ring come from X (forward
+      // results, not yet finalised by this sweep)
       const int cnt = kb - lo;
       const int ncg = (k + 3) / 4;
       for (int idx = tid; idx < cnt * ncg; idx += kThreads) {
@@ -387,6 +415,15 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         if (c0 + 1 < k) win[(size_t)(c0 + 1) * ring + q] -= a1;
         if (c0 + 2 < k) win[(size_t)(c0 + 2) * ring + q] -= a2;
         if (c0 + 3 < k) win[(size_t)(c0 + 3) * ring + q] -= a3;
+      }
+      if (kb > 0) {
+        const int nlo = max(0, kb - kSNB - w);
+        const int ncnt = lo - nlo;
+        for (int idx = tid; idx < ncnt * k; idx += kThreads) {
+          const int rr = nlo + idx % ncnt, c = idx / ncnt;
+          win[(size_t)c * ring + (rr & rmask)] = (T)X[(int64_t)c * n + rr];
+        }
+        lo = nlo;
       }
     }
     __syncthreads();
@@ -441,7 +478,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
   // right-hand sides per launch: as many as fit in shared memory
   // at most 64 per launch: the forward partial-sum buffer holds 4 * kThreads
   // values for b * ceil(k / 4) <= kThreads tiles
-  int kmax = std::min(nrhs, 64);
+  int kmax = std::min(nrhs, 64);  // 8 warps x 8 right-hand sides in registers
   while (kmax > 1 && solve_smem<T>(max_w, kmax, ring, snb) > kSmemCap) kmax = (kmax + 1) / 2;
   const size_t smem = solve_smem<T>(max_w, kmax, ring, snb);
   if (smem > 227 * 1024) return GENEO_ERR_ARG;  // band too wide for the streamed solve

@@ -50,6 +50,7 @@ struct geneo_handle_s {
   std::vector<double> lambda_host; // [N * s] ascending lambda per subdomain
   int s_block = 0;
   int eig_iters = 0;
+  int eig_second_pass = 0;         // subdomains solved again with the full block
 
   // apply / PCG work
   double* u = nullptr;             // [sumD] local solutions

@@ -34,8 +34,9 @@ namespace {
 constexpr int kT = 256;
 constexpr int kMaxW = 104;      // largest [X, Q] width handled by the dense kernels
 constexpr int kRS = 4;          // row splits of the Gram kernel
-constexpr int kRB = 24;         // rows per shared-memory chunk in the Gram kernel
+constexpr int kRB = 32;         // rows per shared-memory chunk in the Gram kernel
 constexpr int kMaxSweeps = 40;  // bound of the Jacobi sweep loop
+constexpr int kFirstPassNev = 8; // wanted pairs of the narrow first pass
 
 // A multivector operand: columns [c0 + c0d[j], + width) of a buffer holding W
 // columns per subdomain (rows = nN_j, column-major, ld = nN_j).
@@ -107,8 +108,11 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef 
 }
 
 // Partial Gram matrices G = A^T B over a row split; ld of G is ldg.
-// Each thread owns up to 3 register tiles of 4x4; sym computes the lower
-// triangle only (A == B).
+// The output is cut into 4x4 register tiles (lower triangle only when sym,
+// A == B); when there are fewer tiles than threads, each tile is shared by
+// several row groups (thread g of a tile takes rows g, g + groups, ... of
+// every staged chunk) and the groups' partials are summed in a fixed order at
+// the end, so all warps issue FP64 FMAs.
 __global__ void __launch_bounds__(kT)
 k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double* __restrict__ Gp,
             int ldg, int nsub, const int32_t* __restrict__ skip) {
@@ -120,46 +124,67 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
   if (p <= 0 || q <= 0) return;
   const double* a = cr_ptr(A, d, j);
   const double* b = cr_ptr(B, d, j);
-  __shared__ double As[kRB][kMaxW + 1];
-  __shared__ double Bs[kRB][kMaxW + 1];
+  extern __shared__ double gsm[];
+  double* As = gsm;                         // [kRB][kMaxW + 1]
+  double* Bs = gsm + kRB * (kMaxW + 1);     // [kRB][kMaxW + 1]
+  constexpr int LDS = kMaxW + 1;
   const int tp = (p + 3) >> 2, tq = (q + 3) >> 2;
-  const int ntiles = tp * tq;
-  double acc[3][16];
+  // tiles: full tp x tq grid, or its lower triangle (ti >= tj) when sym
+  const int ntiles = sym ? tp * (tp + 1) / 2 : tp * tq;
+  const int groups = max(1, kT / ntiles);
+  const int tpt = (ntiles + kT - 1) / kT;   // tiles per thread when groups == 1 (<= 3)
+  const int g = threadIdx.x / ntiles;       // row group (groups > 1)
   int own[3];
 #pragma unroll
   for (int u = 0; u < 3; ++u) {
-    const int t = threadIdx.x + u * kT;
-    own[u] = -1;
-    if (t < ntiles) {
-      const int ti = t % tp, tj = t / tp;
-      if (!sym || tj <= ti) own[u] = t;
+    int t = groups > 1 ? (threadIdx.x < groups * ntiles ? threadIdx.x % ntiles : -1)
+                       : (u < tpt ? threadIdx.x + u * kT : -1);
+    if (groups > 1 && u > 0) t = -1;
+    if (t >= ntiles) t = -1;
+    own[u] = t;
+  }
+  auto tile_rc = [&](int t, int& ti, int& tj) {
+    if (sym) {  // row-major enumeration of the lower triangle
+      int r = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((r + 1) * (r + 2) / 2 <= t) ++r;
+      while (r * (r + 1) / 2 > t) --r;
+      ti = r;
+      tj = t - r * (r + 1) / 2;
+    } else {
+      ti = t % tp;
+      tj = t / tp;
     }
+  };
+  double acc[3][16];
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
 #pragma unroll
     for (int z = 0; z < 16; ++z) acc[u][z] = 0.0;
-  }
   const int r0 = (int)((int64_t)rs * d.nN / kRS), r1 = (int)((int64_t)(rs + 1) * d.nN / kRS);
   for (int rb = r0; rb < r1; rb += kRB) {
     const int nr = min(kRB, r1 - rb);
     __syncthreads();
     for (int idx = threadIdx.x; idx < kRB * p; idx += kT) {
       const int r = idx % kRB, c = idx / kRB;
-      As[r][c] = r < nr ? a[(int64_t)c * d.nN + rb + r] : 0.0;
+      As[r * LDS + c] = r < nr ? a[(int64_t)c * d.nN + rb + r] : 0.0;
     }
     for (int idx = threadIdx.x; idx < kRB * q; idx += kT) {
       const int r = idx % kRB, c = idx / kRB;
-      Bs[r][c] = r < nr ? b[(int64_t)c * d.nN + rb + r] : 0.0;
+      Bs[r * LDS + c] = r < nr ? b[(int64_t)c * d.nN + rb + r] : 0.0;
     }
     __syncthreads();
+    const int rstart = groups > 1 ? g : 0;
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       if (own[u] < 0) continue;
-      const int ti = own[u] % tp, tj = own[u] / tp;
-      for (int r = 0; r < nr; ++r) {
+      int ti, tj;
+      tile_rc(own[u], ti, tj);
+      for (int r = rstart; r < nr; r += groups) {
         double av[4], bv[4];
 #pragma unroll
         for (int z = 0; z < 4; ++z) {
-          av[z] = (4 * ti + z < p) ? As[r][4 * ti + z] : 0.0;
-          bv[z] = (4 * tj + z < q) ? Bs[r][4 * tj + z] : 0.0;
+          av[z] = (4 * ti + z < p) ? As[r * LDS + 4 * ti + z] : 0.0;
+          bv[z] = (4 * tj + z < q) ? Bs[r * LDS + 4 * tj + z] : 0.0;
         }
 #pragma unroll
         for (int z = 0; z < 4; ++z)
@@ -168,10 +193,30 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
       }
     }
   }
+  if (groups > 1) {
+    // sum the row groups' partials: group-major in shared memory
+    __syncthreads();
+    double* red = gsm;  // groups * ntiles * 16 <= kT * 16 doubles
+    if (own[0] >= 0)
+#pragma unroll
+      for (int z = 0; z < 16; ++z) red[((size_t)g * ntiles + own[0]) * 16 + z] = acc[0][z];
+    __syncthreads();
+    for (int o = threadIdx.x; o < ntiles * 16; o += kT) {
+      const int t = o / 16, z = o % 16;
+      double sum = 0.0;
+      for (int gg = 0; gg < groups; ++gg) sum += red[((size_t)gg * ntiles + t) * 16 + z];
+      int ti, tj;
+      tile_rc(t, ti, tj);
+      const int r = 4 * ti + z / 4, c = 4 * tj + z % 4;
+      if (r < p && c < q) G[(int64_t)c * ldg + r] = sum;
+    }
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < 3; ++u) {
     if (own[u] < 0) continue;
-    const int ti = own[u] % tp, tj = own[u] / tp;
+    int ti, tj;
+    tile_rc(own[u], ti, tj);
 #pragma unroll
     for (int z = 0; z < 4; ++z)
 #pragma unroll
@@ -244,8 +289,10 @@ k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ 
 }
 
 // Counter-based start block: uniform(-1, 1) from SplitMix64.
-__global__ void k_init_random(const SubDesc* __restrict__ sub, ColRef X, uint64_t seed) {
+__global__ void k_init_random(const SubDesc* __restrict__ sub, ColRef X, uint64_t seed,
+                              const int32_t* __restrict__ skip) {
   const int j = blockIdx.y;
+  if (skip && skip[j]) return;
   const SubDesc d = sub[j];
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.nN) return;
@@ -452,12 +499,13 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
         const double* __restrict__ nu_all, int ldnu, const int32_t* __restrict__ sj,
         const int32_t* __restrict__ spj, int32_t* __restrict__ aj, int32_t* __restrict__ qj,
         int32_t* __restrict__ done, int32_t* __restrict__ iters, int32_t* __restrict__ notdone,
-        double* __restrict__ rn_out, double tol, double tau, double sigma, int nev, int fixed,
+        double* __restrict__ rn_out, double tol, double tau, double sigma, const int32_t* __restrict__ nevj, int fixed,
         int it) {
   const int j = blockIdx.x;
   if (done[j]) return;
   const SubDesc d = sub[j];
   const int s = sj[j];
+  const int nev = nevj[j];
   const double* nu = nu_all + (int64_t)j * ldnu;
   const double* bx = cr_ptr(BX, d, j);
   const double* kx = cr_ptr(KX, d, j);
@@ -534,6 +582,11 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
   }
 }
 
+__global__ void k_clear_p(int32_t* __restrict__ spj, const int32_t* __restrict__ skip, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && !skip[j]) spj[j] = 0;
+}
+
 __global__ void k_set_i32(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int n,
                           const int32_t* __restrict__ skip) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,7 +621,8 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_TRY(tmp.get(&Tm, (size_t)N * ldg * ldg));
   GENEO_TRY(tmp.get(&nu, (size_t)N * s));
   GENEO_TRY(tmp.get(&rn, (size_t)N * s));
-  int32_t *sj, *aj, *qj, *rj, *spj, *done, *iters, *notdone;
+  int32_t *sj, *aj, *qj, *rj, *spj, *done, *iters, *notdone, *nevj;
+  GENEO_TRY(tmp.get(&nevj, (size_t)N));
   GENEO_TRY(tmp.get(&sj, (size_t)N));
   GENEO_TRY(tmp.get(&aj, (size_t)N));
   GENEO_TRY(tmp.get(&qj, (size_t)N));
@@ -583,18 +637,15 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(cudaMemsetAsync(spj, 0, sizeof(int32_t) * N, st));
   GENEO_CUDA(cudaMemsetAsync(done, 0, sizeof(int32_t) * N, st));
   GENEO_CUDA(cudaMemsetAsync(iters, 0, sizeof(int32_t) * N, st));
-  std::vector<int32_t> hs(N);
   int maxn = 0;
-  for (int j = 0; j < N; ++j) {
-    hs[j] = std::min(s, h->hsub[j].nN);
-    maxn = std::max(maxn, h->hsub[j].nN);
-  }
-  GENEO_CUDA(cudaMemcpyAsync(sj, hs.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+  for (int j = 0; j < N; ++j) maxn = std::max(maxn, h->hsub[j].nN);
   const dim3 gridR(ceil_div(maxn, kT), N);
   const size_t dense_smem = sizeof(double) * (2 * kMaxW * (kMaxW + 1) + 6 * kMaxW + kT / 32 + 8);
   GENEO_CUDA(cudaFuncSetAttribute(k_svqb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
   const size_t nn_smem = sizeof(double) * kMaxW * kMaxW;
+  const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
+  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
 
   const bool f32 = h->fp32;
@@ -631,7 +682,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     return r;
   };
   auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip) -> geneo_status_t {
-    k_gram_part<<<dim3(kRS, N), kT, 0, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    k_gram_part<<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
     k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
@@ -663,74 +714,125 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const ColRef Sr = cref(S, W3, 0, nullptr, 0, sj, qj);  // [X, Q]
   const ColRef BSr = cref(BS, W3, 0, nullptr, 0, sj, qj);
 
-  auto t0 = std::chrono::steady_clock::now();
-  // ---- start block: X = K^{-1} B R, K-orthonormalised, Rayleigh-Ritz
-  k_init_random<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), o.seed); note_launch();
-  spmm(false, true, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, Xr, nullptr);   // S[:, 0:s] = B R
-  GENEO_CUDA(cudaGetLastError());
-  GENEO_TRY(solveK(xoffX, sj, nullptr));
-  spmm(true, false, Xr, KXr, KXr, nullptr);
-  GENEO_TRY(gram(Xr, KXr, 1, nullptr));
-  k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, nullptr); note_launch();
-  GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, nullptr));
-  k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, nullptr); note_launch();
-  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr); note_launch();
-  spmm(false, true, Xr, BXr, BXr, nullptr);
-  GENEO_TRY(gram(Xr, BXr, 1, nullptr));
-  k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, nullptr); note_launch();
-  GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, nullptr));
-  k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, nullptr); note_launch();
-  GENEO_CUDA(cudaGetLastError());
-
-  // ---- iterations
-  std::vector<int64_t> hq(N);
-  for (int j = 0; j < N; ++j) hq[j] = hxoff[j];  // Q offset depends on s_j: computed per iteration
-  int it = 0;
-  int remaining = N;
-  for (it = 0; it < o.eig_maxit; ++it) {
-    spmm(true, true, Xr, KXr, BXr, done);
-    GENEO_CUDA(cudaMemsetAsync(notdone, 0, sizeof(int32_t), st));
-    k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
-                              spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nev,
-                              o.fixed_nev, it); note_launch();
+  // Start block for the subdomains with skip[j] == 0: X = K^{-1} B R
+  // (R counter-based random), K-orthonormalised by SVQB, Rayleigh-Ritz.
+  auto init_block = [&](const int32_t* skip, uint64_t seed) -> geneo_status_t {
+    k_init_random<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), seed, skip); note_launch();
+    spmm(false, true, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, Xr, skip);   // S[:, 0:s] = B R
     GENEO_CUDA(cudaGetLastError());
-    GENEO_CUDA(cudaMemcpyAsync(&remaining, notdone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    GENEO_CUDA(cudaStreamSynchronize(st));
-    if (remaining == 0) break;
-    // W = K^{-1} R (active columns start at column s_j)
-    std::vector<int32_t> hsj(N);
-    GENEO_CUDA(cudaMemcpyAsync(hsj.data(), sj, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
-    GENEO_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < N; ++j) hq[j] = hxoff[j] + (int64_t)hsj[j] * h->hsub[j].nN;
-    GENEO_CUDA(cudaMemcpyAsync(xoffQ, hq.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
-    GENEO_TRY(solveK(xoffQ, aj, done));
-    // K-orthogonalise Q against X (twice), SVQB, once more each
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int rep = 0; rep < (pass == 0 ? 2 : 1); ++rep) {
+    GENEO_TRY(solveK(xoffX, sj, skip));
+    spmm(true, false, Xr, KXr, KXr, skip);
+    GENEO_TRY(gram(Xr, KXr, 1, skip));
+    k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip); note_launch();
+    GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, skip));
+    k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, skip); note_launch();
+    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
+    spmm(false, true, Xr, BXr, BXr, skip);
+    GENEO_TRY(gram(Xr, BXr, 1, skip));
+    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip); note_launch();
+    GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
+    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  };
+  std::vector<int64_t> hq(N);
+  int total_it = 0;
+  auto iterate = [&]() -> geneo_status_t {
+    int remaining = N;
+    for (int it = 0; it < o.eig_maxit; ++it, ++total_it) {
+      spmm(true, true, Xr, KXr, BXr, done);
+      GENEO_CUDA(cudaMemsetAsync(notdone, 0, sizeof(int32_t), st));
+      k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
+                                spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nevj,
+                                o.fixed_nev, it); note_launch();
+      GENEO_CUDA(cudaGetLastError());
+      GENEO_CUDA(cudaMemcpyAsync(&remaining, notdone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      GENEO_CUDA(cudaStreamSynchronize(st));
+      if (remaining == 0) break;
+      // W = K^{-1} R (active columns start at column s_j)
+      std::vector<int32_t> hsj(N);
+      GENEO_CUDA(cudaMemcpyAsync(hsj.data(), sj, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+      GENEO_CUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j) hq[j] = hxoff[j] + (int64_t)hsj[j] * h->hsub[j].nN;
+      GENEO_CUDA(cudaMemcpyAsync(xoffQ, hq.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
+      GENEO_TRY(solveK(xoffQ, aj, done));
+      // Q = [W, P]: K-orthogonalise against X, SVQB; once more each
+      for (int pass = 0; pass < 2; ++pass) {
         spmm(true, false, Qr, KQr, KQr, done);
         GENEO_TRY(gram(Xr, KQr, 0, done));
         GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
+        spmm(true, false, Qr, KQr, KQr, done);
+        GENEO_TRY(gram(Qr, KQr, 1, done));
+        k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch();
+        GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
+        k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
+        k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
+        GENEO_CUDA(cudaGetLastError());
       }
-      spmm(true, false, Qr, KQr, KQr, done);
-      GENEO_TRY(gram(Qr, KQr, 1, done));
-      k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch();
-      GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
-      k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
-      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
+      // Rayleigh-Ritz on S = [X, Q]
+      spmm(false, true, Sr, BSr, BSr, done);
+      GENEO_TRY(gram(Sr, BSr, 1, done));
+      k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch();
+      // P = Q U[s_j:, :], X = S U
+      GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
+      k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
+      GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
+      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
       GENEO_CUDA(cudaGetLastError());
+      GENEO_TRY(check_status(h, st));
     }
-    // Rayleigh-Ritz on S = [X, Q]
-    spmm(false, true, Sr, BSr, BSr, done);
-    GENEO_TRY(gram(Sr, BSr, 1, done));
-    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch();
-    // P = Q U[s_j:, :], X = S U
-    GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
-    k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
-    GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
-    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
-    GENEO_CUDA(cudaGetLastError());
-    GENEO_TRY(check_status(h, st));
+    return GENEO_OK;
+  };
+
+  auto t0 = std::chrono::steady_clock::now();
+  // Pass 1 with a narrow block: most subdomains have only a few eigenvalues
+  // below tau.  A subdomain whose narrow block fills with converged
+  // eigenvalues below tau is solved again with the full width (pass 2).
+  const int guard = s - nev;
+  const int nev1 = o.fixed_nev ? nev : std::min(nev, kFirstPassNev);
+  {
+    std::vector<int32_t> hs1(N), hn1(N, nev1);
+    for (int j = 0; j < N; ++j) hs1[j] = std::min(nev1 + guard, h->hsub[j].nN);
+    GENEO_CUDA(cudaMemcpyAsync(sj, hs1.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    GENEO_CUDA(cudaMemcpyAsync(nevj, hn1.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
   }
+  GENEO_TRY(init_block(nullptr, o.seed));
+  GENEO_TRY(iterate());
+  if (nev1 < nev) {
+    std::vector<double> hnu1((size_t)N * s);
+    GENEO_CUDA(cudaMemcpyAsync(hnu1.data(), nu, sizeof(double) * N * s, cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> redo(N, 1), hs2(N), hn2(N, nev);
+    int nredo = 0;
+    for (int j = 0; j < N; ++j) {
+      int below = 0;
+      for (int i = 0; i < nev1; ++i) {
+        const double v = hnu1[(size_t)j * s + i];
+        if (v > 0.0 && o.sigma + 1.0 / v < o.tau) ++below;
+      }
+      hs2[j] = std::min(s, h->hsub[j].nN);
+      if (below >= nev1 && hs2[j] > nev1) {
+        redo[j] = 0;   // skip flag 0: solve again
+        ++nredo;
+      }
+    }
+    h->eig_second_pass = nredo;
+    if (nredo > 0) {
+      // done[j] = 1 for the others; widen the block of the redone ones
+      for (int j = 0; j < N; ++j) if (redo[j]) hs2[j] = -1;
+      std::vector<int32_t> hsj_now(N);
+      GENEO_CUDA(cudaMemcpyAsync(hsj_now.data(), sj, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+      GENEO_CUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j) if (hs2[j] < 0) hs2[j] = hsj_now[j];
+      GENEO_CUDA(cudaMemcpyAsync(sj, hs2.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+      GENEO_CUDA(cudaMemcpyAsync(nevj, hn2.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+      GENEO_CUDA(cudaMemcpyAsync(done, redo.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+      k_clear_p<<<ceil_div(N, 128), 128, 0, st>>>(spj, done, N); note_launch();
+      GENEO_TRY(init_block(done, o.seed ^ 0x9E3779B97F4A7C15ull));
+      GENEO_TRY(iterate());
+    }
+  }
+  const int it = total_it;
   h->eig_iters = it;
   h->setup_ms[3] = ms_since(t0);
   // eigenvalues lambda = sigma + 1/nu (ascending in lambda = descending nu)
