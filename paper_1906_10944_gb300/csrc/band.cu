@@ -217,8 +217,8 @@ template <> struct Stages<double> { static constexpr int v = 2; };
 // Block v of the visit order 0..nb-1 (forward), nb-1..0 (backward).
 __device__ __forceinline__ int visit_block(int v, int nb) { return v < nb ? v : 2 * nb - 1 - v; }
 
-template <typename T, int kSNB>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int kSNB, int kMaxRhsPerWarp, int kStages>
+__global__ void __launch_bounds__(kThreads, kMaxRhsPerWarp == 1 ? (sizeof(T) == 4 ? 4 : 2) : 1)
 k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
              double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
              const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
@@ -235,7 +235,6 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   const T* L = base + d.off;
   double* X = xbase + xoff[mi] + (int64_t)col0 * n;
   const int rmask = ring - 1;  // ring is a power of two >= w + 2 SNB
-  constexpr int kStages = Stages<T>::v;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                      // kStages
@@ -266,7 +265,6 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
     for (int v = 0; v < min(kStages - 1, nvis); ++v) issue(v);
   bool ok = true;
   int lo = n;  // lowest row held in the ring during the backward sweep
-  constexpr int kMaxRhsPerWarp = 8;
 
   for (int v = 0; v < nvis; ++v) {
     const int s = v % kStages;
@@ -462,9 +460,9 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
 
 // Shared memory of one solve launch with k right-hand sides.
 template <typename T>
-size_t solve_smem(int max_w, int k, int ring, int snb) {
+size_t solve_smem(int max_w, int k, int ring, int snb, int stages) {
   const int ld = band_ld(max_w);
-  return 128 + sizeof(T) * ((size_t)Stages<T>::v * snb * ld + (size_t)ring * k + (size_t)snb * k + 4 * kThreads);
+  return 128 + sizeof(T) * ((size_t)stages * snb * ld + (size_t)ring * k + (size_t)snb * k + 4 * kThreads);
 }
 
 template <typename T>
@@ -472,17 +470,33 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
+  // One right-hand side (the preconditioner's local solves): two stages and
+  // one register slot per warp keep the block small enough for several
+  // blocks per SM, which hides the latency of the sequential sweep.
+  if (nrhs == 1) {
+    int snb = 16;
+    if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16, 2) > kSmemCap) snb = 4;
+    const int ring = next_pow2(max_w + 2 * snb);
+    const size_t smem = solve_smem<T>(max_w, 1, ring, snb, 2);
+    if (smem > 227 * 1024) return GENEO_ERR_ARG;
+    auto kern = snb == 16 ? k_band_solve<T, 16, 1, 2> : k_band_solve<T, 4, 1, 2>;
+    GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  }
+  constexpr int stg = Stages<T>::v;
   int snb = 16;
-  if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16) > kSmemCap) snb = 4;
+  if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16, stg) > kSmemCap) snb = 4;
   const int ring = next_pow2(max_w + 2 * snb);
-  // right-hand sides per launch: as many as fit in shared memory
-  // at most 64 per launch: the forward partial-sum buffer holds 4 * kThreads
-  // values for b * ceil(k / 4) <= kThreads tiles
-  int kmax = std::min(nrhs, 64);  // 8 warps x 8 right-hand sides in registers
-  while (kmax > 1 && solve_smem<T>(max_w, kmax, ring, snb) > kSmemCap) kmax = (kmax + 1) / 2;
-  const size_t smem = solve_smem<T>(max_w, kmax, ring, snb);
+  // right-hand sides per launch: as many as fit in shared memory, at most 64
+  // (8 warps x 8 register slots; the forward partial-sum buffer holds
+  // 4 * kThreads values for b * ceil(k / 4) <= kThreads tiles)
+  int kmax = std::min(nrhs, 64);
+  while (kmax > 1 && solve_smem<T>(max_w, kmax, ring, snb, stg) > kSmemCap) kmax = (kmax + 1) / 2;
+  const size_t smem = solve_smem<T>(max_w, kmax, ring, snb, stg);
   if (smem > 227 * 1024) return GENEO_ERR_ARG;  // band too wide for the streamed solve
-  auto kern = snb == 16 ? k_band_solve<T, 16> : k_band_solve<T, 4>;
+  auto kern = snb == 16 ? k_band_solve<T, 16, 8, stg> : k_band_solve<T, 4, 8, stg>;
   GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int c0 = 0; c0 < nrhs; c0 += kmax) {
     const int kc = std::min(kmax, nrhs - c0);

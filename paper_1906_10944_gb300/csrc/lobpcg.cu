@@ -80,16 +80,38 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
   double* y1 = cr_ptr(Y1, d, j);
   double* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
   const int64_t e0 = lrow[d.offN + a], e1 = lrow[d.offN + a + 1];
-  for (int c = 0; c < w; ++c) {
-    const double* xc = x + (int64_t)c * d.nN;
+  const int64_t nn = d.nN;
+  // four columns per pass: the row's column indices and values are read once
+  // per four vectors
+  int c = 0;
+  for (; c + 4 <= w; c += 4) {
+    const double* xc = x + (int64_t)c * nn;
+    double s10 = 0, s11 = 0, s12 = 0, s13 = 0, s20 = 0, s21 = 0, s22 = 0, s23 = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const int col = lcol[e];
+      const double x0 = xc[col], x1 = xc[nn + col], x2 = xc[2 * nn + col], x3 = xc[3 * nn + col];
+      const double va = v1[e];
+      s10 += va * x0; s11 += va * x1; s12 += va * x2; s13 += va * x3;
+      if (v2) {
+        const double vb = v2[e];
+        s20 += vb * x0; s21 += vb * x1; s22 += vb * x2; s23 += vb * x3;
+      }
+    }
+    y1[c * nn + a] = s10; y1[(c + 1) * nn + a] = s11; y1[(c + 2) * nn + a] = s12; y1[(c + 3) * nn + a] = s13;
+    if (v2) {
+      y2[c * nn + a] = s20; y2[(c + 1) * nn + a] = s21; y2[(c + 2) * nn + a] = s22; y2[(c + 3) * nn + a] = s23;
+    }
+  }
+  for (; c < w; ++c) {
+    const double* xc = x + (int64_t)c * nn;
     double s1 = 0.0, s2 = 0.0;
     for (int64_t e = e0; e < e1; ++e) {
       const double xv = xc[lcol[e]];
       s1 += v1[e] * xv;
       if (v2) s2 += v2[e] * xv;
     }
-    y1[(int64_t)c * d.nN + a] = s1;
-    if (v2) y2[(int64_t)c * d.nN + a] = s2;
+    y1[c * nn + a] = s1;
+    if (v2) y2[c * nn + a] = s2;
   }
 }
 

@@ -159,3 +159,36 @@ def test_host_memory_path():
         assert info["converged"] and res <= 1.01e-8
     finally:
         G.geneo_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["c1", "3d"])
+def test_mixed_precision_matches_oracle(case):
+    """FP32 factors (local solves and the eigensolver's shift-invert operator)
+    with FP64 residuals, Rayleigh-Ritz, coarse problem and PCG: eigenvalues
+    still meet the FP64 tolerance (the eigensolver's residuals are FP64), the
+    solve reaches relative residual 1e-8, and the PCG iteration count stays
+    within 10 % (+2) of the oracle's."""
+    if case == "c1":
+        prob = _c1()
+        nev = 10
+    else:
+        nel = (18, 14, 12)
+        kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
+                                      slab_z=(30, 80), slab_thickness=1)
+        prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
+        nev = 8
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=nev))
+    sol, _ = run_gpu(prob, nev_max=nev, precision=1)
+    try:
+        for j in range(prob.n_sub):
+            g = sol.subdomain(j)
+            m = min(g["m"], orc.ms[j])
+            lo = orc.lams[j][:m]
+            assert np.all(np.abs(g["lambda"][:m] - lo) <= 1e-6 * np.maximum(np.abs(lo), 3e-4)), j
+        x, info = gpu_solve(sol, prob)
+        _, ito, _, _ = orc.solve(tol=1e-8)
+        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
+        assert info["converged"] and res <= 1.01e-8
+        assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
+    finally:
+        sol.close()
