@@ -8,8 +8,11 @@ element layers, kappa = exp(Gaussian field) with 1e6-contrast slabs, at most
 1e-8): geneo_setup (partition of unity, local matrices, factorisations,
 eigensolves, coarse space) + geneo_pcg_solve + geneo_destroy, inputs resident
 in device memory.  value = dofs solved per second over the timed steps.
+The default path is the mixed-precision one (FP32 band factors and local
+solves; FP64 residuals, Rayleigh-Ritz, coarse problem and PCG); `compare`
+holds one timed step of the FP64 path ("mixed vs FP64").
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
 
 Under torchrun (N > 1) every rank solves its own copy of the workload
@@ -198,16 +201,54 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+# roof of each kernel family of geneo_coarse_info_t.prof_*
+FAMILY_BOUND = {
+    "factor": "alu-factor", "eig_solve": "alu-factor", "gram": "alu-fp64", "spmm": "alu-fp64",
+    "gemm": "alu-fp64", "small_eig": "alu-fp64", "local_solve": "hbm", "coarse_solve": "alu-fp64",
+    "spmv": "hbm",
+}
+
+
+def family_roofline(name, rec, precision, hbm_peak, hbm_src):
+    bound = FAMILY_BOUND.get(name, "alu-fp64")
+    ms = rec["ms"]
+    if bound == "hbm":
+        ach = rec["bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": rec["bytes"] / max(rec["launches"], 1)}
+    fp32 = bound == "alu-factor" and precision == "mixed"
+    peak = fp32_peak() if fp32 else fp64_peak()
+    ach = rec["flops"] / (ms / 1e3) if ms > 0 else 0.0
+    return {"bound": "alu", "kernel": name, "achieved": ach / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x %d flop/clk x 2070 MHz (%s ALU)"
+                           % (256 if fp32 else 4, "FP32" if fp32 else "FP64"),
+            "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="darcy3d_128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison steps")
+    ap.add_argument("--no-profile", action="store_true", help="skip the profiled step")
     ap.add_argument("--ref-sample", type=int, default=3)
     ap.add_argument("--ref-pcg-iters", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -235,19 +276,28 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     w = WORKLOADS[args.workload]
     prob = make_problem(args.workload)
     host = G.problem_arrays(prob)
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     b_dev = torch.from_numpy(prob.b).cuda()
     x_dev = torch.zeros_like(b_dev)
-    prec = G.GENEO_PREC_FP32 if args.precision == "fp32" else G.GENEO_PREC_FP64
-    opts = G.geneo_default_options(nev_max=w["nev"], tau=w["tau"], precision=prec)
     problem = G.make_problem(dev, prob.n, prob.n_sub, prob.elem_dofs.shape[1], prob.ndn,
                              G.GENEO_MEM_DEVICE)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def options(precision, profile=0):
+        prec = G.GENEO_PREC_FP32 if precision == "mixed" else G.GENEO_PREC_FP64
+        return G.geneo_default_options(nev_max=w["nev"], tau=w["tau"], precision=prec, profile=profile)
+
+    def step(opts):
         h = G.geneo_setup(problem, opts, stream)
         try:
             info = G.geneo_pcg_solve(h, b_dev, x_dev, 1, args.tol, 2000, G.GENEO_MEM_DEVICE,
@@ -257,32 +307,42 @@ def main():
             G.geneo_destroy(h)
         return info, q
 
-    for _ in range(args.warmup):
-        info, q = step()
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    launches0 = G.geneo_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    infos, qs = [], []
-    for _ in range(args.steps):
-        info, q = step()
-        infos.append(info)
-        qs.append(q)
-    ev1.record(stream)
-    barrier()
-    launches = G.geneo_launch_count() - launches0
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = prob.n * args.steps * world / (t_max / 1e3)
-    res = float(np.linalg.norm(prob.b - prob.A @ x_dev.cpu().numpy()) / np.linalg.norm(prob.b))
+    def timed(precision, steps, warmup, clocks=None):
+        opts = options(precision)
+        for _ in range(warmup):
+            step(opts)
+        barrier()
+        if clocks:
+            clocks.start()
+        l0 = G.geneo_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        infos, qs = [], []
+        for _ in range(steps):
+            info, q = step(opts)
+            infos.append(info)
+            qs.append(q)
+        ev1.record(stream)
+        barrier()
+        launches = G.geneo_launch_count() - l0
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        res = float(np.linalg.norm(prob.b - prob.A @ x_dev.cpu().numpy()) / np.linalg.norm(prob.b))
+        return {"ms": ms, "infos": infos, "qs": qs, "launches": launches, "clocks": clk, "res": res}
+
+    main_run = timed(args.precision, args.steps, args.warmup, ClockSampler(local))
+    value = prob.n * args.steps * world / (main_run["ms"] / 1e3)
+    qm = main_run["qs"][-1]
+    info_m = main_run["infos"][-1]
+
+    compare = None
+    if not args.no_compare:
+        other = "fp64" if args.precision == "mixed" else "mixed"
+        r = timed(other, 1, 1)
+        compare = {"precision": other, "value": prob.n * world / (r["ms"] / 1e3), "unit": UNIT,
+                   "ms_per_step": r["ms"], "pcg_iterations": r["infos"][-1]["iterations"],
+                   "rel_residual_true": r["res"], "dim_coarse": r["qs"][-1]["dim_coarse"]}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -294,6 +354,7 @@ def main():
         x_h = torch.zeros_like(b_h).pin_memory()
         h2d = sum(v.numel() * v.element_size() for v in pinned.values()) + b_h.numel() * 8
         d2h = x_h.numel() * 8
+        opts = options(args.precision)
         times = []
         for _ in range(max(1, min(args.steps, 2))):
             barrier()
@@ -305,54 +366,58 @@ def main():
                 G.geneo_destroy(h)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-        e2e = {"value": prob.n / statistics.median(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": prob.n * world / max_over_ranks(statistics.median(times)), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel (largest share of the step's device time)
-    qm = qs[-1]
-    step_ms = t_max / args.steps
-    cands = {
-        "band_potrf (batched Cholesky of A_j, K_j)": (qm["factor_flops"], qm["factor_event_ms"]),
-        "band_solve (eigensolver K_j^{-1} blocks)": (qm["eigsolve_flops"], qm["eigsolve_event_ms"]),
-    }
-    dom = max(cands, key=lambda k: cands[k][1])
-    fl, kms = cands[dom]
-    peak = fp32_peak() if args.precision == "fp32" else fp64_peak()
-    achieved = fl / (kms / 1e3) if kms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "share_of_step": kms / step_ms,
-                "peak_source": "derived: 152 SMs x %d flop/clk x 2070 MHz (%s ALU)"
-                               % (256 if args.precision == "fp32" else 4, args.precision.upper())}
+    # one untimed profiled step: per kernel family CUDA-event time and work
+    hbm_peak, hbm_src = measured_peaks()
+    roofline, families, apply_roof = None, None, None
+    if not args.no_profile:
+        _, qp = step(options(args.precision, profile=1))
+        fam = qp["prof"]
+        tot = sum(r["ms"] for r in fam.values()) or 1.0
+        families = {k: {"ms": round(r["ms"], 3), "share": round(r["ms"] / tot, 4), "launches": r["launches"],
+                        "flops": r["flops"], "bytes": r["bytes"]} for k, r in fam.items() if r["launches"]}
+        dom = max((k for k in fam if fam[k]["launches"]), key=lambda k: fam[k]["ms"])
+        roofline = family_roofline(dom, fam[dom], args.precision, hbm_peak, hbm_src)
+        roofline["share_of_profiled_step"] = fam[dom]["ms"] / tot
+        if fam["local_solve"]["launches"]:
+            apply_roof = family_roofline("local_solve", fam["local_solve"], args.precision, hbm_peak,
+                                         hbm_src)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r = oracle_sample(prob, w["nev"], w["tau"], args.ref_sample, infos[-1]["iterations"])
+        r = oracle_sample(prob, w["nev"], w["tau"], args.ref_sample, info_m["iterations"])
         cpu = {"value": prob.n / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d largest subdomains (setup incl. ARPACK) + one local solve each, "
                          "1 core, %.1f s of CPU work; extrapolated to %d subdomains and %d PCG "
                          "iterations" % (r["n_sample"], r["sample_s"], prob.n_sub,
-                                         infos[-1]["iterations"])}
+                                         info_m["iterations"])}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32-factors/f64",
+            "dtype": "f32-factors/f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": w["desc"], "precision": args.precision,
-                       "l2": "inputs larger than L2 (2.1M-dof CSR and 1.07 GB of element matrices); no flush",
+            "config": {"workload": w["desc"],
+                       "precision": ("mixed: FP32 band factors and local solves; FP64 residuals, "
+                                     "Rayleigh-Ritz, coarse problem and PCG")
+                                    if args.precision == "mixed" else "fp64",
+                       "l2": "inputs larger than L2 (CSR A 0.7 GB, element matrices 1.07 GB); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu,
-            "detail": {"pcg_iterations": infos[-1]["iterations"], "rel_residual_true": res,
-                       "kappa_estimate": infos[-1]["kappa_estimate"], "dim_coarse": qm["dim_coarse"],
+            "e2e": e2e, "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
+            "roofline": roofline, "cpu_baseline": cpu,
+            "compare": compare,
+            "detail": {"pcg_iterations": info_m["iterations"], "rel_residual_true": main_run["res"],
+                       "kappa_estimate": info_m["kappa_estimate"], "dim_coarse": qm["dim_coarse"],
                        "eig_iterations": qm["eig_iterations"], "block_size": qm["block_size"],
                        "setup_ms": dict(zip(["structure", "assembly", "factor", "eigensolve", "basis",
                                              "coarse_matrix", "coarse_factor", "total"],
                                             [round(v, 3) for v in qm["setup_ms"]])),
-                       "device_gb": qm["device_bytes"] / 1e9},
+                       "device_gb": qm["device_bytes"] / 1e9,
+                       "apply_roofline": apply_roof, "families": families},
         }
         print(json.dumps(line))
     if dist is not None:

@@ -135,6 +135,7 @@ typedef struct {
  *  eig_maxit  iteration cap of the block eigensolver (default 100).
  *  guard      extra block vectors beyond nev_max (default min(5, nev_max)).
  *  precision  geneo_precision_t (default GENEO_PREC_FP64).
+ *  profile    0 (default) or 1, see geneo_coarse_info_t.prof_*.
  *  seed       seed of the counter-based start vectors (SplitMix64).
  */
 typedef struct {
@@ -147,6 +148,11 @@ typedef struct {
   int32_t eig_maxit;
   int32_t guard;
   int32_t precision;
+  int32_t profile;     /* 1: time every kernel family with CUDA events (see
+                          geneo_coarse_info_t.prof_*); adds event records
+                          and one synchronisation at the end of each call.
+                          It creates CUDA events as it goes, so handles used
+                          with geneo_pcg_solve_noalloc keep it at 0. */
   uint64_t seed;
 } geneo_options_t;
 
@@ -187,7 +193,29 @@ typedef struct {
   double apply_flops;        /* algorithmic flops of one geneo_apply */
   double apply_bytes;        /* algorithmic bytes of one geneo_apply: factors,
                                 Z, the coarse factor and the vectors once */
+  /* With options.profile = 1, per kernel family (index GENEO_PROF_*):
+   * CUDA-event milliseconds on the launching stream, launches, and the
+   * algorithmic flops and bytes of those launches (setup and every
+   * apply/solve on the handle so far). */
+  double prof_ms[10];
+  double prof_flops[10];
+  double prof_bytes[10];
+  int64_t prof_launches[10];
 } geneo_coarse_info_t;
+
+/* Kernel families of geneo_coarse_info_t.prof_*. */
+enum {
+  GENEO_PROF_FACTOR = 0,       /* batched banded Cholesky (A_j, K_j, A_H) */
+  GENEO_PROF_EIG_SOLVE = 1,    /* eigensolver block solves with K_j */
+  GENEO_PROF_GRAM = 2,         /* eigensolver Gram matrices (FP64) */
+  GENEO_PROF_SPMM = 3,         /* eigensolver sparse products with K_j, B_j */
+  GENEO_PROF_GEMM = 4,         /* eigensolver block updates (FP64) */
+  GENEO_PROF_SMALL_EIG = 5,    /* Jacobi SVQB and Rayleigh-Ritz */
+  GENEO_PROF_LOCAL_SOLVE = 6,  /* preconditioner local solves L_j L_j^T u = r_j */
+  GENEO_PROF_COARSE_SOLVE = 7, /* preconditioner coarse solve */
+  GENEO_PROF_SPMV = 8,         /* PCG sparse matrix-vector product */
+  GENEO_PROF_OTHER = 9
+};
 
 /* Fill *opt with the defaults listed above. */
 void geneo_default_options(geneo_options_t* opt);

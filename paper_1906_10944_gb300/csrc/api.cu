@@ -124,6 +124,7 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   GENEO_TRY(geneo::alloc_solver(h));
   GENEO_TRY(geneo::check_status(h, s));
   h->setup_ms[7] = ms_since(t_all);
+  h->prof.collect();
   return GENEO_OK;
 }
 
@@ -142,6 +143,7 @@ void geneo_default_options(geneo_options_t* o) {
   o->eig_maxit = 100;
   o->guard = -1;
   o->precision = GENEO_PREC_FP64;
+  o->profile = 0;
   o->seed = 0x5EED5EEDull;
 }
 
@@ -166,6 +168,7 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   if (!h) return GENEO_ERR_OOM;
   h->opt = o;
   h->fp32 = o.precision == GENEO_PREC_FP32;
+  h->prof.on = o.profile != 0;
   const int guard = o.guard >= 0 ? o.guard : std::min(5, o.nev_max);
   h->s_block = std::min(o.nev_max + guard, 34);
   h->stream = (cudaStream_t)stream;
@@ -245,6 +248,14 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->eigsolve_event_ms = h->eig_ms;
   info->apply_flops = h->apply_flops;
   info->apply_bytes = h->apply_bytes;
+  cudaDeviceSynchronize();
+  h->prof.collect();
+  for (int i = 0; i < 10; ++i) {
+    info->prof_ms[i] = h->prof.ms[i];
+    info->prof_flops[i] = h->prof.flops[i];
+    info->prof_bytes[i] = h->prof.bytes[i];
+    info->prof_launches[i] = h->prof.launches[i];
+  }
   return GENEO_OK;
 }
 

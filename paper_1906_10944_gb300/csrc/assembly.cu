@@ -518,6 +518,15 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   // K_j on the main stream, A_j concurrently on the auxiliary stream
   GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
   GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+  double flK = 0, flA = 0, byK = 0, byA = 0;
+  for (const SubDesc& d : h->hsub) {
+    flK += band_factor_flops(d.nN, d.wK);
+    flA += band_factor_flops(d.nD, d.wA);
+    byK += 2.0 * esz * band_entries(d.nN, d.wK);
+    byA += 2.0 * esz * band_entries(d.nD, d.wA);
+  }
+  const int pK = h->prof.begin(GENEO_PROF_FACTOR, flK, byK, s);
+  const int pA = h->prof.begin(GENEO_PROF_FACTOR, flA, byA, h->aux);
   if (h->fp32) {
     GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
     GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
@@ -525,6 +534,8 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
     GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
   }
+  h->prof.end(pK, s);
+  h->prof.end(pA, h->aux);
   GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   ev.stop();

@@ -259,7 +259,10 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   BandDesc bh{0, h->dimH, wH, -2, band_ld(wH)};
   GENEO_TRY(h->mem.get(&h->dbandH, 1));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandH, &bh, sizeof(BandDesc), cudaMemcpyHostToDevice, s));
+  const int pf = h->prof.begin(GENEO_PROF_FACTOR, band_factor_flops(h->dimH, wH),
+                               2.0 * 8.0 * band_entries(h->dimH, wH), s);
   GENEO_TRY(band_potrf<double>(h->bandH, h->dbandH, 1, wH, h->dstat, s));
+  h->prof.end(pf, s);
   GENEO_TRY(check_status(h, s));
   *ms_factor = ms_since(t2);
   tmp.release(Y);

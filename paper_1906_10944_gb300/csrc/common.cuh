@@ -73,6 +73,53 @@ struct EventTimer {
 };
 const std::string& last_cuda_error();
 
+// Opt-in per-family timing: event pairs recorded around launches, summed
+// when the owner synchronises (no synchronisation per launch).
+struct KernelProfiler {
+  struct Rec { int fam; cudaEvent_t a, b; double flops, bytes; };
+  bool on = false;
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[10] = {0}, flops[10] = {0}, bytes[10] = {0};
+  int64_t launches[10] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // returns the index of the open record or -1
+  int begin(int fam, double fl, double by, cudaStream_t s) {
+    if (!on) return -1;
+    Rec r{fam, get(), get(), fl, by};
+    cudaEventRecord(r.a, s);
+    pending.push_back(r);
+    return (int)pending.size() - 1;
+  }
+  void end(int idx, cudaStream_t s) {
+    if (idx < 0) return;
+    cudaEventRecord(pending[idx].b, s);
+  }
+  void collect() {
+    for (Rec& r : pending) {
+      cudaEventSynchronize(r.b);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.fam] += t;
+      flops[r.fam] += r.flops;
+      bytes[r.fam] += r.bytes;
+      launches[r.fam] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~KernelProfiler() {
+    for (Rec& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 // --------------------------------------------------------------------------
 // Per-subdomain descriptor (device and host copies).
 // --------------------------------------------------------------------------

@@ -64,8 +64,11 @@ struct geneo_handle_s {
 
   double factor_flops = 0, factor_ms = 0, eig_flops = 0, eig_ms = 0;
   double apply_flops = 0, apply_bytes = 0;
+  double local_solve_flops = 0, local_solve_bytes = 0, spmv_flops = 0, spmv_bytes = 0;
   double* hist = nullptr;          // PCG alpha/beta history (2 * hist_cap)
   int hist_cap = 0;
+
+  geneo::KernelProfiler prof;
 
   geneo::DevStatus* dstat = nullptr;
   geneo::DevStatus hstat{};

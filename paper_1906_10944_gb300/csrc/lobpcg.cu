@@ -12,7 +12,7 @@
 // preconditioner.  Per iteration and subdomain:
 //   R = B X - K X diag(nu)            residuals, relative norms rn_i
 //   W = K^{-1} R[:, active]           active = columns with rn_i > tol
-//   Q = [W, P], K-orthogonalised against X twice, K-orthonormalised by SVQB
+//   Q = [W, P], K-orthogonalised against X and K-orthonormalised by SVQB, twice
 //   Rayleigh-Ritz on S = [X, Q] (S^T K S = I): eig(S^T B S), top s
 //   P = Q U_Q, X = S U
 // Stop when every Ritz pair below the threshold tau is converged and the
@@ -135,7 +135,7 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef 
 // several row groups (thread g of a tile takes rows g, g + groups, ... of
 // every staged chunk) and the groups' partials are summed in a fixed order at
 // the end, so all warps issue FP64 FMAs.
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 2)
 k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double* __restrict__ Gp,
             int ldg, int nsub, const int32_t* __restrict__ skip) {
   const int j = blockIdx.y, rs = blockIdx.x;
@@ -604,6 +604,12 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
   }
 }
 
+__global__ void k_sub_nnz(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
+                          int64_t* __restrict__ out, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = lrow[sub[j].offN + sub[j].nN] - lrow[sub[j].offN];
+}
+
 __global__ void k_clear_p(int32_t* __restrict__ spj, const int32_t* __restrict__ skip, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n && !skip[j]) spj[j] = 0;
@@ -695,27 +701,97 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaMemcpyAsync(hc.data(), ncols, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
     if (skip) GENEO_CUDA(cudaMemcpyAsync(hk.data(), skip, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
     GENEO_CUDA(cudaStreamSynchronize(st));
+    double fl = 0.0, by = 0.0;
+    const double esz = f32 ? 4.0 : 8.0;
     for (int j = 0; j < N; ++j)
-      if (!hk[j]) h->eig_flops += kflops[j] * hc[j];
+      if (!hk[j] && hc[j] > 0) {
+        fl += kflops[j] * hc[j];
+        by += 2.0 * esz * band_entries(h->hsub[j].nN, h->hsub[j].wK) + 16.0 * h->hsub[j].nN * hc[j];
+      }
+    h->eig_flops += fl;
+    const int pr = h->prof.begin(GENEO_PROF_EIG_SOLVE, fl, by, st);
     evs.start(st);
     geneo_status_t r = solveK_raw(xoff, ncols, skip);
+    h->prof.end(pr, st);
     evs.stop();
     h->eig_ms = evs.ms;
     return r;
   };
+  // --- profile mode: host copies of the per-subdomain widths of a launch
+  const bool prof = h->prof.on;
+  std::vector<int64_t> hnnz(N, 0);
+  if (prof) {
+    int64_t* dnnz = nullptr;
+    GENEO_TRY(tmp.get(&dnnz, (size_t)N));
+    k_sub_nnz<<<ceil_div(N, 128), 128, 0, st>>>(h->dsub, asmb.lrow, dnnz, N); note_launch();
+    GENEO_CUDA(cudaMemcpyAsync(hnnz.data(), dnnz, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+  }
+  // widths of a column reference per subdomain (0 for skipped subdomains)
+  auto host_widths = [&](const ColRef& R, const int32_t* skip, std::vector<int>& out) -> geneo_status_t {
+    out.assign(N, R.w);
+    std::vector<int32_t> t(N), sk(N, 0);
+    if (skip) GENEO_CUDA(cudaMemcpyAsync(sk.data(), skip, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+    for (const int32_t* src : {R.wd, R.wd2}) {
+      if (!src) continue;
+      GENEO_CUDA(cudaMemcpyAsync(t.data(), src, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+      GENEO_CUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j) out[j] += t[j];
+    }
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < N; ++j) if (sk[j]) out[j] = 0;
+    return GENEO_OK;
+  };
   auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip) -> geneo_status_t {
+    double fl = 0.0, by = 0.0;
+    if (prof) {
+      std::vector<int> wa, wb;
+      GENEO_TRY(host_widths(A, skip, wa));
+      GENEO_TRY(host_widths(B, skip, wb));
+      for (int j = 0; j < N; ++j) {
+        const double n = h->hsub[j].nN;
+        fl += sym ? n * wa[j] * (wa[j] + 1.0) : 2.0 * n * wa[j] * wb[j];
+        by += 8.0 * n * (wa[j] + (sym ? 0 : wb[j]));
+      }
+    }
+    const int pr = h->prof.begin(GENEO_PROF_GRAM, fl, by, st);
     k_gram_part<<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
     k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
+    h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
   auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
                   double beta, const int32_t* skip) -> geneo_status_t {
+    double fl = 0.0, by = 0.0;
+    if (prof) {
+      std::vector<int> wa, wc;
+      GENEO_TRY(host_widths(A, skip, wa));
+      GENEO_TRY(host_widths(C, skip, wc));
+      for (int j = 0; j < N; ++j) {
+        const double n = h->hsub[j].nN;
+        fl += 2.0 * n * wa[j] * wc[j];
+        by += 8.0 * n * (wa[j] + wc[j] * (beta == 0.0 ? 1.0 : 2.0));
+      }
+    }
+    const int pr = h->prof.begin(GENEO_PROF_GEMM, fl, by, st);
     k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip); note_launch();
+    h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
   auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip) {
+    double fl = 0.0, by = 0.0;
+    if (prof) {
+      std::vector<int> wx;
+      if (host_widths(X, skip, wx) != GENEO_OK) wx.assign(N, 0);
+      const double nm = (withK && withB) ? 2.0 : 1.0;
+      for (int j = 0; j < N; ++j) {
+        fl += 2.0 * nm * (double)hnnz[j] * wx[j];
+        by += (double)hnnz[j] * (4.0 + 8.0 * nm) + 8.0 * h->hsub[j].nN * wx[j] * (1.0 + nm);
+      }
+    }
+    const int pr = h->prof.begin(GENEO_PROF_SPMM, fl, by, st);
     if (withK && withB) {
       k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
     } else if (withK) {
@@ -724,6 +800,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
     }
     note_launch();
+    h->prof.end(pr, st);
   };
 
   // Column references
@@ -745,13 +822,13 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_TRY(solveK(xoffX, sj, skip));
     spmm(true, false, Xr, KXr, KXr, skip);
     GENEO_TRY(gram(Xr, KXr, 1, skip));
-    k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip); note_launch();
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, skip));
     k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, skip); note_launch();
     k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     spmm(false, true, Xr, BXr, BXr, skip);
     GENEO_TRY(gram(Xr, BXr, 1, skip));
-    k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip); note_launch();
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
     k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
@@ -778,14 +855,17 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       for (int j = 0; j < N; ++j) hq[j] = hxoff[j] + (int64_t)hsj[j] * h->hsub[j].nN;
       GENEO_CUDA(cudaMemcpyAsync(xoffQ, hq.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
       GENEO_TRY(solveK(xoffQ, aj, done));
-      // Q = [W, P]: K-orthogonalise against X, SVQB; once more each
+      // Q = [W, P]: K-orthogonalise against X and K-orthonormalise by SVQB,
+      // twice.  SVQB's rescaling of nearly dependent directions amplifies the
+      // residual X-components a single round leaves, and the Rayleigh-Ritz
+      // step below assumes a K-orthonormal [X, Q].
       for (int pass = 0; pass < 2; ++pass) {
         spmm(true, false, Qr, KQr, KQr, done);
         GENEO_TRY(gram(Xr, KQr, 0, done));
         GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
         spmm(true, false, Qr, KQr, KQr, done);
         GENEO_TRY(gram(Qr, KQr, 1, done));
-        k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch();
+        { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch(); h->prof.end(prs, st); }
         GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
         k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
         k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
@@ -794,7 +874,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // Rayleigh-Ritz on S = [X, Q]
       spmm(false, true, Sr, BSr, BSr, done);
       GENEO_TRY(gram(Sr, BSr, 1, done));
-      k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch();
+      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
       k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();

@@ -229,6 +229,15 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   by += 8.0 * (2.0 * (double)n + 3.0 * sumD);  // r, z, gathered r, u written and read
   h->apply_flops = fl;
   h->apply_bytes = by;
+  double lfl = 0.0, lby = 0.0;
+  for (const SubDesc& d : h->hsub) {
+    lfl += band_solve_flops(d.nD, d.wA);
+    lby += 2.0 * esz * band_entries(d.nD, d.wA) + 8.0 * 4.0 * d.nD;  // factor twice; u in, out each sweep
+  }
+  h->local_solve_flops = lfl;
+  h->local_solve_bytes = lby;
+  h->spmv_flops = 2.0 * (double)h->nnz;
+  h->spmv_bytes = 12.0 * (double)h->nnz + 8.0 * (double)n + 24.0 * (double)n;
   return GENEO_OK;
 }
 
@@ -240,16 +249,21 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
   if (h->dimH > 0) {
     GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
     GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    const int pc = h->prof.begin(GENEO_PROF_COARSE_SOLVE, band_solve_flops(h->dimH, h->wH),
+                                 2.0 * 8.0 * band_entries(h->dimH, h->wH) + 16.0 * h->dimH, h->aux);
     GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr,
                                  h->dstat, h->aux));
+    h->prof.end(pc, h->aux);
     GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   }
+  const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
   if (h->fp32)
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
                                 nullptr, nullptr, h->dstat, s));
   else
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
                                  nullptr, nullptr, h->dstat, s));
+  h->prof.end(pl, s);
   if (h->dimH > 0) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
   k_prolong<<<grid, kT, 0, s>>>(h->n, h->dir, r, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
@@ -307,7 +321,11 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
   double rel = 1.0;
   bool breakdown = false;
   while (rel > tol && it < maxit) {
-    k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red); note_launch();
+    {
+      const int pv = h->prof.begin(GENEO_PROF_SPMV, h->spmv_flops, h->spmv_bytes, s);
+      k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red); note_launch();
+      h->prof.end(pv, s);
+    }
     k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 1, da, db, it); note_launch();
     k_update_xr<<<gridv, kT, 0, s>>>(n, h->scal, h->p, h->q, x, h->r, h->red); note_launch();
     k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 2, da, db, it); note_launch();
@@ -340,6 +358,7 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
     info->resid_hist_len = std::min(hist_len, info->resid_hist ? info->resid_hist_cap : 0);
   }
   GENEO_TRY(check_status(h, s));
+  h->prof.collect();
   if (breakdown) return GENEO_ERR_BREAKDOWN;
   if (rel > tol) return GENEO_ERR_PCG_NOCONV;
   return GENEO_OK;

@@ -23,6 +23,9 @@ GENEO_EIG_FULL = 1
 GENEO_PREC_FP64 = 0
 GENEO_PREC_FP32 = 1
 
+PROF_FAMILIES = ["factor", "eig_solve", "gram", "spmm", "gemm", "small_eig", "local_solve",
+                 "coarse_solve", "spmv", "other"]
+
 STATUS = {
     0: "GENEO_OK", 1: "GENEO_ERR_ARG", 2: "GENEO_ERR_OOM", 3: "GENEO_ERR_NOT_SPD",
     4: "GENEO_ERR_EIG_NOCONV", 5: "GENEO_ERR_PCG_NOCONV", 6: "GENEO_ERR_BREAKDOWN",
@@ -51,7 +54,7 @@ class geneo_options_t(C.Structure):
         ("tau", C.c_double), ("sigma", C.c_double), ("eig_tol", C.c_double),
         ("nev_max", C.c_int32), ("fixed_nev", C.c_int32), ("eig_form", C.c_int32),
         ("eig_maxit", C.c_int32), ("guard", C.c_int32), ("precision", C.c_int32),
-        ("seed", C.c_uint64),
+        ("profile", C.c_int32), ("seed", C.c_uint64),
     ]
 
 
@@ -70,6 +73,8 @@ class geneo_coarse_info_t(C.Structure):
         ("setup_ms", C.c_double * 8), ("factor_flops", C.c_double), ("factor_event_ms", C.c_double),
         ("eigsolve_flops", C.c_double), ("eigsolve_event_ms", C.c_double),
         ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
+        ("prof_ms", C.c_double * 10), ("prof_flops", C.c_double * 10), ("prof_bytes", C.c_double * 10),
+        ("prof_launches", C.c_int64 * 10),
     ]
 
 
@@ -211,7 +216,9 @@ def geneo_query(h):
             "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms),
             "factor_flops": q.factor_flops, "factor_event_ms": q.factor_event_ms,
             "eigsolve_flops": q.eigsolve_flops, "eigsolve_event_ms": q.eigsolve_event_ms,
-            "apply_flops": q.apply_flops, "apply_bytes": q.apply_bytes}
+            "apply_flops": q.apply_flops, "apply_bytes": q.apply_bytes,
+            "prof": {name: {"ms": q.prof_ms[i], "flops": q.prof_flops[i], "bytes": q.prof_bytes[i],
+                            "launches": q.prof_launches[i]} for i, name in enumerate(PROF_FAMILIES)}}
 
 
 def geneo_get_subdomain(h, j):
