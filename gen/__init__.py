@@ -19,6 +19,8 @@ from .problems import (  # noqa: F401
     structured_mesh,
     box_partition,
     darcy_problem,
+    uneven_darcy_problem,
+    kd_partition,
     elasticity_problem,
     kappa_channels_2d,
     kappa_skyscrapers_2d,

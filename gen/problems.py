@@ -179,6 +179,36 @@ def box_partition(nel, parts, overlap):
     return cores, grown
 
 
+def kd_partition(nel, n_parts, min_side, max_side, seed):
+    """Irregular box partition by recursive bisection (k-d splits).
+
+    The box with the longest side that can still be split is cut at a
+    seeded random position so that both halves keep sides >= min_side, until
+    n_parts boxes exist or no box can be split; boxes with a side above
+    max_side are split first.  Returns a list of (lo, hi) element boxes."""
+    rng = np.random.default_rng(seed)
+    boxes = [(tuple(0 for _ in nel), tuple(nel))]
+    while len(boxes) < n_parts:
+        best, bd, blen = -1, -1, 0
+        for i, (lo, hi) in enumerate(boxes):
+            for d in range(len(nel)):
+                L = hi[d] - lo[d]
+                score = L + (10 ** 6 if L > max_side else 0)
+                if L >= 2 * min_side and score > blen:
+                    best, bd, blen = i, d, score
+        if best < 0:
+            break
+        lo, hi = boxes.pop(best)
+        L = hi[bd] - lo[bd]
+        cut = lo[bd] + int(rng.integers(min_side, L - min_side + 1))
+        hi1 = list(hi); hi1[bd] = cut
+        lo2 = list(lo); lo2[bd] = cut
+        boxes.append((lo, tuple(hi1)))
+        boxes.append((tuple(lo2), hi))
+    boxes.sort(key=lambda b: (b[0][::-1], b[1][::-1]))
+    return boxes
+
+
 def _box_ids(lo, hi, strides):
     grids = np.meshgrid(*[np.arange(lo[d], hi[d]) for d in range(len(lo))][::-1], indexing="ij")
     ids = np.zeros(grids[0].size, dtype=np.int64)
@@ -240,7 +270,7 @@ def _assemble(elem_dofs, elem_mats, n):
 
 
 def _finish(dim, nel, ndn, elem_nodes, elem_mats, load, dir_nodes_mask, dir_values,
-            parts, overlap, h, coeff, name):
+            parts, overlap, h, coeff, name, cores=None, overlaps=None):
     nn = [v + 1 for v in nel]
     n_nodes = int(np.prod(nn))
     n = ndn * n_nodes
@@ -272,7 +302,12 @@ def _finish(dim, nel, ndn, elem_nodes, elem_mats, load, dir_nodes_mask, dir_valu
     a.indptr = a.indptr.astype(np.int64)
     a.indices = a.indices.astype(np.int32)
     # partition
-    cores, grown = box_partition(nel, parts, overlap)
+    if cores is None:
+        cores, grown = box_partition(nel, parts, overlap)
+    else:
+        ovs = overlaps if overlaps is not None else [overlap] * len(cores)
+        grown = [(tuple(max(0, lo[d] - o) for d in range(dim)),
+                  tuple(min(nel[d], hi[d] + o) for d in range(dim))) for (lo, hi), o in zip(cores, ovs)]
     estrides = [1, nel[0], nel[0] * (nel[1] if dim > 1 else 1)]
     nstrides = [1, nn[0], nn[0] * (nn[1] if dim > 1 else 1)]
     se_ptr, se, sd_ptr, sdv = [0], [], [0], []
@@ -305,7 +340,8 @@ def _boundary_node_mask(nel, faces):
     return mask, idx
 
 
-def darcy_problem(nel, kappa, parts, overlap, dirichlet="all", f=1.0, name="darcy"):
+def darcy_problem(nel, kappa, parts, overlap, dirichlet="all", f=1.0, name="darcy", cores=None,
+                  overlaps=None):
     """Q1 Darcy -div(kappa grad u) = f on the unit square/cube (Section 2, eq. 2).
 
     ``kappa``: per-element coefficient, shape ``nel`` (x fastest in the flat
@@ -332,7 +368,24 @@ def darcy_problem(nel, kappa, parts, overlap, dirichlet="all", f=1.0, name="darc
     else:
         raise ValueError(dirichlet)
     return _finish(dim, nel, 1, elem_nodes, elem_mats, load, mask, vals, parts, overlap, h,
-                   kflat, name)
+                   kflat, name, cores, overlaps)
+
+
+def uneven_darcy_problem(nel, n_parts, min_side, max_side, seed=3, contrast_range=(1e4, 1e8),
+                         overlap_range=(1, 3), name="uneven"):
+    """3D Darcy on an irregular k-d box partition with per-box overlap drawn
+    from overlap_range and, per box, one inclusion of log-uniform contrast in
+    contrast_range (uneven subdomain sizes for batching)."""
+    rng = np.random.default_rng(seed)
+    cores = kd_partition(nel, n_parts, min_side, max_side, seed)
+    overlaps = [int(rng.integers(overlap_range[0], overlap_range[1] + 1)) for _ in cores]
+    kap = np.ones(nel[::-1])
+    for lo, hi in cores:
+        c = 10.0 ** rng.uniform(np.log10(contrast_range[0]), np.log10(contrast_range[1]))
+        a = [int(rng.integers(lo[d], max(lo[d] + 1, hi[d] - 1))) for d in range(3)]
+        b = [min(hi[d], a[d] + int(rng.integers(1, max(2, (hi[d] - lo[d]) // 2)))) for d in range(3)]
+        kap[a[2]:b[2], a[1]:b[1], a[0]:b[0]] = c
+    return darcy_problem(nel, kap, None, None, cores=cores, overlaps=overlaps, name=name)
 
 
 def elasticity_problem(nel, parts, overlap, layer_thickness=2, body_force=(0.0, 0.0, -1.0),

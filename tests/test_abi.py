@@ -71,3 +71,17 @@ def test_grow_partition_matches_box_growth():
         q = gen.darcy_problem(nel, kap, parts, ov)
         assert np.array_equal(ep, q.sub_elem_ptr) and np.array_equal(el, q.sub_elem)
         assert np.array_equal(dp, q.sub_dof_ptr) and np.array_equal(dl, q.sub_dof)
+
+
+def test_option_limits_rejected_without_gpu():
+    """Options outside the supported range return GENEO_ERR_ARG before any
+    device work (nev_max > 34, sigma >= 0, unknown precision)."""
+    import ctypes as C
+    geneo, lib = _lib()
+    p = gen.darcy_problem((4, 4), np.ones((4, 4)), (1, 1), 0)
+    arrs = geneo.problem_arrays(p)
+    prob = geneo.make_problem(arrs, p.n, p.n_sub, 4, 1, geneo.GENEO_MEM_HOST)
+    for kw in ({"nev_max": 35}, {"sigma": 0.0}, {"precision": 7}, {"eig_form": 3}):
+        o = geneo.geneo_default_options(**kw)
+        h = C.c_void_p()
+        assert lib.geneo_setup(C.byref(prob), C.byref(o), None, C.byref(h)) == 1, kw

@@ -1,0 +1,59 @@
+"""Parity at the benchmark's full size (3D Darcy 128^3, 512 subdomains), in
+the launch configuration bench.py times (mixed path, FP32 factors): sampled
+subdomains against the oracle's ARPACK eigensolves, properties at full size
+(partition of unity sums to one, unit coarse vectors), and the true residual
+of the solution."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    kap = gen.kappa_grf_layers_3d((128, 128, 128), seed=1)
+    return gen.darcy_problem((128, 128, 128), kap, (8, 8, 8), 2)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_darcy_128_sampled_parity(c2, precision):
+    import torch
+    from paper_1906_10944_gb300 import geneo as G
+    prob = c2
+    sol = G.GenEO(prob, nev_max=20, tau=0.3, precision=precision)
+    try:
+        # properties over all subdomains
+        s = np.zeros(prob.n)
+        for j in range(prob.n_sub):
+            g = sol.subdomain(j)
+            N = prob.sub_dofs(j)
+            s[N] += g["pu"]
+            if g["m"]:
+                assert np.allclose(np.linalg.norm(g["Z"], axis=0), 1.0, atol=1e-12)
+        free = prob.dirichlet == 0
+        assert np.abs(s[free] - 1.0).max() < 1e-12 and np.all(s[~free] == 0.0)
+        # sampled subdomains: interior, face, edge, corner
+        sets = oracle.subdomain_sets(prob)
+        e_tau = oracle.element_multiplicity(prob)
+        _, xs = oracle.partition_of_unity(prob, sets)
+        for j in (0, 7, 73, 273):
+            g = sol.subdomain(j)
+            assert np.array_equal(g["D"], sets[j]["D"].astype(np.int32))
+            At, B = oracle.geneo_pencil(prob, j, sets, xs, e_tau)
+            lo, _ = oracle.local_eigenpairs(At, B, 25, -0.01, 0)
+            m_or = oracle.select_count(lo, 0.3, 20)
+            assert g["m"] == m_or or np.any(np.abs(lo[:21] - 0.3) <= 3e-7), (j, g["m"], m_or)
+            m = min(g["m"], m_or)
+            assert np.all(np.abs(g["lambda"][:m] - lo[:m]) <= 1e-6 * np.maximum(np.abs(lo[:m]), 3e-4)), j
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros_like(b)
+        info = sol.solve(b, x, tol=1e-8, maxit=2000)
+        xr = x.cpu().numpy()
+        res = np.linalg.norm(prob.b - prob.A @ xr) / np.linalg.norm(prob.b)
+        assert info["converged"] and res <= 1.01e-8
+        assert 30 <= info["iterations"] <= 120
+    finally:
+        sol.close()

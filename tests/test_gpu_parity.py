@@ -192,3 +192,11 @@ def test_mixed_precision_matches_oracle(case):
         assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
     finally:
         sol.close()
+
+
+def test_uneven_batch_darcy_3d():
+    """Uneven batching: an irregular k-d box partition (sides 3..8 elements,
+    overlap 1..3 per box, one inclusion of contrast 1e4..1e8 per box), so the
+    batch mixes subdomain sizes and band widths; FP64 parity as above."""
+    prob = gen.uneven_darcy_problem((24, 20, 18), 24, 3, 8, seed=3)
+    _full_check(prob, nev=8)
