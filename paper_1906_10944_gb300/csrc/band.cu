@@ -32,12 +32,23 @@ constexpr int kThreads = 256;
 template <typename T>
 __device__ __forceinline__ bool finite_pos(T v) { return v > T(0) && isfinite(v); }
 
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void load4(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* o) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 c = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+}
+
 __device__ __forceinline__ int64_t bidx(int r, int c, int w, int64_t ld) {
   return (int64_t)r * ld + (c - r + w);
 }
 
 template <typename T, int NB, bool SMEMP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
 k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax,
              DevStatus* st) {
   const BandDesc d = descs[blockIdx.x];
@@ -118,6 +129,13 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
         }
       }
     }
+    if (SMEMP) {
+      const int h4 = (h + 3) & ~3;
+      for (int idx = tid; idx < b * (h4 - h); idx += nt) {
+        const int t = idx / (h4 - h), i = h + idx % (h4 - h);
+        Ps[t * phmax + i] = T(0);
+      }
+    }
     __syncthreads();
     // 5. trailing update of the h x h window, 4x4 register tiles
     //    (consecutive threads take consecutive column tiles of one row tile)
@@ -132,13 +150,18 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
         for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
       for (int t = 0; t < b; ++t) {
         T pr[4], pc[4];
+        if (SMEMP) {
+          // the panel rows beyond h are zero in shared memory (phmax >= h
+          // rounded up to 4), so whole 4-vectors can be read: pr is the same
+          // address for the warp (broadcast), pc one 16-byte vector per thread
+          const T* prow = Ps + (size_t)t * phmax;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = 4 * ti + q, j = 4 * tj + q;
-          if (SMEMP) {
-            pr[q] = (i < h) ? Ps[t * phmax + i] : T(0);
-            pc[q] = (j < h) ? Ps[t * phmax + j] : T(0);
-          } else {
+          for (int q = 0; q < 4; ++q) pr[q] = prow[4 * ti + q];
+          load4(prow + 4 * tj, pc);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = 4 * ti + q, j = 4 * tj + q;
             pr[q] = (i < h && b + i - t <= w) ? L[bidx(kb + b + i, kb + t, w, ld)] : T(0);
             pc[q] = (j < h && b + j - t <= w) ? L[bidx(kb + b + j, kb + t, w, ld)] : T(0);
           }
@@ -443,13 +466,16 @@ template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, DevStatus* st,
                           cudaStream_t s) {
   if (count <= 0) return GENEO_OK;
+  // the panel starts at a 16-byte boundary (diag block: 32 x 33 values) and
+  // its row stride phmax is a multiple of 4
   const size_t diag = (size_t)kNB * (kNB + 1) * sizeof(T);
-  const size_t panel = (size_t)max_w * kNB * sizeof(T);
+  const int phmax = (max_w + 3) & ~3;
+  const size_t panel = (size_t)phmax * kNB * sizeof(T);
   if (diag + panel <= kSmemCap) {
     auto kern = k_band_potrf<T, kNB, true>;
     GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(diag + panel)));
-    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, max_w, st); note_launch();
+    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, phmax, st); note_launch();
   } else {
     auto kern = k_band_potrf<T, kNB, false>;
     kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st); note_launch();
