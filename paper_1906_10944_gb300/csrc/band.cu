@@ -232,16 +232,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // rows per streamed block: 16, or 4 for bands too wide for 16-row stages
-// pipeline depth: three stages for FP32 factors, two for FP64 (room for the
-// right-hand-side ring)
-template <typename T> struct Stages { static constexpr int v = 3; };
-template <> struct Stages<double> { static constexpr int v = 2; };
+// pipeline depth of the multi-right-hand-side solve: two stages leave room
+// for the right-hand-side ring and two blocks per SM
+template <typename T> struct Stages { static constexpr int v = 2; };
 
 // Block v of the visit order 0..nb-1 (forward), nb-1..0 (backward).
 __device__ __forceinline__ int visit_block(int v, int nb) { return v < nb ? v : 2 * nb - 1 - v; }
 
 template <typename T, int kSNB, int kMaxRhsPerWarp, int kStages>
-__global__ void __launch_bounds__(kThreads, kMaxRhsPerWarp == 1 ? (sizeof(T) == 4 ? 4 : 2) : 1)
+__global__ void __launch_bounds__(kThreads, kMaxRhsPerWarp == 1 ? (sizeof(T) == 4 ? 4 : 2) : 2)
 k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
              double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
              const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,

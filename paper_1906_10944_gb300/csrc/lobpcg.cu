@@ -688,12 +688,13 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   std::vector<double> kflops(N);
   for (int j = 0; j < N; ++j) kflops[j] = band_solve_flops(h->hsub[j].nN, h->hsub[j].wK);
   h->eig_flops = 0.0;
-  auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
+  auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip,
+                        int kmax) -> geneo_status_t {
     if (f32)
-      return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, s * 2,
+      return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
                                ncols, skip, h->dstat, st);
     return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
-                              s * 2, ncols, skip, h->dstat, st);
+                              kmax, ncols, skip, h->dstat, st);
   };
   // timed with CUDA events; flops from the per-subdomain column counts
   auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
@@ -703,6 +704,9 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaStreamSynchronize(st));
     double fl = 0.0, by = 0.0;
     const double esz = f32 ? 4.0 : 8.0;
+    int kmax = 0;
+    for (int j = 0; j < N; ++j)
+      if (!hk[j]) kmax = std::max(kmax, (int)hc[j]);
     for (int j = 0; j < N; ++j)
       if (!hk[j] && hc[j] > 0) {
         fl += kflops[j] * hc[j];
@@ -711,7 +715,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     h->eig_flops += fl;
     const int pr = h->prof.begin(GENEO_PROF_EIG_SOLVE, fl, by, st);
     evs.start(st);
-    geneo_status_t r = solveK_raw(xoff, ncols, skip);
+    geneo_status_t r = kmax > 0 ? solveK_raw(xoff, ncols, skip, kmax) : GENEO_OK;
     h->prof.end(pr, st);
     evs.stop();
     h->eig_ms = evs.ms;
