@@ -222,7 +222,7 @@ def measured_peaks():
 FAMILY_BOUND = {
     "factor": "alu-factor", "eig_solve": "alu-factor", "gram": "alu-fp64", "spmm": "alu-fp64",
     "gemm": "alu-fp64", "small_eig": "alu-fp64", "local_solve": "hbm", "coarse_solve": "alu-fp64",
-    "spmv": "hbm",
+    "spmv": "hbm", "ortho32": "hbm",
 }
 
 

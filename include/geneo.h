@@ -171,6 +171,23 @@ typedef struct {
   int32_t resid_hist_len;
 } geneo_solve_info_t;
 
+/* Kernel families of geneo_coarse_info_t.prof_*. */
+enum {
+  GENEO_PROF_FACTOR = 0,       /* batched banded Cholesky (A_j, K_j, A_H) */
+  GENEO_PROF_EIG_SOLVE = 1,    /* eigensolver block solves with K_j */
+  GENEO_PROF_GRAM = 2,         /* eigensolver Gram matrices (FP64) */
+  GENEO_PROF_SPMM = 3,         /* eigensolver sparse products with K_j, B_j */
+  GENEO_PROF_GEMM = 4,         /* eigensolver block updates (FP64) */
+  GENEO_PROF_SMALL_EIG = 5,    /* Jacobi SVQB and Rayleigh-Ritz */
+  GENEO_PROF_LOCAL_SOLVE = 6,  /* preconditioner local solves L_j L_j^T u = r_j */
+  GENEO_PROF_COARSE_SOLVE = 7, /* preconditioner coarse solve */
+  GENEO_PROF_SPMV = 8,         /* PCG sparse matrix-vector product */
+  GENEO_PROF_OTHER = 9,
+  GENEO_PROF_ORTHO32 = 10,     /* eigensolver first K-orthogonalisation pass in
+                                  FP32 arithmetic (FP32 factors only) */
+  GENEO_PROF_COUNT = 11
+};
+
 /* Setup summary (host copies). */
 typedef struct {
   int32_t n_sub;
@@ -197,25 +214,12 @@ typedef struct {
    * CUDA-event milliseconds on the launching stream, launches, and the
    * algorithmic flops and bytes of those launches (setup and every
    * apply/solve on the handle so far). */
-  double prof_ms[10];
-  double prof_flops[10];
-  double prof_bytes[10];
-  int64_t prof_launches[10];
+  double prof_ms[GENEO_PROF_COUNT];
+  double prof_flops[GENEO_PROF_COUNT];
+  double prof_bytes[GENEO_PROF_COUNT];
+  int64_t prof_launches[GENEO_PROF_COUNT];
 } geneo_coarse_info_t;
 
-/* Kernel families of geneo_coarse_info_t.prof_*. */
-enum {
-  GENEO_PROF_FACTOR = 0,       /* batched banded Cholesky (A_j, K_j, A_H) */
-  GENEO_PROF_EIG_SOLVE = 1,    /* eigensolver block solves with K_j */
-  GENEO_PROF_GRAM = 2,         /* eigensolver Gram matrices (FP64) */
-  GENEO_PROF_SPMM = 3,         /* eigensolver sparse products with K_j, B_j */
-  GENEO_PROF_GEMM = 4,         /* eigensolver block updates (FP64) */
-  GENEO_PROF_SMALL_EIG = 5,    /* Jacobi SVQB and Rayleigh-Ritz */
-  GENEO_PROF_LOCAL_SOLVE = 6,  /* preconditioner local solves L_j L_j^T u = r_j */
-  GENEO_PROF_COARSE_SOLVE = 7, /* preconditioner coarse solve */
-  GENEO_PROF_SPMV = 8,         /* PCG sparse matrix-vector product */
-  GENEO_PROF_OTHER = 9
-};
 
 /* Fill *opt with the defaults listed above. */
 void geneo_default_options(geneo_options_t* opt);

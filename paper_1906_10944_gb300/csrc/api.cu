@@ -250,7 +250,7 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->apply_bytes = h->apply_bytes;
   cudaDeviceSynchronize();
   h->prof.collect();
-  for (int i = 0; i < 10; ++i) {
+  for (int i = 0; i < GENEO_PROF_COUNT; ++i) {
     info->prof_ms[i] = h->prof.ms[i];
     info->prof_flops[i] = h->prof.flops[i];
     info->prof_bytes[i] = h->prof.bytes[i];

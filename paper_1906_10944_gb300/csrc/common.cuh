@@ -80,8 +80,8 @@ struct KernelProfiler {
   bool on = false;
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
-  double ms[10] = {0}, flops[10] = {0}, bytes[10] = {0};
-  int64_t launches[10] = {0};
+  double ms[GENEO_PROF_COUNT] = {0}, flops[GENEO_PROF_COUNT] = {0}, bytes[GENEO_PROF_COUNT] = {0};
+  int64_t launches[GENEO_PROF_COUNT] = {0};
   cudaEvent_t get() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e = nullptr;

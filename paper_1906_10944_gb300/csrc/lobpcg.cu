@@ -66,6 +66,9 @@ ColRef cref(double* base, int W, int c0, const int32_t* c0d, int w, const int32_
 // ---------------------------------------------------------------------------
 // Multivector kernels (grid: x = row blocks, y = subdomain).
 // ---------------------------------------------------------------------------
+// C is the arithmetic type: double, or float for the first orthogonalisation
+// pass (operands rounded to FP32 on load, results stored as FP64).
+template <typename C>
 __global__ void __launch_bounds__(kT)
 k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
        const int32_t* __restrict__ lcol, const double* __restrict__ v1, const double* __restrict__ v2,
@@ -86,14 +89,14 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
   int c = 0;
   for (; c + 4 <= w; c += 4) {
     const double* xc = x + (int64_t)c * nn;
-    double s10 = 0, s11 = 0, s12 = 0, s13 = 0, s20 = 0, s21 = 0, s22 = 0, s23 = 0;
+    C s10 = 0, s11 = 0, s12 = 0, s13 = 0, s20 = 0, s21 = 0, s22 = 0, s23 = 0;
     for (int64_t e = e0; e < e1; ++e) {
       const int col = lcol[e];
-      const double x0 = xc[col], x1 = xc[nn + col], x2 = xc[2 * nn + col], x3 = xc[3 * nn + col];
-      const double va = v1[e];
+      const C x0 = (C)xc[col], x1 = (C)xc[nn + col], x2 = (C)xc[2 * nn + col], x3 = (C)xc[3 * nn + col];
+      const C va = (C)v1[e];
       s10 += va * x0; s11 += va * x1; s12 += va * x2; s13 += va * x3;
       if (v2) {
-        const double vb = v2[e];
+        const C vb = (C)v2[e];
         s20 += vb * x0; s21 += vb * x1; s22 += vb * x2; s23 += vb * x3;
       }
     }
@@ -104,11 +107,11 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
   }
   for (; c < w; ++c) {
     const double* xc = x + (int64_t)c * nn;
-    double s1 = 0.0, s2 = 0.0;
+    C s1 = 0, s2 = 0;
     for (int64_t e = e0; e < e1; ++e) {
-      const double xv = xc[lcol[e]];
-      s1 += v1[e] * xv;
-      if (v2) s2 += v2[e] * xv;
+      const C xv = (C)xc[lcol[e]];
+      s1 += (C)v1[e] * xv;
+      if (v2) s2 += (C)v2[e] * xv;
     }
     y1[c * nn + a] = s1;
     if (v2) y2[c * nn + a] = s2;
@@ -135,6 +138,7 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef 
 // several row groups (thread g of a tile takes rows g, g + groups, ... of
 // every staged chunk) and the groups' partials are summed in a fixed order at
 // the end, so all warps issue FP64 FMAs.
+template <typename C>
 __global__ void __launch_bounds__(kT, 2)
 k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double* __restrict__ Gp,
             int ldg, int nsub, const int32_t* __restrict__ skip) {
@@ -146,9 +150,9 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
   if (p <= 0 || q <= 0) return;
   const double* a = cr_ptr(A, d, j);
   const double* b = cr_ptr(B, d, j);
-  extern __shared__ double gsm[];
-  double* As = gsm;                         // [kRB][kMaxW + 1]
-  double* Bs = gsm + kRB * (kMaxW + 1);     // [kRB][kMaxW + 1]
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  C* As = reinterpret_cast<C*>(gsm_raw);   // [kRB][kMaxW + 1]
+  C* Bs = As + kRB * (kMaxW + 1);          // [kRB][kMaxW + 1]
   constexpr int LDS = kMaxW + 1;
   const int tp = (p + 3) >> 2, tq = (q + 3) >> 2;
   // tiles: full tp x tq grid, or its lower triangle (ti >= tj) when sym
@@ -177,22 +181,22 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
       tj = t / tp;
     }
   };
-  double acc[3][16];
+  C acc[3][16];
 #pragma unroll
   for (int u = 0; u < 3; ++u)
 #pragma unroll
-    for (int z = 0; z < 16; ++z) acc[u][z] = 0.0;
+    for (int z = 0; z < 16; ++z) acc[u][z] = 0;
   const int r0 = (int)((int64_t)rs * d.nN / kRS), r1 = (int)((int64_t)(rs + 1) * d.nN / kRS);
   for (int rb = r0; rb < r1; rb += kRB) {
     const int nr = min(kRB, r1 - rb);
     __syncthreads();
     for (int idx = threadIdx.x; idx < kRB * p; idx += kT) {
       const int r = idx % kRB, c = idx / kRB;
-      As[r * LDS + c] = r < nr ? a[(int64_t)c * d.nN + rb + r] : 0.0;
+      As[r * LDS + c] = r < nr ? (C)a[(int64_t)c * d.nN + rb + r] : (C)0;
     }
     for (int idx = threadIdx.x; idx < kRB * q; idx += kT) {
       const int r = idx % kRB, c = idx / kRB;
-      Bs[r * LDS + c] = r < nr ? b[(int64_t)c * d.nN + rb + r] : 0.0;
+      Bs[r * LDS + c] = r < nr ? (C)b[(int64_t)c * d.nN + rb + r] : (C)0;
     }
     __syncthreads();
     const int rstart = groups > 1 ? g : 0;
@@ -202,11 +206,11 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
       int ti, tj;
       tile_rc(own[u], ti, tj);
       for (int r = rstart; r < nr; r += groups) {
-        double av[4], bv[4];
+        C av[4], bv[4];
 #pragma unroll
         for (int z = 0; z < 4; ++z) {
-          av[z] = (4 * ti + z < p) ? As[r * LDS + 4 * ti + z] : 0.0;
-          bv[z] = (4 * tj + z < q) ? Bs[r * LDS + 4 * tj + z] : 0.0;
+          av[z] = (4 * ti + z < p) ? As[r * LDS + 4 * ti + z] : (C)0;
+          bv[z] = (4 * tj + z < q) ? Bs[r * LDS + 4 * tj + z] : (C)0;
         }
 #pragma unroll
         for (int z = 0; z < 4; ++z)
@@ -218,7 +222,7 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
   if (groups > 1) {
     // sum the row groups' partials: group-major in shared memory
     __syncthreads();
-    double* red = gsm;  // groups * ntiles * 16 <= kT * 16 doubles
+    double* red = reinterpret_cast<double*>(gsm_raw);  // groups * ntiles * 16 <= kT * 16
     if (own[0] >= 0)
 #pragma unroll
       for (int z = 0; z < 16; ++z) red[((size_t)g * ntiles + own[0]) * 16 + z] = acc[0][z];
@@ -268,33 +272,35 @@ __global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRef A, ColRef 
 
 // C = beta*C + alpha * A * T, T = rows [t0 + t0d[j], ...) of a per-subdomain
 // ldg x ldg matrix (column-major).  p = width(A), q = width(C).
+template <typename C>
 __global__ void __launch_bounds__(kT)
 k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
-          int t0, const int32_t* __restrict__ t0d, ColRef C, double alpha, double beta,
+          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
           const int32_t* __restrict__ skip) {
   const int j = blockIdx.y;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
-  const int p = cr_w(A, j), q = cr_w(C, j);
+  const int p = cr_w(A, j), q = cr_w(Cout, j);
   if (q <= 0) return;
-  extern __shared__ double Ts[];  // p x q, Ts[i*q + c]
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  C* Ts = reinterpret_cast<C*>(ts_raw);  // p x q, Ts[i*q + c]
   const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
   for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
     const int i = idx % p, c = idx / p;
-    Ts[i * q + c] = T[(int64_t)c * ldg + i];
+    Ts[i * q + c] = (C)T[(int64_t)c * ldg + i];
   }
   __syncthreads();
   const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
   if (a_row >= d.nN) return;
   const double* a = cr_ptr(A, d, j);
-  double* cm = cr_ptr(C, d, j);
+  double* cm = cr_ptr(Cout, d, j);
   constexpr int CB = 8;
   for (int c0 = 0; c0 < q; c0 += CB) {
-    double acc[CB];
+    C acc[CB];
 #pragma unroll
-    for (int z = 0; z < CB; ++z) acc[z] = 0.0;
+    for (int z = 0; z < CB; ++z) acc[z] = 0;
     for (int i = 0; i < p; ++i) {
-      const double av = a[(int64_t)i * d.nN + a_row];
+      const C av = (C)a[(int64_t)i * d.nN + a_row];
 #pragma unroll
       for (int z = 0; z < CB; ++z)
         if (c0 + z < q) acc[z] += av * Ts[i * q + c0 + z];
@@ -304,7 +310,7 @@ k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ 
       const int c = c0 + z;
       if (c < q) {
         double* o = cm + (int64_t)c * d.nN + a_row;
-        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc[z];
+        *o = (beta == 0.0 ? (C)0 : (C)beta * (C)*o) + (C)alpha * acc[z];
       }
     }
   }
@@ -673,8 +679,10 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
   const size_t nn_smem = sizeof(double) * kMaxW * kMaxW;
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
-  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
 
   const bool f32 = h->fp32;
   std::vector<int64_t> hxoff(N);
@@ -746,7 +754,9 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     for (int j = 0; j < N; ++j) if (sk[j]) out[j] = 0;
     return GENEO_OK;
   };
-  auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip) -> geneo_status_t {
+  // f32: FP32 arithmetic (first orthogonalisation pass), profiled as its own
+  // family
+  auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip, bool f32a = false) -> geneo_status_t {
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wa, wb;
@@ -758,15 +768,19 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
         by += 8.0 * n * (wa[j] + (sym ? 0 : wb[j]));
       }
     }
-    const int pr = h->prof.begin(GENEO_PROF_GRAM, fl, by, st);
-    k_gram_part<<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_GRAM, fl, by, st);
+    if (f32a)
+      k_gram_part<float><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
+    else
+      k_gram_part<double><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
+    note_launch();
     k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
   auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
-                  double beta, const int32_t* skip) -> geneo_status_t {
+                  double beta, const int32_t* skip, bool f32a = false) -> geneo_status_t {
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wa, wc;
@@ -778,13 +792,18 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
         by += 8.0 * n * (wa[j] + wc[j] * (beta == 0.0 ? 1.0 : 2.0));
       }
     }
-    const int pr = h->prof.begin(GENEO_PROF_GEMM, fl, by, st);
-    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip); note_launch();
+    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_GEMM, fl, by, st);
+    if (f32a)
+      k_gemm_nn<float><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+    else
+      k_gemm_nn<double><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+    note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
-  auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip) {
+  auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip,
+                  bool f32a = false) {
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wx;
@@ -795,13 +814,14 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
         by += (double)hnnz[j] * (4.0 + 8.0 * nm) + 8.0 * h->hsub[j].nN * wx[j] * (1.0 + nm);
       }
     }
-    const int pr = h->prof.begin(GENEO_PROF_SPMM, fl, by, st);
+    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_SPMM, fl, by, st);
+    auto kern = f32a ? k_spmm<float> : k_spmm<double>;
     if (withK && withB) {
-      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
+      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
     } else if (withK) {
-      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, nullptr, X, YK, YK, skip);
+      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, nullptr, X, YK, YK, skip);
     } else {
-      k_spmm<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
+      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
     }
     note_launch();
     h->prof.end(pr, st);
@@ -816,6 +836,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const ColRef Pr = cref(P, W3 / 3, 0, nullptr, 0, spj);
   const ColRef Sr = cref(S, W3, 0, nullptr, 0, sj, qj);  // [X, Q]
   const ColRef BSr = cref(BS, W3, 0, nullptr, 0, sj, qj);
+  const ColRef BQr = cref(BS, W3, 0, sj, 0, qj);
 
   // Start block for the subdomains with skip[j] == 0: X = K^{-1} B R
   // (R counter-based random), K-orthonormalised by SVQB, Rayleigh-Ritz.
@@ -863,20 +884,25 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // twice.  SVQB's rescaling of nearly dependent directions amplifies the
       // residual X-components a single round leaves, and the Rayleigh-Ritz
       // step below assumes a K-orthonormal [X, Q].
+      // X^T K Q is formed as (KX)^T Q: KX from the residual step is current.
+      // With FP32 factors the first pass runs in FP32 arithmetic (it removes
+      // the bulk of the X components); the second, FP64 pass sets the final
+      // K-orthonormality that Rayleigh-Ritz relies on.
       for (int pass = 0; pass < 2; ++pass) {
-        spmm(true, false, Qr, KQr, KQr, done);
-        GENEO_TRY(gram(Xr, KQr, 0, done));
-        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
-        spmm(true, false, Qr, KQr, KQr, done);
-        GENEO_TRY(gram(Qr, KQr, 1, done));
+        const bool a32 = f32 && pass == 0;
+        GENEO_TRY(gram(KXr, Qr, 0, done, a32));
+        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done, a32));
+        spmm(true, false, Qr, KQr, KQr, done, a32);
+        GENEO_TRY(gram(Qr, KQr, 1, done, a32));
         { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch(); h->prof.end(prs, st); }
-        GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
+        GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, a32));
         k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
         k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
         GENEO_CUDA(cudaGetLastError());
       }
-      // Rayleigh-Ritz on S = [X, Q]
-      spmm(false, true, Sr, BSr, BSr, done);
+      // Rayleigh-Ritz on S = [X, Q]; BX from the residual step is current,
+      // only BQ is new
+      spmm(false, true, Qr, BQr, BQr, done);
       GENEO_TRY(gram(Sr, BSr, 1, done));
       { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U

@@ -24,7 +24,8 @@ GENEO_PREC_FP64 = 0
 GENEO_PREC_FP32 = 1
 
 PROF_FAMILIES = ["factor", "eig_solve", "gram", "spmm", "gemm", "small_eig", "local_solve",
-                 "coarse_solve", "spmv", "other"]
+                 "coarse_solve", "spmv", "other", "ortho32"]
+NPROF = len(PROF_FAMILIES)  # GENEO_PROF_COUNT
 
 STATUS = {
     0: "GENEO_OK", 1: "GENEO_ERR_ARG", 2: "GENEO_ERR_OOM", 3: "GENEO_ERR_NOT_SPD",
@@ -73,8 +74,8 @@ class geneo_coarse_info_t(C.Structure):
         ("setup_ms", C.c_double * 8), ("factor_flops", C.c_double), ("factor_event_ms", C.c_double),
         ("eigsolve_flops", C.c_double), ("eigsolve_event_ms", C.c_double),
         ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
-        ("prof_ms", C.c_double * 10), ("prof_flops", C.c_double * 10), ("prof_bytes", C.c_double * 10),
-        ("prof_launches", C.c_int64 * 10),
+        ("prof_ms", C.c_double * NPROF), ("prof_flops", C.c_double * NPROF),
+        ("prof_bytes", C.c_double * NPROF), ("prof_launches", C.c_int64 * NPROF),
     ]
 
 
