@@ -446,6 +446,7 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   int64_t bandK_tot = 0, bandA_tot = 0;
   out.maxwK = 0;
   h->maxwA = 0;
+  h->maxnD = 0;
   for (int j = 0; j < N; ++j) {
     SubDesc& d = h->hsub[j];
     d.wK = hwK[j];
@@ -456,6 +457,7 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     bandA_tot += (int64_t)d.nD * band_ld(d.wA);
     out.maxwK = std::max(out.maxwK, d.wK);
     h->maxwA = std::max(h->maxwA, d.wA);
+    h->maxnD = std::max(h->maxnD, d.nD);
   }
   GENEO_CUDA(cudaMemcpyAsync(h->dsub, h->hsub.data(), sizeof(SubDesc) * N, cudaMemcpyHostToDevice, s));
 
@@ -470,15 +472,26 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
 
   // band storage, descriptors
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
-  GENEO_TRY(tmp.alloc(&out.bandK, esz * (size_t)std::max<int64_t>(bandK_tot, 1)));
-  GENEO_TRY(h->mem.alloc(&h->bandA, esz * (size_t)std::max<int64_t>(bandA_tot, 1)));
+  // the inverted diagonal blocks follow all bands in the same allocation
+  int64_t dinvK_tot = 0, dinvA_tot = 0;
+  int maxnK = 0;
+  for (const SubDesc& d : h->hsub) {
+    dinvK_tot += dinv_elems(d.nN);
+    dinvA_tot += dinv_elems(d.nD);
+    maxnK = std::max(maxnK, d.nN);
+  }
+  GENEO_TRY(tmp.alloc(&out.bandK, esz * (size_t)std::max<int64_t>(bandK_tot + dinvK_tot, 1)));
+  GENEO_TRY(h->mem.alloc(&h->bandA, esz * (size_t)std::max<int64_t>(bandA_tot + dinvA_tot, 1)));
   GENEO_CUDA(cudaMemsetAsync(out.bandK, 0, esz * bandK_tot, s));
   GENEO_CUDA(cudaMemsetAsync(h->bandA, 0, esz * bandA_tot, s));
   std::vector<BandDesc> bk(N), ba(N);
+  int64_t dK = bandK_tot, dA = bandA_tot;
   for (int j = 0; j < N; ++j) {
     const SubDesc& d = h->hsub[j];
-    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, band_ld(d.wK)};
-    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, band_ld(d.wA)};
+    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, band_ld(d.wK), dK};
+    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, band_ld(d.wA), dA};
+    dK += dinv_elems(d.nN);
+    dA += dinv_elems(d.nD);
   }
   // largest factorisations first: blocks are dispatched in index order, so
   // this shortens the tail of the last wave (descriptors carry their id)
@@ -528,11 +541,11 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   const int pK = h->prof.begin(GENEO_PROF_FACTOR, flK, byK, s);
   const int pA = h->prof.begin(GENEO_PROF_FACTOR, flA, byA, h->aux);
   if (h->fp32) {
-    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
-    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
+    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
+    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));
   } else {
-    GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, h->dstat, s));
-    GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->dstat, h->aux));
+    GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
+    GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));
   }
   h->prof.end(pK, s);
   h->prof.end(pA, h->aux);

@@ -43,6 +43,14 @@ __device__ __forceinline__ void load4(const double* p, double* o) {
   o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
 }
 
+__device__ __forceinline__ void store4(float* p, const float* o) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double* o) {
+  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+}
+
 __device__ __forceinline__ int64_t bidx(int r, int c, int w, int64_t ld) {
   return (int64_t)r * ld + (c - r + w);
 }
@@ -186,6 +194,38 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
   }
 }
 
+// Inverses M of the 16 x 16 diagonal blocks of a factored band (FP64
+// arithmetic, rounded to T), stored transposed (M(i, t) at 16 t + i): a
+// half-warp per block, lane c forms column c by forward substitution.  The solves apply these blocks as small products, so
+// no dependent chain of divisions sits on their sequential path.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_band_dinv(T* __restrict__ base, const BandDesc* __restrict__ descs) {
+  const BandDesc d = descs[blockIdx.y];
+  const int lane = threadIdx.x & 31, c = lane & 15;
+  const int blk = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 2 + (lane >> 4);
+  const int nb = (d.n + 15) / 16;
+  if (blk >= nb || d.dinv < 0) return;
+  const int kb = blk * 16, b = min(16, d.n - kb), w = d.w, ld = d.ld;
+  const T* L = base + d.off;
+  double x[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    double v = 0.0;
+    if (r < b && c < b && r >= c) {
+      v = r == c ? 1.0 : 0.0;
+#pragma unroll
+      for (int t = 0; t < r; ++t)
+        if (t >= c && r - t <= w) v -= (double)L[(int64_t)(kb + r) * ld + (t - r + w)] * x[t];
+      v /= (double)L[(int64_t)(kb + r) * ld + w];
+    }
+    x[r] = v;
+  }
+  T* D = base + d.dinv + (int64_t)blk * 256;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) D[c * 16 + r] = (T)x[r];
+}
+
 // ---------------------------------------------------------------------------
 // Bulk-copy pipeline helpers (cp.async.bulk + mbarrier, sm_90 and later).
 // ---------------------------------------------------------------------------
@@ -283,15 +323,17 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
     mbar_arrive_expect_tx(&bars[s], bytes);
     bulk_load(stage + (size_t)s * kSNB * ld, L + (int64_t)kb * ld, bytes, &bars[s]);
   };
+  int issued = 0;  // copies issued by thread 0
   if (tid == 0)
-    for (int v = 0; v < min(kStages - 1, nvis); ++v) issue(v);
+    for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
   bool ok = true;
+  int waited = 0;  // stages this thread has waited for
   int lo = n;  // lowest row held in the ring during the backward sweep
 
   for (int v = 0; v < nvis; ++v) {
     const int s = v % kStages;
     const uint32_t parity = (uint32_t)((v / kStages) & 1);
-    if (tid == 0 && v + kStages - 1 < nvis) issue(v + kStages - 1);
+    if (tid == 0 && ok && issued < nvis) issue(issued++);
     const int kb = visit_block(v, nb) * kSNB;
     const int b = min(kSNB, n - kb);
     if (v < nb) {
@@ -304,7 +346,10 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         const int c = wid + u * nw;
         xb[u] = (c < k && lane < b) ? (T)X[(int64_t)c * n + kb + lane] : T(0);
       }
-      if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
       const T* S = stage + (size_t)s * kSNB * ld;
       // dot products with the solved rows [kb + i - w, kb) held in the ring:
       // a (b x w) x (w x k) product; a thread owns one row and CT right-hand
@@ -390,7 +435,10 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
       if (v == nb - 1) lo = max(0, kb - w);  // the ring holds rows [lo, n) for the backward sweep
     } else {
       // ---------------- backward, block kb (right-looking on L^T)
-      if (ok) ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
       const T* S = stage + (size_t)s * kSNB * ld;
       T lcol[kSNB];
 #pragma unroll
@@ -448,6 +496,352 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
     }
     __syncthreads();
   }
+  // after a timed-out wait, let the copies still in flight land (bounded)
+  if (tid == 0 && !ok)
+    for (int v = waited; v < issued; ++v)
+      mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
+}
+
+// One right-hand side with the whole vector resident in shared memory (the
+// preconditioner's local solves and the coarse solve).  The vector is read
+// once at the start and written once at the end, so no global access sits on
+// the sequential path of the sweeps; only the factor (band rows and the
+// inverted diagonal block) streams in.  Forward block (left-looking): row i
+// of the block is a dot product over the w solved entries to its left, split
+// over a half-warp (16 segments, shuffle reduction), then the inverted
+// diagonal block is applied.  Backward block (right-looking): the transposed
+// inverse is applied, then every thread updates rows above the block.
+template <typename T, int kStages>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
+k_band_solve_res(const T* __restrict__ base, const BandDesc* __restrict__ descs,
+                 double* __restrict__ xbase, const int64_t* __restrict__ xoff,
+                 const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, DevStatus* st) {
+  constexpr int SNB = 16;
+  const int mi = blockIdx.x;
+  if (skip && skip[mi]) return;
+  if (nrhs_dev && nrhs_dev[mi] <= 0) return;
+  const BandDesc d = descs[mi];
+  const int n = d.n, w = d.w;
+  if (n <= 0) return;
+  const int ld = d.ld;
+  const T* L = base + d.off;
+  const T* Dg = base + d.dinv;
+  double* X = xbase + xoff[mi];
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);             // kStages
+  T* stage = reinterpret_cast<T*>(smem_raw + 128);                    // kStages * SNB * ld
+  T* dstage = stage + (size_t)kStages * SNB * ld;                     // kStages * 256
+  T* vec = dstage + (size_t)kStages * 256;                            // n (padded to 4)
+  T* zb = vec + ((n + 3) & ~3);                                       // SNB
+  const int tid = threadIdx.x;
+  const int nb = (n + SNB - 1) / SNB;
+  const int nvis = 2 * nb;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int v) {
+    const int blk = visit_block(v, nb), kb = blk * SNB;
+    const int b = min(SNB, n - kb);
+    const int s = v % kStages;
+    const uint32_t bytes = (uint32_t)((size_t)b * ld * sizeof(T));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bars[s], bytes + 256 * (uint32_t)sizeof(T));
+    bulk_load(stage + (size_t)s * SNB * ld, L + (int64_t)kb * ld, bytes, &bars[s]);
+    bulk_load(dstage + (size_t)s * 256, Dg + (int64_t)blk * 256, 256 * sizeof(T), &bars[s]);
+  };
+  int issued = 0;  // copies issued by thread 0
+  if (tid == 0)
+    for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
+  for (int i = tid; i < n; i += kThreads) vec[i] = (T)X[i];
+  __syncthreads();
+  bool ok = true;
+  int waited = 0;  // stages this thread has waited for
+
+  for (int v = 0; v < nvis; ++v) {
+    const int s = v % kStages;
+    const uint32_t parity = (uint32_t)((v / kStages) & 1);
+    if (tid == 0 && ok && issued < nvis) issue(issued++);
+    const int kb = visit_block(v, nb) * SNB;
+    const int b = min(SNB, n - kb);
+    if (ok) {
+      ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+      waited += ok ? 1 : 0;
+    }
+    const T* S = stage + (size_t)s * SNB * ld;
+    const T* D = dstage + (size_t)s * 256;   // M(i, t) at D[16 t + i]
+    if (v < nb) {
+      // ---------------- forward: z_i = b_i - sum_{c < kb} L(kb+i, c) y_c
+      const int i = tid >> 4, sl = tid & 15;
+      T acc = T(0);
+      if (i < b) {
+        const int r = kb + i;
+        const int olo = max(0, w - r), ohi = w - i;  // band offsets of the columns [r - w, kb)
+        const int len = ohi - olo;
+        const T* sp = S + (size_t)i * ld + olo;
+        const T* vp = vec + (r - w + olo);
+        T a1 = T(0);
+        int j = sl;
+        for (; j + 16 < len; j += 32) {
+          acc += sp[j] * vp[j];
+          a1 += sp[j + 16] * vp[j + 16];
+        }
+        if (j < len) acc += sp[j] * vp[j];
+        acc += a1;
+      }
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, 16);
+      if (sl == 0 && i < b) zb[i] = vec[kb + i] - acc;
+      __syncthreads();
+      // y = M z
+      if (tid < b) {
+        T y = T(0);
+#pragma unroll
+        for (int t = 0; t < SNB; ++t)
+          if (t <= tid) y += D[t * SNB + tid] * zb[t];
+        vec[kb + tid] = y;
+      }
+    } else {
+      // ---------------- backward: x = M^T y, then rows above the block
+      if (tid < b) {
+        T x = T(0);
+#pragma unroll
+        for (int j = 0; j < SNB; ++j) {
+          const int i = (tid + j) & (SNB - 1);  // rotated: conflict-free reads of M
+          if (i >= tid && i < b) x += D[tid * SNB + i] * vec[kb + i];
+        }
+        zb[tid] = x;
+      }
+      __syncthreads();
+      if (tid < b) vec[kb + tid] = zb[tid];
+      // y_rr -= sum_t L(kb + t, rr) x_{kb+t} for rr in [kb - w, kb)
+      const int lo = max(0, kb - w);
+      for (int rr = lo + tid; rr < kb; rr += kThreads) {
+        const int tmax = min(b - 1, rr - kb + w);
+        T a0 = T(0), a1 = T(0);
+        int t = 0;
+        for (; t + 1 <= tmax; t += 2) {
+          a0 += S[t * ld + (rr - kb - t + w)] * zb[t];
+          a1 += S[(t + 1) * ld + (rr - kb - t - 1 + w)] * zb[t + 1];
+        }
+        if (t <= tmax) a0 += S[t * ld + (rr - kb - t + w)] * zb[t];
+        vec[rr] -= a0 + a1;
+      }
+    }
+    __syncthreads();
+  }
+  // after a timed-out wait, let the copies still in flight land (bounded)
+  if (tid == 0 && !ok)
+    for (int v = waited; v < issued; ++v)
+      mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
+  if (!ok) return;
+  for (int i = tid; i < n; i += kThreads) X[i] = (double)vec[i];
+}
+
+// Several right-hand sides (the eigensolver's K_j^{-1} blocks), at most
+// 2 CT per launch.  The solved rows of the last w + 32 block rows sit in a
+// shared ring stored row-major (row stride KP = 2 CT + 4 values, so rows
+// taken by consecutive threads fall in distinct banks).
+// Forward block: the (16 x w) x (w x k) product with the solved rows is cut
+// into eight ranges of the band, one per warp; lane (i, g) owns row i and
+// columns [g CT, g CT + CT), reads one factor value and CT/4 four-wide ring
+// vectors per band position, and the warps' partial sums are added in a
+// fixed order; the inverted diagonal block is then applied (one output per
+// thread).  Backward block: the transposed inverse is applied, then the ring
+// rows above the block are updated, one (row, four columns) item per thread.
+// Right-hand sides of the next block and the rows that enter the ring are
+// loaded one block ahead.
+template <typename T, int CT, int kStages>
+__global__ void __launch_bounds__(kThreads, 1)
+k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ descs,
+                   double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
+                   const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
+                   DevStatus* st) {
+  constexpr int SNB = 16;
+  constexpr int KP = 2 * CT + 4;
+  constexpr int NW = kThreads / 32;
+  const int mi = blockIdx.x;
+  if (skip && skip[mi]) return;
+  int k = min(kcap, 2 * CT);
+  if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
+  if (k <= 0) return;
+  const BandDesc d = descs[mi];
+  const int n = d.n, w = d.w;
+  if (n <= 0) return;
+  const int ld = d.ld;
+  const T* L = base + d.off;
+  const T* Dg = base + d.dinv;
+  double* X = xbase + xoff[mi] + (int64_t)col0 * n;
+  const int rmask = ring - 1;  // ring: power of two >= w + 2 SNB
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);      // kStages
+  T* stage = reinterpret_cast<T*>(smem_raw + 128);             // kStages * SNB * ld
+  T* dstage = stage + (size_t)kStages * SNB * ld;              // kStages * 256
+  T* win = dstage + (size_t)kStages * 256;                     // ring * KP
+  T* red = win + (size_t)ring * KP;                            // NW * SNB * KP
+  T* zb = red + (size_t)NW * SNB * KP;                         // SNB * KP
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = (n + SNB - 1) / SNB;
+  const int nvis = 2 * nb;
+
+  for (int idx = tid; idx < ring * KP; idx += kThreads) win[idx] = T(0);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int v) {
+    const int blk = visit_block(v, nb), kb = blk * SNB;
+    const int b = min(SNB, n - kb);
+    const int s = v % kStages;
+    const uint32_t bytes = (uint32_t)((size_t)b * ld * sizeof(T));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bars[s], bytes + 256 * (uint32_t)sizeof(T));
+    bulk_load(stage + (size_t)s * SNB * ld, L + (int64_t)kb * ld, bytes, &bars[s]);
+    bulk_load(dstage + (size_t)s * 256, Dg + (int64_t)blk * 256, 256 * sizeof(T), &bars[s]);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
+  // element e of a (16 rows x k columns) block handled by this thread:
+  // idx = tid + e * kThreads, column idx >> 4, row idx & 15
+  auto load_rows = [&](int r0, int cnt, T* out) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+      out[e] = (c < k && t < cnt) ? (T)X[(int64_t)c * n + r0 + t] : T(0);
+    }
+  };
+  T xr[2];
+  load_rows(0, min(SNB, n), xr);
+  bool ok = true;
+  int waited = 0;
+  int lo = n;
+
+  for (int v = 0; v < nvis; ++v) {
+    const int s = v % kStages;
+    const uint32_t parity = (uint32_t)((v / kStages) & 1);
+    if (tid == 0 && ok && issued < nvis) issue(issued++);
+    const int kb = visit_block(v, nb) * SNB;
+    const int b = min(SNB, n - kb);
+    const T* S = stage + (size_t)s * SNB * ld;
+    const T* D = dstage + (size_t)s * 256;   // M(i, t) at D[16 t + i]
+    if (v < nb) {
+      // ---------------- forward
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+        if (c < k) zb[t * KP + c] = xr[e];
+      }
+      if (v + 1 < nb) load_rows(kb + SNB, min(SNB, n - kb - SNB), xr);
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
+      {
+        const int i = lane & 15, g = lane >> 4;
+        T acc[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[c] = T(0);
+        if (i < b) {
+          const int ua = (int)((int64_t)w * wid / NW), ub = (int)((int64_t)w * (wid + 1) / NW);
+          const int u0 = max(ua, max(i, w - kb));
+          const T* srow = S + (size_t)i * ld - i;   // srow[u] = L(kb + i, kb - w + u)
+          for (int u = u0; u < ub; ++u) {
+            const T a = srow[u];
+            const T* rr = win + (size_t)((kb - w + u) & rmask) * KP + g * CT;
+#pragma unroll
+            for (int q = 0; q < CT / 4; ++q) {
+              T xv[4];
+              load4(rr + 4 * q, xv);
+#pragma unroll
+              for (int z = 0; z < 4; ++z) acc[4 * q + z] += a * xv[z];
+            }
+          }
+        }
+        T* rp = red + (size_t)(wid * SNB + i) * KP + g * CT;
+#pragma unroll
+        for (int q = 0; q < CT / 4; ++q) store4(rp + 4 * q, acc + 4 * q);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, t = idx & 15;
+        T sum = T(0);
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) sum += red[(size_t)(ww * SNB + t) * KP + c];
+        zb[t * KP + c] -= sum;
+      }
+      __syncthreads();
+      // y = M z: one (row, column) output per thread
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, i = idx & 15;
+        if (i < b) {
+          T y = T(0);
+#pragma unroll
+          for (int t = 0; t < SNB; ++t)
+            if (t <= i) y += D[t * SNB + i] * zb[t * KP + c];
+          win[(size_t)((kb + i) & rmask) * KP + c] = y;
+          X[(int64_t)c * n + kb + i] = (double)y;
+        }
+      }
+      if (v == nb - 1) lo = max(0, kb - w);
+    } else {
+      // ---------------- backward
+      const int nlo = max(0, kb - SNB - w);
+      T er[2];
+      load_rows(nlo, lo - nlo, er);  // rows entering the ring (forward results)
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
+      // x = M^T y into zb (the ring rows of the block are not needed again)
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, t = idx & 15;
+        T x = T(0);
+        if (t < b) {
+#pragma unroll
+          for (int j = 0; j < SNB; ++j) {
+            const int i = (t + j) & (SNB - 1);  // rotated: conflict-free reads of M
+            if (i >= t && i < b) x += D[t * SNB + i] * win[(size_t)((kb + i) & rmask) * KP + c];
+          }
+          X[(int64_t)c * n + kb + t] = (double)x;
+        }
+        zb[t * KP + c] = x;
+      }
+      __syncthreads();
+      // rows [lo, kb): y_rr -= sum_t L(kb + t, rr) x_{kb+t}, items (row, four columns)
+      const int cnt = kb - lo, nq = (k + 3) >> 2;
+      for (int it = tid; it < cnt * nq; it += kThreads) {
+        const int rr = lo + it % cnt, q = it / cnt;
+        const int tmax = min(b - 1, rr - kb + w);
+        T* yrow = win + (size_t)(rr & rmask) * KP + 4 * q;
+        T acc[4];
+        load4(yrow, acc);
+        for (int t = 0; t <= tmax; ++t) {
+          const T lv = S[t * ld + (rr - kb - t + w)];
+          T xv[4];
+          load4(zb + t * KP + 4 * q, xv);
+#pragma unroll
+          for (int z = 0; z < 4; ++z) acc[z] -= lv * xv[z];
+        }
+        store4(yrow, acc);
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+        if (c < k && t < lo - nlo) win[(size_t)((nlo + t) & rmask) * KP + c] = er[e];
+      }
+      lo = nlo;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && !ok)
+    for (int v = waited; v < issued; ++v)
+      mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
 }
 
 constexpr int kNB = 32;
@@ -462,8 +856,8 @@ inline int next_pow2(int v) {
 }  // namespace
 
 template <typename T>
-geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, DevStatus* st,
-                          cudaStream_t s) {
+geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
+                          DevStatus* st, cudaStream_t s) {
   if (count <= 0) return GENEO_OK;
   // the panel starts at a 16-byte boundary (diag block: 32 x 33 values) and
   // its row stride phmax is a multiple of 4
@@ -480,6 +874,11 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
     kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st); note_launch();
   }
   GENEO_CUDA(cudaGetLastError());
+  if (max_n > 0) {
+    const int nb = (max_n + 15) / 16;
+    k_band_dinv<T><<<dim3((nb + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+  }
   return GENEO_OK;
 }
 
@@ -490,15 +889,77 @@ size_t solve_smem(int max_w, int k, int ring, int snb, int stages) {
   return 128 + sizeof(T) * ((size_t)stages * snb * ld + (size_t)ring * k + (size_t)snb * k + 4 * kThreads);
 }
 
+// Shared memory of the register-tiled multi-right-hand-side solve.
+template <typename T>
+size_t multi_smem(int max_w, int ring, int CT, int stages) {
+  const int ld = band_ld(max_w);
+  const int KP = 2 * CT + 4;
+  return 128 + sizeof(T) * ((size_t)stages * (16 * ld + 256) + (size_t)ring * KP +
+                            (size_t)(kThreads / 32 + 1) * 16 * KP);
+}
+
+template <typename T, int CT, int kStages>
+geneo_status_t launch_multi_t(int count, size_t smem, cudaStream_t s, const T* base, const BandDesc* d_desc,
+                              double* xbase, const int64_t* xoff, int c0, int kc,
+                              const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
+  auto kern = k_band_solve_multi<T, CT, kStages>;
+  GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
+  note_launch();
+  GENEO_CUDA(cudaGetLastError());
+  return GENEO_OK;
+}
+
+template <typename T>
+geneo_status_t launch_multi(int CT, int stages, int count, size_t smem, cudaStream_t s, const T* base,
+                            const BandDesc* d_desc, double* xbase, const int64_t* xoff, int c0, int kc,
+                            const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
+#define GENEO_MULTI(ct, sg)                                                                       \
+  if (CT == ct && stages == sg)                                                                  \
+    return launch_multi_t<T, ct, sg>(count, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, \
+                                     skip_dev, ring, st);
+  GENEO_MULTI(4, 2) GENEO_MULTI(4, 4) GENEO_MULTI(8, 2) GENEO_MULTI(8, 4)
+  if constexpr (sizeof(T) == 4) {
+    GENEO_MULTI(12, 2) GENEO_MULTI(12, 4) GENEO_MULTI(16, 2) GENEO_MULTI(16, 4)
+  }
+#undef GENEO_MULTI
+  return GENEO_ERR_ARG;
+}
+
+// Shared memory of the resident-vector one-right-hand-side solve.
+template <typename T>
+size_t res_smem(int max_w, int max_n, int snb, int stages) {
+  const int ld = band_ld(max_w);
+  return 128 + sizeof(T) * ((size_t)stages * (snb * ld + 256) + (size_t)((max_n + 3) & ~3) + snb);
+}
+
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
   // One right-hand side (the preconditioner's local solves): two stages and
   // one register slot per warp keep the block small enough for several
   // blocks per SM, which hides the latency of the sequential sweep.
   if (nrhs == 1) {
+    // whole vector resident in shared memory when it fits; the deepest
+    // pipeline (at most four stages) that keeps two blocks per SM for FP32
+    // batches (one for FP64 or a small batch) hides the latency of the
+    // factor stream
+    if (max_n > 0) {
+      const size_t budget = (sizeof(T) == 4 && count > 152) ? 112 * 1024 : 226 * 1024;
+      int stages = 4;
+      while (stages > 2 && res_smem<T>(max_w, max_n, 16, stages) > budget) --stages;
+      const size_t smem = res_smem<T>(max_w, max_n, 16, stages);
+      if (smem <= 227 * 1024) {
+        auto kern = stages == 4 ? k_band_solve_res<T, 4>
+                  : stages == 3 ? k_band_solve_res<T, 3> : k_band_solve_res<T, 2>;
+        GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, nrhs_dev, skip_dev, st); note_launch();
+        GENEO_CUDA(cudaGetLastError());
+        return GENEO_OK;
+      }
+    }
     int snb = 16;
     if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16, 2) > kSmemCap) snb = 4;
     const int ring = next_pow2(max_w + 2 * snb);
@@ -509,6 +970,22 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
+  }
+  // register-tiled kernel: up to 32 (FP32) or 16 (FP64) columns per launch
+  {
+    const int ring = next_pow2(max_w + 32);
+    const int kmax = std::min(nrhs, sizeof(T) == 4 ? 32 : 16);
+    const int CT0 = (((kmax + 1) / 2) + 3) & ~3;
+    if (multi_smem<T>(max_w, ring, CT0, 2) <= 227 * 1024) {
+      for (int c0 = 0; c0 < nrhs; c0 += kmax) {
+        const int kc = std::min(kmax, nrhs - c0);
+        const int CT = (((kc + 1) / 2) + 3) & ~3;
+        const int stages = multi_smem<T>(max_w, ring, CT, 4) <= 227 * 1024 ? 4 : 2;
+        GENEO_TRY(launch_multi<T>(CT, stages, count, multi_smem<T>(max_w, ring, CT, stages), s, base,
+                                  d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st));
+      }
+      return GENEO_OK;
+    }
   }
   constexpr int stg = Stages<T>::v;
   int snb = 16;
@@ -531,15 +1008,15 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
   return GENEO_OK;
 }
 
-template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, DevStatus*,
+template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, int, DevStatus*,
                                            cudaStream_t);
-template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, DevStatus*,
+template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, int, DevStatus*,
                                           cudaStream_t);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
-                                           DevStatus*, cudaStream_t);
+                                           DevStatus*, cudaStream_t, int);
 template geneo_status_t band_solve<float>(const float*, const BandDesc*, int, int, double*,
                                           const int64_t*, int, const int32_t*, const int32_t*,
-                                          DevStatus*, cudaStream_t);
+                                          DevStatus*, cudaStream_t, int);
 
 }  // namespace geneo

@@ -244,7 +244,7 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
     }
   }
   h->wH = wH;
-  GENEO_TRY(h->mem.get(&h->bandH, (size_t)h->dimH * band_ld(wH)));
+  GENEO_TRY(h->mem.get(&h->bandH, (size_t)h->dimH * band_ld(wH) + dinv_elems(h->dimH)));
   GENEO_CUDA(cudaMemsetAsync(h->bandH, 0, sizeof(double) * h->dimH * band_ld(wH), s));
   int2* dpairs = nullptr;
   GENEO_TRY(tmp.get(&dpairs, pairs.size()));
@@ -256,12 +256,12 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   *ms_matrix = ms_since(t1);
 
   auto t2 = std::chrono::steady_clock::now();
-  BandDesc bh{0, h->dimH, wH, -2, band_ld(wH)};
+  BandDesc bh{0, h->dimH, wH, -2, band_ld(wH), (int64_t)h->dimH * band_ld(wH)};
   GENEO_TRY(h->mem.get(&h->dbandH, 1));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandH, &bh, sizeof(BandDesc), cudaMemcpyHostToDevice, s));
   const int pf = h->prof.begin(GENEO_PROF_FACTOR, band_factor_flops(h->dimH, wH),
                                2.0 * 8.0 * band_entries(h->dimH, wH), s);
-  GENEO_TRY(band_potrf<double>(h->bandH, h->dbandH, 1, wH, h->dstat, s));
+  GENEO_TRY(band_potrf<double>(h->bandH, h->dbandH, 1, wH, h->dimH, h->dstat, s));
   h->prof.end(pf, s);
   GENEO_TRY(check_status(h, s));
   *ms_factor = ms_since(t2);

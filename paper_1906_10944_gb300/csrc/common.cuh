@@ -142,14 +142,21 @@ struct SubDesc {
 // base[r * ld + (c - r + w)]; ld = w + 1 rounded up to a multiple of 4, so
 // every row (and every block of rows) starts on a 16-byte boundary (32 for
 // FP64) and can be moved by one bulk copy.  Slots with c < 0 are zero.
+// Beside the band, the factorisation stores the inverses of the 16 x 16
+// diagonal blocks of L (block b: rows and columns 16 b .. 16 b + 15; entry
+// (i, t) at dinv + 256 b + 16 i + t, zero outside the lower triangle and
+// beyond n), which the solves apply instead of substituting.
 struct BandDesc {
   int64_t off;     // element offset of the band (a multiple of 4)
   int32_t n, w;
   int32_t id;      // reported in errors
   int32_t ld;      // row stride
+  int64_t dinv;    // element offset of the inverted diagonal blocks
 };
 
 __host__ __device__ __forceinline__ int band_ld(int w) { return (w + 4) & ~3; }
+// elements of the inverted diagonal blocks of an order-n band
+__host__ __device__ __forceinline__ int64_t dinv_elems(int n) { return (int64_t)((n + 15) / 16) * 256; }
 
 // --------------------------------------------------------------------------
 // Device helpers.
@@ -249,15 +256,17 @@ geneo_status_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, in
 
 // band.cu
 template <typename T>
-geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
+geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
                           DevStatus* st, cudaStream_t s);
 // Solve L L^T X = X in place for `nrhs` columns per matrix (column-major,
 // leading dimension = matrix n, column stride = n); X for matrix i starts
 // at xbase + xoff[i]; nrhs_dev (may be NULL) gives per-matrix column counts
 // capped by nrhs; skip_dev (may be NULL) skips matrices with a non-zero flag.
+// max_n (largest matrix order, 0 if unknown) enables the one-right-hand-side
+// solve with the vector resident in shared memory.
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s);
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0);
 
 }  // namespace geneo

@@ -39,6 +39,7 @@ struct geneo_handle_s {
   void* bandA = nullptr;           // double or float
   geneo::BandDesc* dbandA = nullptr;
   int maxwA = 0;
+  int maxnD = 0;                   // largest Dirichlet dof count
 
   // coarse space
   int dimH = 0, wH = 0;

@@ -700,9 +700,9 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
                         int kmax) -> geneo_status_t {
     if (f32)
       return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
-                               ncols, skip, h->dstat, st);
+                               ncols, skip, h->dstat, st, maxn);
     return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
-                              kmax, ncols, skip, h->dstat, st);
+                              kmax, ncols, skip, h->dstat, st, maxn);
   };
   // timed with CUDA events; flops from the per-subdomain column counts
   auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {

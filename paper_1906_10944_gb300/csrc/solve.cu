@@ -232,7 +232,7 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   double lfl = 0.0, lby = 0.0;
   for (const SubDesc& d : h->hsub) {
     lfl += band_solve_flops(d.nD, d.wA);
-    lby += 2.0 * esz * band_entries(d.nD, d.wA) + 8.0 * 4.0 * d.nD;  // factor twice; u in, out each sweep
+    lby += 2.0 * esz * band_entries(d.nD, d.wA) + 8.0 * 2.0 * d.nD;  // factor twice; u in and out once
   }
   h->local_solve_flops = lfl;
   h->local_solve_bytes = lby;
@@ -252,17 +252,17 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
     const int pc = h->prof.begin(GENEO_PROF_COARSE_SOLVE, band_solve_flops(h->dimH, h->wH),
                                  2.0 * 8.0 * band_entries(h->dimH, h->wH) + 16.0 * h->dimH, h->aux);
     GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr,
-                                 h->dstat, h->aux));
+                                 h->dstat, h->aux, h->dimH));
     h->prof.end(pc, h->aux);
     GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   }
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
   if (h->fp32)
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                nullptr, nullptr, h->dstat, s));
+                                nullptr, nullptr, h->dstat, s, h->maxnD));
   else
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                 nullptr, nullptr, h->dstat, s));
+                                 nullptr, nullptr, h->dstat, s, h->maxnD));
   h->prof.end(pl, s);
   if (h->dimH > 0) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
