@@ -12,7 +12,8 @@
 // preconditioner.  Per iteration and subdomain:
 //   R = B X - K X diag(nu)            residuals, relative norms rn_i
 //   W = K^{-1} R[:, active]           active = columns with rn_i > tol
-//   Q = [W, P], K-orthogonalised against X and K-orthonormalised by SVQB, twice
+//   Q = [W, P], K-orthogonalised against X and K-orthonormalised, twice
+//     (SVQB the first time, Cholesky QR the second, SVQB where it fails)
 //   Rayleigh-Ritz on S = [X, Q] (S^T K S = I): eig(S^T B S), top s
 //   P = Q U_Q, X = S U
 // Stop when every Ritz pair below the threshold tau is converged and the
@@ -334,32 +335,36 @@ __global__ void k_init_random(const SubDesc* __restrict__ sub, ColRef X, uint64_
 }
 
 // ---------------------------------------------------------------------------
-// Dense symmetric eigensolver: parallel cyclic Jacobi (round-robin pairs).
-// A (m x m, row stride lda) is overwritten by its diagonal form, V receives
-// the eigenvectors (columns).  Whole block participates.
+// Dense symmetric eigensolver: parallel cyclic Jacobi (round-robin pairs) in
+// arithmetic T.  A (m x m, row stride lda) is overwritten by its diagonal
+// form, V receives the eigenvectors (columns).  Whole block participates.
 // ---------------------------------------------------------------------------
-__device__ void jacobi_eig(double* A, int lda, double* V, int ldv, int m, double* cs, double* sn,
-                           double* red) {
+template <typename T>
+__device__ void jacobi_eig(T* A, int lda, T* V, int ldv, int m, T* cs, T* sn, T* red) {
+  // stop when the off-diagonal mass is below eps_off of the whole (squared
+  // norms); rotations smaller than eps_rot relative to the pivots are skipped
+  const T eps_off = sizeof(T) == 4 ? T(1e-13) : T(1e-30);
+  const T eps_rot = sizeof(T) == 4 ? T(1e-9) : T(1e-18);
+  const T tiny = sizeof(T) == 4 ? T(1e-37) : T(1e-300);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int M = m + (m & 1);
   for (int idx = tid; idx < m * m; idx += nt) {
     const int r = idx % m, c = idx / m;
-    V[r * ldv + c] = (r == c) ? 1.0 : 0.0;
+    V[r * ldv + c] = (r == c) ? T(1) : T(0);
   }
   __syncthreads();
   if (m <= 1) return;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    // convergence test: off-diagonal mass relative to the whole
-    double off = 0.0, all = 0.0;
+    T off = T(0), all = T(0);
     for (int idx = tid; idx < m * m; idx += nt) {
       const int r = idx % m, c = idx / m;
-      const double v = A[r * lda + c];
+      const T v = A[r * lda + c];
       all += v * v;
       if (r != c) off += v * v;
     }
     off = block_sum(off, red);
     all = block_sum(all, red);
-    if (off <= 1e-30 * all || all == 0.0) break;
+    if (off <= eps_off * all || all == T(0)) break;
     for (int round = 0; round < M - 1; ++round) {
       // pair k: (M-1, round) for k = 0; ((round+k)%(M-1), (round-k+M-1)%(M-1)) otherwise
       for (int k = tid; k < M / 2; k += nt) {
@@ -367,19 +372,19 @@ __device__ void jacobi_eig(double* A, int lda, double* V, int ldv, int m, double
         if (k == 0) { pi = M - 1; qi = round; }
         else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
         if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        double c = 1.0, s = 0.0;
+        T c = T(1), sv = T(0);
         if (qi < m) {
-          const double apq = A[pi * lda + qi];
-          const double app = A[pi * lda + pi], aqq = A[qi * lda + qi];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
+          const T apq = A[pi * lda + qi];
+          const T app = A[pi * lda + pi], aqq = A[qi * lda + qi];
+          if (fabs(apq) > tiny && fabs(apq) > eps_rot * sqrt(fabs(app * aqq))) {
+            const T theta = (aqq - app) / (T(2) * apq);
+            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            c = T(1) / sqrt(t * t + T(1));
+            sv = t * c;
           }
         }
         cs[k] = c;
-        sn[k] = s;
+        sn[k] = sv;
       }
       __syncthreads();
       // rows: new_p = c p - s q, new_q = s p + c q
@@ -389,11 +394,11 @@ __device__ void jacobi_eig(double* A, int lda, double* V, int ldv, int m, double
         if (k == 0) { pi = M - 1; qi = round; }
         else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
         if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        if (qi >= m || sn[k] == 0.0) continue;
-        const double c = cs[k], s = sn[k];
-        const double ap = A[pi * lda + col], aq = A[qi * lda + col];
-        A[pi * lda + col] = c * ap - s * aq;
-        A[qi * lda + col] = s * ap + c * aq;
+        if (qi >= m || sn[k] == T(0)) continue;
+        const T c = cs[k], sv = sn[k];
+        const T ap = A[pi * lda + col], aq = A[qi * lda + col];
+        A[pi * lda + col] = c * ap - sv * aq;
+        A[qi * lda + col] = sv * ap + c * aq;
       }
       __syncthreads();
       // columns of A and of V
@@ -403,39 +408,48 @@ __device__ void jacobi_eig(double* A, int lda, double* V, int ldv, int m, double
         if (k == 0) { pi = M - 1; qi = round; }
         else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
         if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        if (qi >= m || sn[k] == 0.0) continue;
-        const double c = cs[k], s = sn[k];
-        const double ap = A[row * lda + pi], aq = A[row * lda + qi];
-        A[row * lda + pi] = c * ap - s * aq;
-        A[row * lda + qi] = s * ap + c * aq;
-        const double vp = V[row * ldv + pi], vq = V[row * ldv + qi];
-        V[row * ldv + pi] = c * vp - s * vq;
-        V[row * ldv + qi] = s * vp + c * vq;
+        if (qi >= m || sn[k] == T(0)) continue;
+        const T c = cs[k], sv = sn[k];
+        const T ap = A[row * lda + pi], aq = A[row * lda + qi];
+        A[row * lda + pi] = c * ap - sv * aq;
+        A[row * lda + qi] = sv * ap + c * aq;
+        const T vp = V[row * ldv + pi], vq = V[row * ldv + qi];
+        V[row * ldv + pi] = c * vp - sv * vq;
+        V[row * ldv + qi] = sv * vp + c * vq;
       }
       __syncthreads();
     }
   }
 }
 
+// Shared memory of the dense kernels for matrices of order <= wmax (row
+// stride wmax + 1), arithmetic T.
+template <typename T>
+size_t dense_smem_bytes(int wmax) {
+  return sizeof(T) * ((size_t)2 * wmax * (wmax + 1) + 6 * (size_t)wmax + kT / 32 + 8);
+}
+
 // SVQB: columns whose Gram matrix is G (q x q) -> T (q x r) with
 // (M T)^T K (M T) = I; directions with eigenvalue below drop * max are
-// removed.  Writes T into Tout (ldg) and r into r_out[j].
+// removed.  Writes T into Tout (ldg) and r into r_out[j].  The Jacobi step
+// runs in arithmetic T (FP32 for a Gram formed in FP32 arithmetic).
+template <typename T>
 __global__ void __launch_bounds__(kT)
 k_svqb(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
        const int32_t* __restrict__ wq, const int32_t* __restrict__ wq2, int32_t* __restrict__ r_out,
-       double drop, const int32_t* __restrict__ skip) {
+       double drop, const int32_t* __restrict__ skip, int wmax) {
   const int j = blockIdx.x;
   if (skip && skip[j]) return;
   const int q = (wq ? wq[j] : 0) + (wq2 ? wq2[j] : 0);
-  extern __shared__ double sm[];
-  constexpr int LD = kMaxW + 1;
-  double* A = sm;
-  double* V = A + kMaxW * LD;
-  double* dsc = V + kMaxW * LD;
-  double* ev = dsc + kMaxW;
-  double* cs = ev + kMaxW;
-  double* sn = cs + kMaxW;
-  double* red = sn + kMaxW;
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int LD = wmax + 1;
+  T* A = reinterpret_cast<T*>(dsm_raw);
+  T* V = A + (size_t)wmax * LD;
+  T* dsc = V + (size_t)wmax * LD;
+  T* ev = dsc + wmax;
+  T* cs = ev + wmax;
+  T* sn = cs + wmax;
+  T* red = sn + wmax;
   __shared__ int keep[kMaxW];
   __shared__ int nkeep;
   if (q <= 0) {
@@ -445,34 +459,124 @@ k_svqb(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
   const double* G = Gall + (int64_t)j * ldg * ldg;
   for (int i = threadIdx.x; i < q; i += blockDim.x) {
     const double g = G[(int64_t)i * ldg + i];
-    dsc[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    dsc[i] = g > 0.0 ? (T)(1.0 / sqrt(g)) : T(0);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
     const int r = idx % q, c = idx / q;
     const double g = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
-    A[r * LD + c] = dsc[r] * g * dsc[c];
+    A[r * LD + c] = (T)((double)dsc[r] * g * (double)dsc[c]);
   }
   __syncthreads();
-  jacobi_eig(A, LD, V, LD, q, cs, sn, red);
+  jacobi_eig<T>(A, LD, V, LD, q, cs, sn, red);
   for (int i = threadIdx.x; i < q; i += blockDim.x) ev[i] = A[i * LD + i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mx = 0.0;
+    T mx = T(0);
     for (int i = 0; i < q; ++i) mx = fmax(mx, ev[i]);
     int r = 0;
     for (int i = 0; i < q; ++i)
-      if (mx > 0.0 && ev[i] > drop * mx) keep[r++] = i;
+      if (mx > T(0) && (double)ev[i] > drop * (double)mx) keep[r++] = i;
     nkeep = r;
     r_out[j] = r;
   }
   __syncthreads();
-  double* T = Tout + (int64_t)j * ldg * ldg;
+  double* Tm = Tout + (int64_t)j * ldg * ldg;
   for (int idx = threadIdx.x; idx < q * nkeep; idx += blockDim.x) {
     const int r = idx % q, k = idx / q;
     const int i = keep[k];
-    T[(int64_t)k * ldg + r] = dsc[r] * V[r * LD + i] / sqrt(ev[i]);
+    Tm[(int64_t)k * ldg + r] = (double)dsc[r] * (double)V[r * LD + i] / sqrt((double)ev[i]);
   }
+}
+
+// K-orthonormalisation of a nearly orthonormal block (Cholesky QR): with
+// D = diag(G)^{-1/2} and D G D = L L^T, T = D L^{-T} gives (M T)^T K (M T) = I
+// and keeps all q columns.  A pivot below 1e-8 (D G D has unit diagonal)
+// switches this subdomain to the SVQB path above, which drops dependent
+// directions.
+__global__ void __launch_bounds__(kT)
+k_cholqr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
+         const int32_t* __restrict__ wq, int32_t* __restrict__ r_out, double drop,
+         const int32_t* __restrict__ skip, int wmax) {
+  const int j = blockIdx.x;
+  if (skip && skip[j]) return;
+  const int q = wq[j];
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int LD = wmax + 1;
+  double* A = reinterpret_cast<double*>(dsm_raw);
+  double* V = A + (size_t)wmax * LD;
+  double* dsc = V + (size_t)wmax * LD;
+  __shared__ int bad;
+  if (q <= 0) {
+    if (threadIdx.x == 0) r_out[j] = 0;
+    return;
+  }
+  const double* G = Gall + (int64_t)j * ldg * ldg;
+  for (int i = threadIdx.x; i < q; i += blockDim.x) {
+    const double g = G[(int64_t)i * ldg + i];
+    dsc[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    const int r = idx % q, c = idx / q;
+    A[r * LD + c] = dsc[r] * 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]) * dsc[c];
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle of A
+  for (int c = 0; c < q; ++c) {
+    const double piv = A[c * LD + c];
+    if (!(piv > 1e-8)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;
+    }
+    const double dl = sqrt(piv);
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < q; r += blockDim.x) A[r * LD + c] /= dl;
+    if (threadIdx.x == 0) A[c * LD + c] = dl;
+    __syncthreads();
+    const int rem = q - c - 1;
+    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+      const int r = c + 1 + idx % rem, t = c + 1 + idx / rem;
+      if (t <= r) A[r * LD + t] -= A[r * LD + c] * A[t * LD + c];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) return;  // r_out left for the SVQB fallback (flagged below)
+  // V = L^{-T} (upper triangular): column k solves L^T v = e_k by back
+  // substitution, one thread per column
+  for (int k = threadIdx.x; k < q; k += blockDim.x) {
+    for (int r = q - 1; r >= 0; --r) {
+      double v = r == k ? 1.0 : 0.0;
+      if (r > k) v = 0.0;
+      else {
+        for (int t = r + 1; t <= k; ++t) v -= A[t * LD + r] * V[t * LD + k];
+        v /= A[r * LD + r];
+      }
+      V[r * LD + k] = v;
+    }
+  }
+  __syncthreads();
+  double* Tm = Tout + (int64_t)j * ldg * ldg;
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    const int r = idx % q, k = idx / q;
+    Tm[(int64_t)k * ldg + r] = dsc[r] * V[r * LD + k];
+  }
+  if (threadIdx.x == 0) r_out[j] = q;
+}
+
+// Marks the subdomains whose Cholesky QR failed: the kernel above leaves
+// r_out[j] = -1 (set here beforehand) so the SVQB pass can run on them only.
+__global__ void k_mark_fallback(const int32_t* __restrict__ r_out, const int32_t* __restrict__ skip,
+                                int32_t* __restrict__ redo, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) redo[j] = (skip && skip[j]) ? 1 : (r_out[j] < 0 ? 0 : 1);
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ dst, int32_t v, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) dst[j] = v;
 }
 
 // Rayleigh-Ritz: eig of G (m x m, m = s_j + q_j), keep the s_j largest in
@@ -480,19 +584,19 @@ k_svqb(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
 __global__ void __launch_bounds__(kT)
 k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
      const int32_t* __restrict__ sj, const int32_t* __restrict__ qj, double* __restrict__ nu_out,
-     int ldnu, const int32_t* __restrict__ skip) {
+     int ldnu, const int32_t* __restrict__ skip, int wmax) {
   const int j = blockIdx.x;
   if (skip && skip[j]) return;
   const int s = sj[j];
   const int m = s + (qj ? qj[j] : 0);
-  extern __shared__ double sm[];
-  constexpr int LD = kMaxW + 1;
-  double* A = sm;
-  double* V = A + kMaxW * LD;
-  double* ev = V + kMaxW * LD;
-  double* cs = ev + kMaxW;
-  double* sn = cs + kMaxW;
-  double* red = sn + kMaxW;
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int LD = wmax + 1;
+  double* A = reinterpret_cast<double*>(dsm_raw);
+  double* V = A + (size_t)wmax * LD;
+  double* ev = V + (size_t)wmax * LD;
+  double* cs = ev + wmax;
+  double* sn = cs + wmax;
+  double* red = sn + wmax;
   __shared__ int order[kMaxW];
   if (m <= 0) return;
   const double* G = Gall + (int64_t)j * ldg * ldg;
@@ -501,7 +605,7 @@ k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
     A[r * LD + c] = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
   }
   __syncthreads();
-  jacobi_eig(A, LD, V, LD, m, cs, sn, red);
+  jacobi_eig<double>(A, LD, V, LD, m, cs, sn, red);
   for (int i = threadIdx.x; i < m; i += blockDim.x) ev[i] = A[i * LD + i];
   __syncthreads();
   // rank in descending order (ties by index)
@@ -674,9 +778,16 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   int maxn = 0;
   for (int j = 0; j < N; ++j) maxn = std::max(maxn, h->hsub[j].nN);
   const dim3 gridR(ceil_div(maxn, kT), N);
-  const size_t dense_smem = sizeof(double) * (2 * kMaxW * (kMaxW + 1) + 6 * kMaxW + kT / 32 + 8);
-  GENEO_CUDA(cudaFuncSetAttribute(k_svqb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  // dense kernels sized by the block width: [X, Q] has at most 3 s columns
+  const int wmax = W3;
+  const size_t dense_smem = dense_smem_bytes<double>(wmax);
+  const size_t dense_smem32 = dense_smem_bytes<float>(wmax);
+  GENEO_CUDA(cudaFuncSetAttribute(k_svqb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_svqb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem32));
+  GENEO_CUDA(cudaFuncSetAttribute(k_cholqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  int32_t* redo = nullptr;
+  GENEO_TRY(tmp.get(&redo, (size_t)N));
   const size_t nn_smem = sizeof(double) * kMaxW * kMaxW;
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
@@ -847,13 +958,13 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_TRY(solveK(xoffX, sj, skip));
     spmm(true, false, Xr, KXr, KXr, skip);
     GENEO_TRY(gram(Xr, KXr, 1, skip));
-    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip); note_launch(); h->prof.end(prs, st); }
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip, wmax); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, skip));
     k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, skip); note_launch();
     k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     spmm(false, true, Xr, BXr, BXr, skip);
     GENEO_TRY(gram(Xr, BXr, 1, skip));
-    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip); note_launch(); h->prof.end(prs, st); }
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip, wmax); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
     k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
@@ -894,7 +1005,26 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
         GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done, a32));
         spmm(true, false, Qr, KQr, KQr, done, a32);
         GENEO_TRY(gram(Qr, KQr, 1, done, a32));
-        { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done); note_launch(); h->prof.end(prs, st); }
+        {
+          const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
+          if (pass == 0) {
+            // SVQB with dropping; Jacobi in FP32 when the Gram matrix was
+            // formed in FP32 arithmetic
+            if (a32)
+              k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
+            else
+              k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
+            note_launch();
+          } else {
+            // the block is nearly K-orthonormal: Cholesky QR, SVQB where a
+            // pivot is too small
+            k_fill_i32<<<ceil_div(N, 128), 128, 0, st>>>(rj, -1, N); note_launch();
+            k_cholqr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, rj, 1e-12, done, wmax); note_launch();
+            k_mark_fallback<<<ceil_div(N, 128), 128, 0, st>>>(rj, done, redo, N); note_launch();
+            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, redo, wmax); note_launch();
+          }
+          h->prof.end(prs, st);
+        }
         GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, a32));
         k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
         k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
@@ -904,7 +1034,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // only BQ is new
       spmm(false, true, Qr, BQr, BQr, done);
       GENEO_TRY(gram(Sr, BSr, 1, done));
-      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done); note_launch(); h->prof.end(prs, st); }
+      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wmax); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
       k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();

@@ -68,23 +68,37 @@ k_prolong(int64_t n, const uint8_t* __restrict__ dir, const double* __restrict__
   }
 }
 
-// q = A p with one warp per row; partial sums of p.q per block.
+// q = A p; partial sums of p.q per block.  Eight lanes per row and two rows
+// per lane group in flight (rows r0 + g and r0 + 4 + g of an eight-row group
+// per warp), so each warp keeps several independent load chains going; the
+// in-row and per-block summation orders are fixed.
 __global__ void __launch_bounds__(kT)
 k_spmv_dot(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
            const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
            double* __restrict__ part) {
   __shared__ double red[kT / 32];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double dsum = 0.0;
-  for (int64_t row = warp; row < n; row += nwarps) {
-    double s = 0.0;
-    for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) s += val[e] * p[col[e]];
-    s = warp_sum(s);
-    if (lane == 0) {
-      q[row] = s;
-      dsum += s * p[row];
+  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
+    const int64_t ra = r0 + g, rb = r0 + 4 + g;
+    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
+    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
+    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
+    double sa = 0.0, sb = 0.0;
+    while (ea < ea1 || eb < eb1) {
+      if (ea < ea1) { sa += val[ea] * p[col[ea]]; ea += 8; }
+      if (eb < eb1) { sb += val[eb] * p[col[eb]]; eb += 8; }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
+      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
+    }
+    if (sl == 0) {
+      if (ra < n) { q[ra] = sa; dsum += sa * p[ra]; }
+      if (rb < n) { q[rb] = sb; dsum += sb * p[rb]; }
     }
   }
   dsum = block_sum(dsum, red);
