@@ -273,28 +273,29 @@ __global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRef A, ColRef 
 
 // C = beta*C + alpha * A * T, T = rows [t0 + t0d[j], ...) of a per-subdomain
 // ldg x ldg matrix (column-major).  p = width(A), q = width(C).
+// Arithmetic C: double, or float with one of two epilogues:
+//  corr = 0: everything rounded to FP32 (the first orthogonalisation pass
+//            and the search directions P);
+//  corr = 1: only the product is accumulated in FP32, the update is added
+//            to the FP64 operand in FP64 (for corrections that are small
+//            next to the operand: X G after the first pass, and A (T - I)
+//            when addI = 1, i.e. A T = A + A (T - I) with T near I).
+// f64 (may be NULL): subdomains with f64[j] == 0 use FP64 arithmetic.
 template <typename C>
-__global__ void __launch_bounds__(kT)
-k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
-          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
-          const int32_t* __restrict__ skip) {
-  const int j = blockIdx.y;
-  if (skip && skip[j]) return;
-  const SubDesc d = sub[j];
-  const int p = cr_w(A, j), q = cr_w(Cout, j);
-  if (q <= 0) return;
-  extern __shared__ __align__(16) unsigned char ts_raw[];
-  C* Ts = reinterpret_cast<C*>(ts_raw);  // p x q, Ts[i*q + c]
-  const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
+__device__ __forceinline__ void gemm_body(const SubDesc& d, const double* __restrict__ a, int p, int q,
+                                          const double* __restrict__ T, int ldg, int addI, int corr,
+                                          unsigned char* smem, double* __restrict__ cm, double alpha,
+                                          double beta) {
+  C* Ts = reinterpret_cast<C*>(smem);  // p x q, Ts[i*q + c]
   for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
     const int i = idx % p, c = idx / p;
-    Ts[i * q + c] = (C)T[(int64_t)c * ldg + i];
+    double v = T[(int64_t)c * ldg + i];
+    if (addI && i == c) v -= 1.0;
+    Ts[i * q + c] = (C)v;
   }
   __syncthreads();
   const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
   if (a_row >= d.nN) return;
-  const double* a = cr_ptr(A, d, j);
-  double* cm = cr_ptr(Cout, d, j);
   constexpr int CB = 8;
   for (int c0 = 0; c0 < q; c0 += CB) {
     C acc[CB];
@@ -311,10 +312,35 @@ k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ 
       const int c = c0 + z;
       if (c < q) {
         double* o = cm + (int64_t)c * d.nN + a_row;
-        *o = (beta == 0.0 ? (C)0 : (C)beta * (C)*o) + (C)alpha * acc[z];
+        if (corr || sizeof(C) == 8) {
+          double v = (double)acc[z] + (addI ? a[(int64_t)c * d.nN + a_row] : 0.0);
+          *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * v;
+        } else {
+          *o = (beta == 0.0 ? (C)0 : (C)beta * (C)*o) + (C)alpha * acc[z];
+        }
       }
     }
   }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kT)
+k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
+          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
+          const int32_t* __restrict__ skip, int corr, int addI, const int32_t* __restrict__ f64) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(Cout, j);
+  if (q <= 0) return;
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
+  const double* a = cr_ptr(A, d, j);
+  double* cm = cr_ptr(Cout, d, j);
+  if (sizeof(C) == 8 || (f64 && f64[j] == 0))
+    gemm_body<double>(d, a, p, q, T, ldg, addI, 1, ts_raw, cm, alpha, beta);
+  else
+    gemm_body<C>(d, a, p, q, T, ldg, addI, corr, ts_raw, cm, alpha, beta);
 }
 
 // Counter-based start block: uniform(-1, 1) from SplitMix64.
@@ -788,7 +814,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
   int32_t* redo = nullptr;
   GENEO_TRY(tmp.get(&redo, (size_t)N));
-  const size_t nn_smem = sizeof(double) * kMaxW * kMaxW;
+  const size_t nn_smem = sizeof(double) * W3 * W3;
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
@@ -890,8 +916,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
+  // mode: 0 FP64; 1 FP32 throughout; 2 FP32 product added in FP64 (with
+  // addI: A T = A + A (T - I)); f64flag: per-subdomain FP64 override
   auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
-                  double beta, const int32_t* skip, bool f32a = false) -> geneo_status_t {
+                  double beta, const int32_t* skip, int mode = 0, int addI = 0,
+                  const int32_t* f64flag = nullptr) -> geneo_status_t {
+    const bool f32a = mode != 0;
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wa, wc;
@@ -905,9 +935,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     }
     const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_GEMM, fl, by, st);
     if (f32a)
-      k_gemm_nn<float><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+      k_gemm_nn<float><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip,
+                                                    mode == 2, addI, f64flag);
     else
-      k_gemm_nn<double><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip);
+      k_gemm_nn<double><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip,
+                                                     1, addI, nullptr);
     note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
@@ -1001,8 +1033,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // K-orthonormality that Rayleigh-Ritz relies on.
       for (int pass = 0; pass < 2; ++pass) {
         const bool a32 = f32 && pass == 0;
+        // second pass with FP32 factors: X G is a small correction, its
+        // product is accumulated in FP32 and subtracted in FP64
+        const int gm = a32 ? 1 : (f32 ? 2 : 0);
         GENEO_TRY(gram(KXr, Qr, 0, done, a32));
-        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done, a32));
+        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done, gm));
         spmm(true, false, Qr, KQr, KQr, done, a32);
         GENEO_TRY(gram(Qr, KQr, 1, done, a32));
         {
@@ -1025,7 +1060,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
           }
           h->prof.end(prs, st);
         }
-        GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, a32));
+        // second pass: T = D L^{-T} is near I where Cholesky QR succeeded
+        // (redo[j] == 1); the SVQB fallback subdomains stay FP64
+        if (pass == 0 || !f32)
+          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, a32 ? 1 : 0));
+        else
+          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, 2, 1, redo));
         k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
         k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
         GENEO_CUDA(cudaGetLastError());
@@ -1036,7 +1076,8 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       GENEO_TRY(gram(Sr, BSr, 1, done));
       { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wmax); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
-      GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
+      // P only spans the next search block: FP32 arithmetic with FP32 factors
+      GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, f32 ? 1 : 0));
       k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
       GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
       k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
