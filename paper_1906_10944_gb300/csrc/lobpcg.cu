@@ -25,6 +25,7 @@
 // cyclic Jacobi in shared memory, one thread block per subdomain.
 #include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <cstdio>
 
 #include "handle.cuh"
@@ -40,9 +41,11 @@ constexpr int kMaxSweeps = 40;  // bound of the Jacobi sweep loop
 constexpr int kFirstPassNev = 8; // wanted pairs of the narrow first pass
 
 // A multivector operand: columns [c0 + c0d[j], + width) of a buffer holding W
-// columns per subdomain (rows = nN_j, column-major, ld = nN_j).
-struct ColRef {
-  double* base;
+// columns per subdomain (rows = nN_j, column-major, ld = nN_j), storage S
+// (FP64 buffers, or the FP32 copies used by the first orthogonalisation pass).
+template <typename S>
+struct ColRefT {
+  S* base;
   int W;
   int c0;
   const int32_t* c0d;
@@ -50,46 +53,54 @@ struct ColRef {
   const int32_t* wd;
   const int32_t* wd2;  // width = w + wd[j] + wd2[j] (NULL terms are 0)
 };
+using ColRef = ColRefT<double>;
+using ColRef32 = ColRefT<float>;
 
-__device__ __forceinline__ int cr_c0(const ColRef& r, int j) { return r.c0 + (r.c0d ? r.c0d[j] : 0); }
-__device__ __forceinline__ int cr_w(const ColRef& r, int j) {
+template <typename S>
+__device__ __forceinline__ int cr_c0(const ColRefT<S>& r, int j) { return r.c0 + (r.c0d ? r.c0d[j] : 0); }
+template <typename S>
+__device__ __forceinline__ int cr_w(const ColRefT<S>& r, int j) {
   return r.w + (r.wd ? r.wd[j] : 0) + (r.wd2 ? r.wd2[j] : 0);
 }
-__device__ __forceinline__ double* cr_ptr(const ColRef& r, const SubDesc& d, int j) {
+template <typename S>
+__device__ __forceinline__ S* cr_ptr(const ColRefT<S>& r, const SubDesc& d, int j) {
   return r.base + d.offN * (int64_t)r.W + (int64_t)cr_c0(r, j) * d.nN;
 }
 
-ColRef cref(double* base, int W, int c0, const int32_t* c0d, int w, const int32_t* wd,
-            const int32_t* wd2 = nullptr) {
-  return ColRef{base, W, c0, c0d, w, wd, wd2};
+template <typename S>
+ColRefT<S> cref(S* base, int W, int c0, const int32_t* c0d, int w, const int32_t* wd,
+                const int32_t* wd2 = nullptr) {
+  return ColRefT<S>{base, W, c0, c0d, w, wd, wd2};
 }
 
 // ---------------------------------------------------------------------------
 // Multivector kernels (grid: x = row blocks, y = subdomain).
 // ---------------------------------------------------------------------------
-// C is the arithmetic type: double, or float for the first orthogonalisation
-// pass (operands rounded to FP32 on load, results stored as FP64).
-template <typename C>
+// S is the storage and arithmetic type: double, or float for the first
+// orthogonalisation pass (FP32 copies of the operand and of K's values, so
+// nothing is converted in the inner loop).
+template <typename S>
 __global__ void __launch_bounds__(kT)
 k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
-       const int32_t* __restrict__ lcol, const double* __restrict__ v1, const double* __restrict__ v2,
-       ColRef X, ColRef Y1, ColRef Y2, const int32_t* __restrict__ skip) {
+       const int32_t* __restrict__ lcol, const S* __restrict__ v1, const S* __restrict__ v2,
+       ColRefT<S> X, ColRefT<S> Y1, ColRefT<S> Y2, const int32_t* __restrict__ skip) {
+  using C = S;
   const int j = blockIdx.y;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.nN) return;
   const int w = cr_w(X, j);
-  const double* x = cr_ptr(X, d, j);
-  double* y1 = cr_ptr(Y1, d, j);
-  double* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
+  const S* x = cr_ptr(X, d, j);
+  S* y1 = cr_ptr(Y1, d, j);
+  S* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
   const int64_t e0 = lrow[d.offN + a], e1 = lrow[d.offN + a + 1];
   const int64_t nn = d.nN;
   // four columns per pass: the row's column indices and values are read once
   // per four vectors
   int c = 0;
   for (; c + 4 <= w; c += 4) {
-    const double* xc = x + (int64_t)c * nn;
+    const S* xc = x + (int64_t)c * nn;
     C s10 = 0, s11 = 0, s12 = 0, s13 = 0, s20 = 0, s21 = 0, s22 = 0, s23 = 0;
     for (int64_t e = e0; e < e1; ++e) {
       const int col = lcol[e];
@@ -107,7 +118,7 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
     }
   }
   for (; c < w; ++c) {
-    const double* xc = x + (int64_t)c * nn;
+    const S* xc = x + (int64_t)c * nn;
     C s1 = 0, s2 = 0;
     for (int64_t e = e0; e < e1; ++e) {
       const C xv = (C)xc[lcol[e]];
@@ -119,8 +130,9 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
   }
 }
 
-// Y = X columnwise copy
-__global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef Dst,
+// Y = X columnwise copy (with conversion between storage types)
+template <typename SS, typename SD>
+__global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRefT<SS> Src, ColRefT<SD> Dst,
                             const int32_t* __restrict__ skip) {
   const int j = blockIdx.y;
   if (skip && skip[j]) return;
@@ -128,9 +140,9 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef 
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.nN) return;
   const int w = cr_w(Src, j);
-  const double* s = cr_ptr(Src, d, j);
-  double* t = cr_ptr(Dst, d, j);
-  for (int c = 0; c < w; ++c) t[(int64_t)c * d.nN + a] = s[(int64_t)c * d.nN + a];
+  const SS* s = cr_ptr(Src, d, j);
+  SD* t = cr_ptr(Dst, d, j);
+  for (int c = 0; c < w; ++c) t[(int64_t)c * d.nN + a] = (SD)s[(int64_t)c * d.nN + a];
 }
 
 // Partial Gram matrices G = A^T B over a row split; ld of G is ldg.
@@ -139,18 +151,19 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRef Src, ColRef 
 // several row groups (thread g of a tile takes rows g, g + groups, ... of
 // every staged chunk) and the groups' partials are summed in a fixed order at
 // the end, so all warps issue FP64 FMAs.
-template <typename C>
+template <typename S>
 __global__ void __launch_bounds__(kT, 2)
-k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double* __restrict__ Gp,
+k_gram_part(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym, double* __restrict__ Gp,
             int ldg, int nsub, const int32_t* __restrict__ skip) {
+  using C = S;
   const int j = blockIdx.y, rs = blockIdx.x;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
   const int p = cr_w(A, j), q = cr_w(B, j);
   double* G = Gp + ((int64_t)rs * nsub + j) * ldg * ldg;
   if (p <= 0 || q <= 0) return;
-  const double* a = cr_ptr(A, d, j);
-  const double* b = cr_ptr(B, d, j);
+  const S* a = cr_ptr(A, d, j);
+  const S* b = cr_ptr(B, d, j);
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   C* As = reinterpret_cast<C*>(gsm_raw);   // [kRB][kMaxW + 1]
   C* Bs = As + kRB * (kMaxW + 1);          // [kRB][kMaxW + 1]
@@ -164,8 +177,8 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
   int own[3];
 #pragma unroll
   for (int u = 0; u < 3; ++u) {
-    int t = groups > 1 ? (threadIdx.x < groups * ntiles ? threadIdx.x % ntiles : -1)
-                       : (u < tpt ? threadIdx.x + u * kT : -1);
+    const int tx = (int)threadIdx.x;
+    int t = groups > 1 ? (tx < groups * ntiles ? tx % ntiles : -1) : (u < tpt ? tx + u * kT : -1);
     if (groups > 1 && u > 0) t = -1;
     if (t >= ntiles) t = -1;
     own[u] = t;
@@ -255,7 +268,8 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym, double
 }
 
 // G = sum of the row-split partials (fixed order); sym mirrors the lower part.
-__global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRef A, ColRef B, int sym,
+template <typename S>
+__global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
                               const double* __restrict__ Gp, double* __restrict__ G, int ldg,
                               int nsub, const int32_t* __restrict__ skip) {
   const int j = blockIdx.x;
@@ -273,36 +287,35 @@ __global__ void k_gram_reduce(const SubDesc* __restrict__ sub, ColRef A, ColRef 
 
 // C = beta*C + alpha * A * T, T = rows [t0 + t0d[j], ...) of a per-subdomain
 // ldg x ldg matrix (column-major).  p = width(A), q = width(C).
-// Arithmetic C: double, or float with one of two epilogues:
-//  corr = 0: everything rounded to FP32 (the first orthogonalisation pass
-//            and the search directions P);
-//  corr = 1: only the product is accumulated in FP32, the update is added
-//            to the FP64 operand in FP64 (for corrections that are small
-//            next to the operand: X G after the first pass, and A (T - I)
-//            when addI = 1, i.e. A T = A + A (T - I) with T near I).
-// f64 (may be NULL): subdomains with f64[j] == 0 use FP64 arithmetic.
-template <typename C>
-__device__ __forceinline__ void gemm_body(const SubDesc& d, const double* __restrict__ a, int p, int q,
-                                          const double* __restrict__ T, int ldg, int addI, int corr,
-                                          unsigned char* smem, double* __restrict__ cm, double alpha,
-                                          double beta) {
-  C* Ts = reinterpret_cast<C*>(smem);  // p x q, Ts[i*q + c]
+// FP64 kernel: one row per thread, eight output columns at a time.
+__global__ void __launch_bounds__(kT)
+k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
+          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
+          const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(Cout, j);
+  if (q <= 0) return;
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  double* Ts = reinterpret_cast<double*>(ts_raw);  // p x q, Ts[i*q + c]
+  const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
   for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
     const int i = idx % p, c = idx / p;
-    double v = T[(int64_t)c * ldg + i];
-    if (addI && i == c) v -= 1.0;
-    Ts[i * q + c] = (C)v;
+    Ts[i * q + c] = T[(int64_t)c * ldg + i];
   }
   __syncthreads();
   const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
   if (a_row >= d.nN) return;
+  const double* a = cr_ptr(A, d, j);
+  double* cm = cr_ptr(Cout, d, j);
   constexpr int CB = 8;
   for (int c0 = 0; c0 < q; c0 += CB) {
-    C acc[CB];
+    double acc[CB];
 #pragma unroll
-    for (int z = 0; z < CB; ++z) acc[z] = 0;
+    for (int z = 0; z < CB; ++z) acc[z] = 0.0;
     for (int i = 0; i < p; ++i) {
-      const C av = (C)a[(int64_t)i * d.nN + a_row];
+      const double av = a[(int64_t)i * d.nN + a_row];
 #pragma unroll
       for (int z = 0; z < CB; ++z)
         if (c0 + z < q) acc[z] += av * Ts[i * q + c0 + z];
@@ -312,35 +325,95 @@ __device__ __forceinline__ void gemm_body(const SubDesc& d, const double* __rest
       const int c = c0 + z;
       if (c < q) {
         double* o = cm + (int64_t)c * d.nN + a_row;
-        if (corr || sizeof(C) == 8) {
-          double v = (double)acc[z] + (addI ? a[(int64_t)c * d.nN + a_row] : 0.0);
-          *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * v;
-        } else {
-          *o = (beta == 0.0 ? (C)0 : (C)beta * (C)*o) + (C)alpha * acc[z];
-        }
+        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc[z];
       }
     }
   }
 }
 
-template <typename C>
+// FP32-arithmetic GEMM.  A has storage SA, C storage SO; each A value is
+// read (and converted) once per 32 output columns; T rows are read as
+// four-wide vectors.  Epilogue:
+//  corr = 0 and SO = float: everything in FP32 (first orthogonalisation pass);
+//  otherwise the FP32 product is added in FP64: C = beta C + alpha (acc +
+//  [addI] A[:, c]).  With addI, T - I is used in the product, so A T = A +
+//  A (T - I) keeps FP64 accuracy for T near I (the second pass).
+// f64 (may be NULL): subdomains with f64[j] == 0 take FP64 arithmetic
+// (T not near I there).
+template <typename SA, typename SO>
 __global__ void __launch_bounds__(kT)
-k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
-          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
-          const int32_t* __restrict__ skip, int corr, int addI, const int32_t* __restrict__ f64) {
+k_gemm32(const SubDesc* __restrict__ sub, ColRefT<SA> A, const double* __restrict__ Tm, int ldg,
+         int t0, const int32_t* __restrict__ t0d, ColRefT<SO> Cout, double alpha, double beta,
+         const int32_t* __restrict__ skip, int corr, int addI, const int32_t* __restrict__ f64) {
   const int j = blockIdx.y;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
   const int p = cr_w(A, j), q = cr_w(Cout, j);
   if (q <= 0) return;
+  const bool wide = f64 && f64[j] == 0;
+  const int qp = (q + 3) & ~3;
   extern __shared__ __align__(16) unsigned char ts_raw[];
+  float* Ts = reinterpret_cast<float*>(ts_raw);        // p x qp, Ts[i*qp + c]
+  double* Td = reinterpret_cast<double*>(ts_raw);      // p x q (FP64 override)
   const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
-  const double* a = cr_ptr(A, d, j);
-  double* cm = cr_ptr(Cout, d, j);
-  if (sizeof(C) == 8 || (f64 && f64[j] == 0))
-    gemm_body<double>(d, a, p, q, T, ldg, addI, 1, ts_raw, cm, alpha, beta);
-  else
-    gemm_body<C>(d, a, p, q, T, ldg, addI, corr, ts_raw, cm, alpha, beta);
+  for (int idx = threadIdx.x; idx < p * qp; idx += blockDim.x) {
+    const int i = idx / qp, c = idx % qp;
+    double v = c < q ? T[(int64_t)c * ldg + i] : 0.0;
+    if (addI && i == c) v -= 1.0;
+    if (wide) {
+      if (c < q) Td[i * q + c] = v;
+    } else {
+      Ts[i * qp + c] = (float)v;
+    }
+  }
+  __syncthreads();
+  const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a_row >= d.nN) return;
+  const SA* a = cr_ptr(A, d, j);
+  SO* cm = cr_ptr(Cout, d, j);
+  if (wide) {
+    for (int c = 0; c < q; ++c) {
+      double acc = 0.0;
+      for (int i = 0; i < p; ++i) acc += (double)a[(int64_t)i * d.nN + a_row] * Td[i * q + c];
+      SO* o = cm + (int64_t)c * d.nN + a_row;
+      const double v = acc + (addI ? (double)a[(int64_t)c * d.nN + a_row] : 0.0);
+      *o = (SO)((beta == 0.0 ? 0.0 : beta * (double)*o) + alpha * v);
+    }
+    return;
+  }
+  for (int c0 = 0; c0 < q; c0 += 32) {
+    const int nc = min(32, q - c0);
+    float acc[32];
+#pragma unroll
+    for (int z = 0; z < 32; ++z) acc[z] = 0.f;
+    for (int i = 0; i < p; ++i) {
+      const float av = (float)a[(int64_t)i * d.nN + a_row];
+      const float* tr = Ts + i * qp + c0;
+#pragma unroll
+      for (int z4 = 0; z4 < 8; ++z4) {
+        if (4 * z4 < nc) {
+          const float4 t4 = *reinterpret_cast<const float4*>(tr + 4 * z4);
+          acc[4 * z4] += av * t4.x;
+          acc[4 * z4 + 1] += av * t4.y;
+          acc[4 * z4 + 2] += av * t4.z;
+          acc[4 * z4 + 3] += av * t4.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int z = 0; z < 32; ++z) {
+      if (z < nc) {
+        const int c = c0 + z;
+        SO* o = cm + (int64_t)c * d.nN + a_row;
+        if (corr || sizeof(SO) == 8) {
+          const double v = (double)acc[z] + (addI ? (double)a[(int64_t)c * d.nN + a_row] : 0.0);
+          *o = (SO)((beta == 0.0 ? 0.0 : beta * (double)*o) + alpha * v);
+        } else {
+          *o = (SO)((beta == 0.0 ? 0.f : (float)beta * (float)*o) + (float)alpha * acc[z]);
+        }
+      }
+    }
+  }
 }
 
 // Counter-based start block: uniform(-1, 1) from SplitMix64.
@@ -740,6 +813,11 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
   }
 }
 
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 __global__ void k_sub_nnz(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
                           int64_t* __restrict__ out, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -818,10 +896,23 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
 
   const bool f32 = h->fp32;
+  // FP32 copies for the first orthogonalisation pass: [X, Q] and [KX, KQ]
+  // (same layout as S and KS) and the values of K
+  float *S32 = nullptr, *KS32 = nullptr, *lK32 = nullptr;
+  if (f32) {
+    GENEO_TRY(tmp.get(&S32, (size_t)rows * W3));
+    GENEO_TRY(tmp.get(&KS32, (size_t)rows * W3));
+    GENEO_TRY(tmp.get(&lK32, (size_t)std::max<int64_t>(asmb.lnnz, 1)));
+    k_to_f32<<<(unsigned)std::min<int64_t>((asmb.lnnz + kT - 1) / kT, 152 * 16), kT, 0, st>>>(asmb.lK, lK32, asmb.lnnz);
+    note_launch();
+    GENEO_CUDA(cudaGetLastError());
+  }
   std::vector<int64_t> hxoff(N);
   for (int j = 0; j < N; ++j) hxoff[j] = h->hsub[j].offN * (int64_t)W3;
   int64_t *xoffX, *xoffQ;
@@ -877,11 +968,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaStreamSynchronize(st));
   }
   // widths of a column reference per subdomain (0 for skipped subdomains)
-  auto host_widths = [&](const ColRef& R, const int32_t* skip, std::vector<int>& out) -> geneo_status_t {
+  auto host_widths = [&](const auto& R, const int32_t* skip, std::vector<int>& out) -> geneo_status_t {
     out.assign(N, R.w);
     std::vector<int32_t> t(N), sk(N, 0);
     if (skip) GENEO_CUDA(cudaMemcpyAsync(sk.data(), skip, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
-    for (const int32_t* src : {R.wd, R.wd2}) {
+    const int32_t* srcs[2] = {R.wd, R.wd2};
+    for (const int32_t* src : srcs) {
       if (!src) continue;
       GENEO_CUDA(cudaMemcpyAsync(t.data(), src, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
       GENEO_CUDA(cudaStreamSynchronize(st));
@@ -891,9 +983,9 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     for (int j = 0; j < N; ++j) if (sk[j]) out[j] = 0;
     return GENEO_OK;
   };
-  // f32: FP32 arithmetic (first orthogonalisation pass), profiled as its own
-  // family
-  auto gram = [&](ColRef A, ColRef B, int sym, const int32_t* skip, bool f32a = false) -> geneo_status_t {
+  // Launches on FP32 copies are profiled as their own family.
+  auto gram = [&](auto A, auto B, int sym, const int32_t* skip) -> geneo_status_t {
+    using S = std::remove_pointer_t<decltype(A.base)>;
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wa, wb;
@@ -902,51 +994,60 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       for (int j = 0; j < N; ++j) {
         const double n = h->hsub[j].nN;
         fl += sym ? n * wa[j] * (wa[j] + 1.0) : 2.0 * n * wa[j] * wb[j];
-        by += 8.0 * n * (wa[j] + (sym ? 0 : wb[j]));
+        by += sizeof(S) * n * (wa[j] + (sym ? 0 : wb[j]));
       }
     }
-    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_GRAM, fl, by, st);
-    if (f32a)
-      k_gram_part<float><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
-    else
-      k_gram_part<double><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip);
-    note_launch();
-    k_gram_reduce<<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
+    const int pr = h->prof.begin(sizeof(S) == 4 ? GENEO_PROF_ORTHO32 : GENEO_PROF_GRAM, fl, by, st);
+    k_gram_part<S><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    k_gram_reduce<S><<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
-  // mode: 0 FP64; 1 FP32 throughout; 2 FP32 product added in FP64 (with
-  // addI: A T = A + A (T - I)); f64flag: per-subdomain FP64 override
+  auto gemm_cost = [&](const auto& A, const auto& C, double beta, const int32_t* skip, double esz,
+                       double& fl, double& by) -> geneo_status_t {
+    fl = 0.0;
+    by = 0.0;
+    if (!prof) return GENEO_OK;
+    std::vector<int> wa, wc;
+    GENEO_TRY(host_widths(A, skip, wa));
+    GENEO_TRY(host_widths(C, skip, wc));
+    for (int j = 0; j < N; ++j) {
+      const double n = h->hsub[j].nN;
+      fl += 2.0 * n * wa[j] * wc[j];
+      by += esz * n * (wa[j] + wc[j] * (beta == 0.0 ? 1.0 : 2.0));
+    }
+    return GENEO_OK;
+  };
+  // FP64 C = beta C + alpha A T
   auto gemm = [&](ColRef A, const double* Tmat, int t0, const int32_t* t0d, ColRef C, double alpha,
-                  double beta, const int32_t* skip, int mode = 0, int addI = 0,
-                  const int32_t* f64flag = nullptr) -> geneo_status_t {
-    const bool f32a = mode != 0;
-    double fl = 0.0, by = 0.0;
-    if (prof) {
-      std::vector<int> wa, wc;
-      GENEO_TRY(host_widths(A, skip, wa));
-      GENEO_TRY(host_widths(C, skip, wc));
-      for (int j = 0; j < N; ++j) {
-        const double n = h->hsub[j].nN;
-        fl += 2.0 * n * wa[j] * wc[j];
-        by += 8.0 * n * (wa[j] + wc[j] * (beta == 0.0 ? 1.0 : 2.0));
-      }
-    }
-    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_GEMM, fl, by, st);
-    if (f32a)
-      k_gemm_nn<float><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip,
-                                                    mode == 2, addI, f64flag);
-    else
-      k_gemm_nn<double><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip,
-                                                     1, addI, nullptr);
+                  double beta, const int32_t* skip) -> geneo_status_t {
+    double fl, by;
+    GENEO_TRY(gemm_cost(A, C, beta, skip, 8.0, fl, by));
+    const int pr = h->prof.begin(GENEO_PROF_GEMM, fl, by, st);
+    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip); note_launch();
+    h->prof.end(pr, st);
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  };
+  // FP32-arithmetic C = beta C + alpha A T (epilogue rules at k_gemm32)
+  auto gemm32 = [&](auto A, const double* Tmat, int t0, const int32_t* t0d, auto C, double alpha,
+                    double beta, const int32_t* skip, int corr, int addI = 0,
+                    const int32_t* f64flag = nullptr) -> geneo_status_t {
+    using SA = std::remove_pointer_t<decltype(A.base)>;
+    using SO = std::remove_pointer_t<decltype(C.base)>;
+    double fl, by;
+    GENEO_TRY(gemm_cost(A, C, beta, skip, 4.0, fl, by));
+    const int pr = h->prof.begin(GENEO_PROF_ORTHO32, fl, by, st);
+    k_gemm32<SA, SO><<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip,
+                                                 corr, addI, f64flag);
     note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
-  auto spmm = [&](bool withK, bool withB, ColRef X, ColRef YK, ColRef YB, const int32_t* skip,
-                  bool f32a = false) {
+  auto spmm = [&](bool withK, bool withB, auto X, auto YK, auto YB, const int32_t* skip) {
+    using S = std::remove_pointer_t<decltype(X.base)>;
     double fl = 0.0, by = 0.0;
     if (prof) {
       std::vector<int> wx;
@@ -954,19 +1055,35 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       const double nm = (withK && withB) ? 2.0 : 1.0;
       for (int j = 0; j < N; ++j) {
         fl += 2.0 * nm * (double)hnnz[j] * wx[j];
-        by += (double)hnnz[j] * (4.0 + 8.0 * nm) + 8.0 * h->hsub[j].nN * wx[j] * (1.0 + nm);
+        by += (double)hnnz[j] * (4.0 + sizeof(S) * nm) + sizeof(S) * h->hsub[j].nN * wx[j] * (1.0 + nm);
       }
     }
-    const int pr = h->prof.begin(f32a ? GENEO_PROF_ORTHO32 : GENEO_PROF_SPMM, fl, by, st);
-    auto kern = f32a ? k_spmm<float> : k_spmm<double>;
-    if (withK && withB) {
-      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, X, YK, YB, skip);
-    } else if (withK) {
-      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, nullptr, X, YK, YK, skip);
+    const int pr = h->prof.begin(sizeof(S) == 4 ? GENEO_PROF_ORTHO32 : GENEO_PROF_SPMM, fl, by, st);
+    const S* vK;
+    const S* vB;
+    if constexpr (sizeof(S) == 4) {
+      vK = lK32;
+      vB = nullptr;
     } else {
-      kern<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lB, nullptr, X, YB, YB, skip);
+      vK = asmb.lK;
+      vB = asmb.lB;
+    }
+    if (withK && withB) {
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, vB, X, YK, YB, skip);
+    } else if (withK) {
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, nullptr, X, YK, YK, skip);
+    } else {
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vB, nullptr, X, YB, YB, skip);
     }
     note_launch();
+    h->prof.end(pr, st);
+  };
+  // storage conversion of a column block (FP64 <-> FP32 copies)
+  auto cvt = [&](auto Src, auto Dst, const int32_t* skip) {
+    using SS = std::remove_pointer_t<decltype(Src.base)>;
+    using SD = std::remove_pointer_t<decltype(Dst.base)>;
+    const int pr = h->prof.begin(GENEO_PROF_ORTHO32, 0.0, 0.0, st);
+    k_copy_cols<SS, SD><<<gridR, kT, 0, st>>>(h->dsub, Src, Dst, skip); note_launch();
     h->prof.end(pr, st);
   };
 
@@ -980,6 +1097,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const ColRef Sr = cref(S, W3, 0, nullptr, 0, sj, qj);  // [X, Q]
   const ColRef BSr = cref(BS, W3, 0, nullptr, 0, sj, qj);
   const ColRef BQr = cref(BS, W3, 0, sj, 0, qj);
+  const ColRef32 Sr32 = cref(S32, W3, 0, nullptr, 0, sj, qj);   // FP32 [X, Q]
+  const ColRef32 Xr32 = cref(S32, W3, 0, nullptr, 0, sj);
+  const ColRef32 Qr32 = cref(S32, W3, 0, sj, 0, qj);
+  const ColRef32 KXr32 = cref(KS32, W3, 0, nullptr, 0, sj);
+  const ColRef32 KQr32 = cref(KS32, W3, 0, sj, 0, qj);
 
   // Start block for the subdomains with skip[j] == 0: X = K^{-1} B R
   // (R counter-based random), K-orthonormalised by SVQB, Rayleigh-Ritz.
@@ -993,12 +1115,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip, wmax); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, skip));
     k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, skip); note_launch();
-    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
+    k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     spmm(false, true, Xr, BXr, BXr, skip);
     GENEO_TRY(gram(Xr, BXr, 1, skip));
     { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip, wmax); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
-    k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
+    k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   };
@@ -1028,27 +1150,39 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // residual X-components a single round leaves, and the Rayleigh-Ritz
       // step below assumes a K-orthonormal [X, Q].
       // X^T K Q is formed as (KX)^T Q: KX from the residual step is current.
-      // With FP32 factors the first pass runs in FP32 arithmetic (it removes
-      // the bulk of the X components); the second, FP64 pass sets the final
-      // K-orthonormality that Rayleigh-Ritz relies on.
+      // With FP32 factors the first pass runs on FP32 copies of X, Q and KX
+      // (it removes the bulk of the X components); the second, FP64 pass sets
+      // the final K-orthonormality that Rayleigh-Ritz relies on.
       for (int pass = 0; pass < 2; ++pass) {
-        const bool a32 = f32 && pass == 0;
-        // second pass with FP32 factors: X G is a small correction, its
-        // product is accumulated in FP32 and subtracted in FP64
-        const int gm = a32 ? 1 : (f32 ? 2 : 0);
-        GENEO_TRY(gram(KXr, Qr, 0, done, a32));
-        GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done, gm));
-        spmm(true, false, Qr, KQr, KQr, done, a32);
-        GENEO_TRY(gram(Qr, KQr, 1, done, a32));
+        if (f32 && pass == 0) {
+          cvt(Sr, Sr32, done);
+          cvt(KXr, KXr32, done);
+          GENEO_TRY(gram(KXr32, Qr32, 0, done));
+          GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr32, -1.0, 1.0, done, 0));
+          spmm(true, false, Qr32, KQr32, KQr32, done);
+          GENEO_TRY(gram(Qr32, KQr32, 1, done));
+          {
+            const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
+            k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax); note_launch();
+            h->prof.end(prs, st);
+          }
+          // Q = Q32 T straight into the FP64 block (no aliasing: T acts on the copy)
+          GENEO_TRY(gemm32(Qr32, Tm, 0, nullptr, cref(S, W3, 0, sj, 0, rj), 1.0, 0.0, done, 1));
+          k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
+          GENEO_CUDA(cudaGetLastError());
+          continue;
+        }
+        GENEO_TRY(gram(KXr, Qr, 0, done));
+        // after an FP32 first pass X G is a small correction: FP32 product,
+        // subtracted in FP64
+        if (f32) GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr, -1.0, 1.0, done, 1));
+        else GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
+        spmm(true, false, Qr, KQr, KQr, done);
+        GENEO_TRY(gram(Qr, KQr, 1, done));
         {
           const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
           if (pass == 0) {
-            // SVQB with dropping; Jacobi in FP32 when the Gram matrix was
-            // formed in FP32 arithmetic
-            if (a32)
-              k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
-            else
-              k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
+            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
             note_launch();
           } else {
             // the block is nearly K-orthonormal: Cholesky QR, SVQB where a
@@ -1060,14 +1194,15 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
           }
           h->prof.end(prs, st);
         }
-        // second pass: T = D L^{-T} is near I where Cholesky QR succeeded
-        // (redo[j] == 1); the SVQB fallback subdomains stay FP64
-        if (pass == 0 || !f32)
-          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, a32 ? 1 : 0));
+        // second pass with FP32 factors: T = D L^{-T} is near I where
+        // Cholesky QR succeeded (redo[j] == 1): Q T = Q + Q (T - I) with an
+        // FP32 product; the SVQB fallback subdomains stay FP64
+        if (pass == 1 && f32)
+          GENEO_TRY(gemm32(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, 1, 1, redo));
         else
-          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, 2, 1, redo));
+          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
         k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
-        k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
+        k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
         GENEO_CUDA(cudaGetLastError());
       }
       // Rayleigh-Ritz on S = [X, Q]; BX from the residual step is current,
@@ -1077,10 +1212,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wmax); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       // P only spans the next search block: FP32 arithmetic with FP32 factors
-      GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, f32 ? 1 : 0));
+      if (f32) GENEO_TRY(gemm32(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, 0));
+      else GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
       k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
       GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));
-      k_copy_cols<<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
+      k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, done); note_launch();
       GENEO_CUDA(cudaGetLastError());
       GENEO_TRY(check_status(h, st));
     }
