@@ -271,6 +271,259 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// ---------------------------------------------------------------------------
+// Left-looking FP32 band Cholesky on the tensor cores.
+//
+// Panel j (columns j .. j+b-1, b <= 32) of the rows r in [j, j + R),
+// R = min(n, j + b + w) - j, is first brought up to date with all finished
+// columns k in [j - w, j):
+//   U(r, c) = A(r, c) - sum_k L(r, k) L(c, k),
+// an (R x w) x (w x 32) product whose operands are whole band rows: the
+// panel's own rows (staged once per panel) and the rows r (streamed in
+// chunks of 32 by bulk copies, two buffers).  Each warp owns one 16 x 8 tile
+// of a chunk's 32 x 32 block and accumulates it with m16n8k8 TF32 MMAs in
+// three passes (hi*hi + hi*lo + lo*hi with x = hi + lo, hi = tf32(x)), which
+// keeps about FP32 accuracy.  Then the panel is factored as in the
+// right-looking kernel: the 32 x 32 diagonal block by one warp, the rows
+// below by substitution, one row per thread.  Only the panel columns are
+// written; the trailing window is never rewritten.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo with hi the TF32 truncation of x (low 13 mantissa bits
+// cleared); the MMA reads the TF32 bits of lo the same way, so the product
+// error is of the order of the dropped lo * lo term
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(x) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+constexpr int kPB = 32;   // panel width of the tensor-core factorisation
+constexpr int kMC = 16;   // rows per streamed chunk (one 16-row MMA tile)
+constexpr int kUS = kPB + 1;  // row stride of the panel block in shared memory
+
+// Shared memory of the tensor-core factorisation for half-bandwidth w.
+inline size_t potrf_tc_smem(int w) {
+  const size_t ld = (size_t)band_ld(w);
+  return 128 + sizeof(float) * ((kPB + 2 * kMC) * ld + (size_t)(w + kPB) * kUS + kPB + 8 * 16 * 32);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, DevStatus* st) {
+  const BandDesc d = descs[blockIdx.x];
+  const int n = d.n, w = d.w;
+  const int ld = d.ld;
+  float* L = base + d.off;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // 0: panel rows, 1-2: chunks
+  float* Cs = reinterpret_cast<float*>(smem_raw + 128);                    // kPB x ld
+  float* Rs = Cs + (size_t)kPB * ld;                                       // 2 x kMC x ld
+  float* Us = Rs + (size_t)2 * kMC * ld;                                   // (w + kPB) x kUS panel block
+  float* Dinv = Us + (size_t)(w + kPB) * kUS;                              // kPB reciprocal pivots
+  float* Red = Dinv + kPB;                                                 // 8 warps x 16 x 32 partials
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t ph[3] = {0, 0, 0};      // next phase to wait for, per barrier
+  int issued[3] = {0, 0, 0};       // thread 0: copies issued per barrier
+  bool ok = true;                  // warp 0's view (thread 0 issues the copies)
+  auto load_rows = [&](int bar, float* dst, int r0, int rows) {
+    const uint32_t bytes = (uint32_t)((size_t)rows * ld * sizeof(float));
+    mbar_arrive_expect_tx(&bars[bar], bytes);
+    bulk_load(dst, L + (int64_t)r0 * ld, bytes, &bars[bar]);
+    ++issued[bar];
+  };
+  // warp 0 waits; the block is released by the barrier that follows
+  auto wait_bar = [&](int bar, int64_t where) {
+    if (wid == 0 && ok) {
+      ok = mbar_wait_bounded(&bars[bar], ph[bar] & 1, st, d.id, where);
+    }
+    ++ph[bar];
+    __syncthreads();
+  };
+
+  for (int j = 0; j < n; j += kPB) {
+    const int b = min(kPB, n - j);
+    const int R = min(n, j + b + w) - j;
+    const int kbeg = max(0, j - w);
+    const int nch = (R + kMC - 1) / kMC;
+    // the previous panel's columns were written by ordinary stores: order
+    // them before the bulk copies that read them
+    if (tid == 0 && ok) {
+      fence_proxy_async_global();
+      fence_proxy_async();
+      load_rows(0, Cs, j, b);
+      load_rows(1, Rs, j, min(kMC, R));
+    }
+    wait_bar(0, j);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      const int r0 = j + ch * kMC;
+      if (tid == 0 && ok && ch + 1 < nch)
+        load_rows(1 + (buf ^ 1), Rs + (size_t)(buf ^ 1) * kMC * ld, r0 + kMC, min(kMC, R - (ch + 1) * kMC));
+      wait_bar(1 + buf, (int64_t)j * 1024 + ch);
+      const float* Rb = Rs + (size_t)buf * kMC * ld;
+      // warp kq: rows r0 .. r0 + 15, all 32 panel columns, over the kq-th
+      // eighth of the k-steps of the tile's range
+      const int kq = wid;
+      const int ra = r0 + g, rb = r0 + g + 8;
+      const bool va = ra < j + R, vb = rb < j + R;
+      // element offsets of L(r, 0) in the staged rows (may be negative; an
+      // index is formed only for k in the row's band)
+      const int ia = g * ld + (w - ra);
+      const int ib = (g + 8) * ld + (w - rb);
+      const int klo = max(kbeg, r0 - w);          // no row of the tile reaches below klo
+      const int kst = kbeg + ((klo - kbeg) & ~7);
+      const int nsteps = (j - kst + 7) >> 3;
+      const int s0 = kst + 8 * ((nsteps * kq) >> 3), s1 = kst + 8 * ((nsteps * (kq + 1)) >> 3);
+      // every row and column is in band from kfull on
+      const int kfull = max(r0 + 15, j + b - 1) - w;
+      float acc[4][3][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][v][q] = 0.f;
+      for (int k0 = s0; k0 < s1; k0 += 8) {
+        const bool masked = k0 < kfull || k0 + 8 > j;
+        const int k1 = k0 + tg, k2 = k0 + tg + 4;
+        float x[4];
+        if (!masked) {
+          x[0] = va ? Rb[ia + k1] : 0.f;
+          x[1] = vb ? Rb[ib + k1] : 0.f;
+          x[2] = va ? Rb[ia + k2] : 0.f;
+          x[3] = vb ? Rb[ib + k2] : 0.f;
+        } else {
+          x[0] = (va && k1 < j && k1 >= ra - w && k1 >= 0) ? Rb[ia + k1] : 0.f;
+          x[1] = (vb && k1 < j && k1 >= rb - w && k1 >= 0) ? Rb[ib + k1] : 0.f;
+          x[2] = (va && k2 < j && k2 >= ra - w && k2 >= 0) ? Rb[ia + k2] : 0.f;
+          x[3] = (vb && k2 < j && k2 >= rb - w && k2 >= 0) ? Rb[ib + k2] : 0.f;
+        }
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) split_tf32(x[q], ah[q], al[q]);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int cn = 8 * nt + g, cc = j + cn;
+          const int ic = cn * ld + (w - cc);
+          float y0, y1;
+          if (!masked) {
+            y0 = cn < b ? Cs[ic + k1] : 0.f;
+            y1 = cn < b ? Cs[ic + k2] : 0.f;
+          } else {
+            y0 = (cn < b && k1 < j && k1 >= cc - w && k1 >= 0) ? Cs[ic + k1] : 0.f;
+            y1 = (cn < b && k2 < j && k2 >= cc - w && k2 >= 0) ? Cs[ic + k2] : 0.f;
+          }
+          uint32_t bh[2], bl[2];
+          split_tf32(y0, bh[0], bl[0]);
+          split_tf32(y1, bh[1], bl[1]);
+          mma_tf32(acc[nt][0], al, bh);
+          mma_tf32(acc[nt][1], ah, bl);
+          mma_tf32(acc[nt][2], ah, bh);
+        }
+      }
+      // partial sums of this eighth (small terms first), lane-contiguous
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          Red[((size_t)kq * 16 + nt * 4 + q) * 32 + lane] = (acc[nt][0][q] + acc[nt][1][q]) + acc[nt][2][q];
+      __syncthreads();
+      // warps 0-3: n-tile wid; U = A - sum into the panel block (zero
+      // outside the lower band)
+      if (wid < 4) {
+        const int nt2 = wid;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float sum = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) sum += Red[((size_t)kk * 16 + nt2 * 4 + q) * 32 + lane];
+          const int r = r0 + g + ((q & 2) ? 8 : 0);  // c0,c1: row g; c2,c3: row g+8
+          const int cl = 8 * nt2 + 2 * tg + (q & 1), c = j + cl;
+          if (r < j + R) {
+            float u = 0.f;
+            if (cl < b && c <= r && r - c <= w) u = Rb[(size_t)(r - r0) * ld + (c - r + w)] - sum;
+            Us[(size_t)(r - j) * kUS + cl] = u;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- factor the panel block: diagonal block in place by warp 0
+    if (tid < 32) {
+      for (int t = 0; t < b; ++t) {
+        if (lane == t) {
+          float dv = Us[t * kUS + t];
+          if (!finite_pos(dv)) {
+            record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
+            dv = 1.f;
+          }
+          Us[t * kUS + t] = sqrtf(dv);
+        }
+        __syncwarp();
+        const float piv = Us[t * kUS + t];
+        if (lane > t && lane < b) Us[lane * kUS + t] /= piv;
+        __syncwarp();
+        if (lane > t && lane < b) {
+          const float lrt = Us[lane * kUS + t];
+          for (int u = t + 1; u <= lane; ++u) Us[lane * kUS + u] -= lrt * Us[u * kUS + t];
+        }
+        __syncwarp();
+      }
+      Dinv[lane] = lane < b ? 1.f / Us[lane * kUS + lane] : 0.f;
+    }
+    __syncthreads();
+    // rows below: x L_jj^T = u, one row per thread (stride kUS: no bank conflicts)
+    for (int i = b + tid; i < R; i += kThreads) {
+      float* ur = Us + (size_t)i * kUS;
+      float x[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) x[t] = ur[t];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        if (t < b) {
+          float v = x[t];
+#pragma unroll
+          for (int u = 0; u < t; ++u) v -= x[u] * Us[t * kUS + u];
+          x[t] = v * Dinv[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) ur[t] = x[t];
+    }
+    __syncthreads();
+    // the panel's columns back to the band, one warp per row (coalesced)
+    for (int i = wid; i < R; i += kThreads / 32) {
+      const int r = j + i, c = j + lane;
+      if (lane < b && c <= r && r - c <= w) L[(int64_t)r * ld + (c - r + w)] = Us[(size_t)i * kUS + lane];
+    }
+    __syncthreads();
+  }
+  // after a timed-out wait, let the copies still in flight land (bounded)
+  if (tid == 0 && !ok)
+    for (int bar = 0; bar < 3; ++bar)
+      for (uint32_t p = ph[bar]; p < (uint32_t)issued[bar]; ++p)
+        mbar_wait_bounded(&bars[bar], p & 1, st, d.id, -1);
+}
+
 // rows per streamed block: 16, or 4 for bands too wide for 16-row stages
 // pipeline depth of the multi-right-hand-side solve: two stages leave room
 // for the right-hand-side ring and two blocks per SM
@@ -844,6 +1097,278 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
       mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
 }
 
+// Tensor-core variant of the multi-right-hand-side solve for FP32 factors:
+// the same sweeps as k_band_solve_multi, with the two contractions done by
+// m16n8k8 TF32 MMAs in three passes (hi*hi + hi*lo + lo*hi, about FP32
+// accuracy):
+//  forward  (16 x w) x (w x k): rows of the block against the solved ring
+//           rows, the band cut into eight k-ranges (one per warp), partial
+//           sums added in a fixed order;
+//  backward (w x 16) x (16 x k): ring rows above the block minus L^T x, one
+//           16-row tile per warp at a time, the ring values as the MMA's C.
+// k <= 8 NT columns per launch; the ring row stride KP puts the four k-rows
+// of a B fragment in distinct eight-bank groups.
+template <int NT>
+struct MtcKP { static constexpr int v = NT == 1 ? 8 : (NT == 4 ? 40 : 24); };
+
+template <int NT, int kStages>
+__global__ void __launch_bounds__(kThreads, 1)
+k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ descs,
+                 double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
+                 const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
+                 DevStatus* st) {
+  constexpr int SNB = 16;
+  constexpr int KP = MtcKP<NT>::v;
+  constexpr int NW = kThreads / 32;
+  const int mi = blockIdx.x;
+  if (skip && skip[mi]) return;
+  int k = min(kcap, 8 * NT);
+  if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
+  if (k <= 0) return;
+  const BandDesc d = descs[mi];
+  const int n = d.n, w = d.w;
+  if (n <= 0) return;
+  const int ld = d.ld;
+  const float* L = base + d.off;
+  const float* Dg = base + d.dinv;
+  double* X = xbase + xoff[mi] + (int64_t)col0 * n;
+  const int rmask = ring - 1;  // ring: power of two >= w + 2 SNB
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);      // kStages
+  float* stage = reinterpret_cast<float*>(smem_raw + 128);     // kStages * SNB * ld
+  float* dstage = stage + (size_t)kStages * SNB * ld;          // kStages * 256
+  float* win = dstage + (size_t)kStages * 256;                 // ring * KP
+  float* red = win + (size_t)ring * KP;                        // NW * SNB * KP
+  float* zb = red + (size_t)NW * SNB * KP;                     // SNB * KP
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  const int nb = (n + SNB - 1) / SNB;
+  const int nvis = 2 * nb;
+
+  // columns >= k stay zero in the ring and in zb
+  for (int idx = tid; idx < ring * KP; idx += kThreads) win[idx] = 0.f;
+  for (int idx = tid; idx < SNB * KP; idx += kThreads) zb[idx] = 0.f;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto issue = [&](int v) {
+    const int blk = visit_block(v, nb), kb = blk * SNB;
+    const int b = min(SNB, n - kb);
+    const int s = v % kStages;
+    const uint32_t bytes = (uint32_t)((size_t)b * ld * sizeof(float));
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bars[s], bytes + 256 * (uint32_t)sizeof(float));
+    bulk_load(stage + (size_t)s * SNB * ld, L + (int64_t)kb * ld, bytes, &bars[s]);
+    bulk_load(dstage + (size_t)s * 256, Dg + (int64_t)blk * 256, 256 * sizeof(float), &bars[s]);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
+  auto load_rows = [&](int r0, int cnt, float* out) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+      out[e] = (c < k && t < cnt) ? (float)X[(int64_t)c * n + r0 + t] : 0.f;
+    }
+  };
+  float xr[2];
+  load_rows(0, min(SNB, n), xr);
+  bool ok = true;
+  int waited = 0;
+  int lo = n;
+  const int nsteps = (w + 7) >> 3;  // k-steps of eight band positions
+  const int s0 = (nsteps * wid) / NW, s1 = (nsteps * (wid + 1)) / NW;
+
+  for (int v = 0; v < nvis; ++v) {
+    const int s = v % kStages;
+    const uint32_t parity = (uint32_t)((v / kStages) & 1);
+    if (tid == 0 && ok && issued < nvis) issue(issued++);
+    const int kb = visit_block(v, nb) * SNB;
+    const int b = min(SNB, n - kb);
+    const float* S = stage + (size_t)s * SNB * ld;
+    const float* D = dstage + (size_t)s * 256;   // M(i, t) at D[16 t + i]
+    if (v < nb) {
+      // ---------------- forward
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+        if (c < k) zb[t * KP + c] = xr[e];
+      }
+      if (v + 1 < nb) load_rows(kb + SNB, min(SNB, n - kb - SNB), xr);
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
+      {
+        // A(i, u) = L(kb + i, kb - w + u) = S[i ld + u - i] for u >= i and
+        // u >= w - kb (rows i = g, g + 8); B(u, c) = ring row kb - w + u
+        float acc[NT][3][4];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[nt][p][q] = 0.f;
+        const bool va = g < b, vb = g + 8 < b;
+        const int ia = g * (ld - 1), ib = (g + 8) * (ld - 1);
+        const int kfull = max(15, w - kb);   // from here every row's element is in band
+        for (int st8 = s0; st8 < s1; ++st8) {
+          const int u0 = 8 * st8;
+          const int k1 = u0 + tg, k2 = u0 + tg + 4;
+          const bool masked = u0 < kfull || u0 + 8 > w;
+          float x[4];
+          if (!masked) {
+            x[0] = va ? S[ia + k1] : 0.f;
+            x[1] = vb ? S[ib + k1] : 0.f;
+            x[2] = va ? S[ia + k2] : 0.f;
+            x[3] = vb ? S[ib + k2] : 0.f;
+          } else {
+            const int lo0 = max(0, w - kb);
+            x[0] = (va && k1 < w && k1 >= g && k1 >= lo0) ? S[ia + k1] : 0.f;
+            x[1] = (vb && k1 < w && k1 >= g + 8 && k1 >= lo0) ? S[ib + k1] : 0.f;
+            x[2] = (va && k2 < w && k2 >= g && k2 >= lo0) ? S[ia + k2] : 0.f;
+            x[3] = (vb && k2 < w && k2 >= g + 8 && k2 >= lo0) ? S[ib + k2] : 0.f;
+          }
+          uint32_t ah[4], al[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) split_tf32(x[q], ah[q], al[q]);
+          const float* r1 = win + (size_t)((kb - w + k1) & rmask) * KP + g;
+          const float* r2 = win + (size_t)((kb - w + k2) & rmask) * KP + g;
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            uint32_t bh[2], bl[2];
+            split_tf32(r1[8 * nt], bh[0], bl[0]);
+            split_tf32(r2[8 * nt], bh[1], bl[1]);
+            mma_tf32(acc[nt][0], al, bh);
+            mma_tf32(acc[nt][1], ah, bl);
+            mma_tf32(acc[nt][2], ah, bh);
+          }
+        }
+        // partial sums: rows g, g + 8, columns 8 nt + 2 tg (+1)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int row = g + ((q & 2) ? 8 : 0), col = 8 * nt + 2 * tg + (q & 1);
+            red[(size_t)(wid * SNB + row) * KP + col] = (acc[nt][0][q] + acc[nt][1][q]) + acc[nt][2][q];
+          }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, t = idx & 15;
+        float sum = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) sum += red[(size_t)(ww * SNB + t) * KP + c];
+        zb[t * KP + c] -= sum;
+      }
+      __syncthreads();
+      // y = M z: one (row, column) output per thread
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, i = idx & 15;
+        if (i < b) {
+          float y = 0.f;
+#pragma unroll
+          for (int t = 0; t < SNB; ++t)
+            if (t <= i) y += D[t * SNB + i] * zb[t * KP + c];
+          win[(size_t)((kb + i) & rmask) * KP + c] = y;
+          X[(int64_t)c * n + kb + i] = (double)y;
+        }
+      }
+      if (v == nb - 1) lo = max(0, kb - w);
+    } else {
+      // ---------------- backward
+      const int nlo = max(0, kb - SNB - w);
+      float er[2];
+      load_rows(nlo, lo - nlo, er);  // rows entering the ring (forward results)
+      if (ok) {
+        ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
+        waited += ok ? 1 : 0;
+      }
+      // x = M^T y into zb (the ring rows of the block are not needed again)
+      for (int idx = tid; idx < SNB * k; idx += kThreads) {
+        const int c = idx >> 4, t = idx & 15;
+        float x = 0.f;
+        if (t < b) {
+#pragma unroll
+          for (int j = 0; j < SNB; ++j) {
+            const int i = (t + j) & (SNB - 1);  // rotated: conflict-free reads of M
+            if (i >= t && i < b) x += D[t * SNB + i] * win[(size_t)((kb + i) & rmask) * KP + c];
+          }
+          X[(int64_t)c * n + kb + t] = (double)x;
+        }
+        zb[t * KP + c] = x;
+      }
+      __syncthreads();
+      // rows [lo, kb): y_rr -= sum_t L(kb + t, rr) x_t, 16-row tiles
+      {
+        uint32_t bh[2][NT][2], bl[2][NT][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            split_tf32(zb[(8 * h + tg) * KP + 8 * nt + g], bh[h][nt][0], bl[h][nt][0]);
+            split_tf32(zb[(8 * h + tg + 4) * KP + 8 * nt + g], bh[h][nt][1], bl[h][nt][1]);
+          }
+        const int cnt = kb - lo;
+        const int ntile = (cnt + 15) >> 4;
+        for (int tile = wid; tile < ntile; tile += NW) {
+          const int ra = lo + 16 * tile + g, rb = ra + 8;
+          float cacc[NT][4];
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const int col = 8 * nt + 2 * tg;
+            const float2 ya = ra < kb ? *reinterpret_cast<const float2*>(win + (size_t)(ra & rmask) * KP + col)
+                                      : make_float2(0.f, 0.f);
+            const float2 yb = rb < kb ? *reinterpret_cast<const float2*>(win + (size_t)(rb & rmask) * KP + col)
+                                      : make_float2(0.f, 0.f);
+            cacc[nt][0] = ya.x; cacc[nt][1] = ya.y; cacc[nt][2] = yb.x; cacc[nt][3] = yb.y;
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            // A(rr, t) = -L(kb + t, rr) = -S[t ld + rr - kb - t + w], t <= min(b - 1, rr - kb + w)
+            float x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = (q & 1) ? rb : ra;
+              const int t = 8 * h + tg + ((q & 2) ? 4 : 0);
+              const int off = rr - kb - t + w;
+              x[q] = (rr < kb && t < b && off >= 0) ? -S[t * ld + off] : 0.f;
+            }
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_tf32(x[q], ah[q], al[q]);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              mma_tf32(cacc[nt], al, bh[h][nt]);
+              mma_tf32(cacc[nt], ah, bl[h][nt]);
+              mma_tf32(cacc[nt], ah, bh[h][nt]);
+            }
+          }
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const int col = 8 * nt + 2 * tg;
+            if (ra < kb) *reinterpret_cast<float2*>(win + (size_t)(ra & rmask) * KP + col) = make_float2(cacc[nt][0], cacc[nt][1]);
+            if (rb < kb) *reinterpret_cast<float2*>(win + (size_t)(rb & rmask) * KP + col) = make_float2(cacc[nt][2], cacc[nt][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
+        if (c < k && t < lo - nlo) win[(size_t)((nlo + t) & rmask) * KP + c] = er[e];
+      }
+      lo = nlo;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && !ok)
+    for (int v = waited; v < issued; ++v)
+      mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
+}
+
 constexpr int kNB = 32;
 constexpr size_t kSmemCap = 200 * 1024;
 
@@ -859,6 +1384,22 @@ template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
                           DevStatus* st, cudaStream_t s) {
   if (count <= 0) return GENEO_OK;
+  // FP32: left-looking tensor-core kernel when a panel's rows and two chunk
+  // buffers fit in shared memory
+  if constexpr (sizeof(T) == 4) {
+    const size_t tc_smem = potrf_tc_smem(max_w);
+    if (tc_smem <= 227 * 1024) {
+      GENEO_CUDA(cudaFuncSetAttribute(k_band_potrf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem));
+      k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st); note_launch();
+      GENEO_CUDA(cudaGetLastError());
+      if (max_n > 0) {
+        const int nb = (max_n + 15) / 16;
+        k_band_dinv<T><<<dim3((nb + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
+        GENEO_CUDA(cudaGetLastError());
+      }
+      return GENEO_OK;
+    }
+  }
   // the panel starts at a 16-byte boundary (diag block: 32 x 33 values) and
   // its row stride phmax is a multiple of 4
   const size_t diag = (size_t)kNB * (kNB + 1) * sizeof(T);
@@ -926,6 +1467,39 @@ geneo_status_t launch_multi(int CT, int stages, int count, size_t smem, cudaStre
   return GENEO_ERR_ARG;
 }
 
+// Shared memory of the tensor-core multi-right-hand-side solve.
+inline size_t mtc_smem(int max_w, int ring, int NT, int stages) {
+  const int ld = band_ld(max_w);
+  const int KP = NT == 1 ? 8 : (NT == 4 ? 40 : 24);
+  return 128 + sizeof(float) * ((size_t)stages * (16 * ld + 256) + (size_t)ring * KP +
+                                (size_t)(kThreads / 32 + 1) * 16 * KP);
+}
+
+template <int NT, int kStages>
+geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float* base, const BandDesc* d_desc,
+                            double* xbase, const int64_t* xoff, int c0, int kc,
+                            const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
+  auto kern = k_band_solve_mtc<NT, kStages>;
+  GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
+  note_launch();
+  GENEO_CUDA(cudaGetLastError());
+  return GENEO_OK;
+}
+
+geneo_status_t launch_mtc(int NT, int stages, int count, size_t smem, cudaStream_t s, const float* base,
+                          const BandDesc* d_desc, double* xbase, const int64_t* xoff, int c0, int kc,
+                          const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
+#define GENEO_MTC(nt, sg)                                                                          \
+  if (NT == nt && stages == sg)                                                                    \
+    return launch_mtc_t<nt, sg>(count, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, \
+                                ring, st);
+  GENEO_MTC(1, 2) GENEO_MTC(1, 3) GENEO_MTC(1, 4) GENEO_MTC(2, 2) GENEO_MTC(2, 3) GENEO_MTC(2, 4)
+  GENEO_MTC(3, 2) GENEO_MTC(3, 3) GENEO_MTC(3, 4) GENEO_MTC(4, 2) GENEO_MTC(4, 3) GENEO_MTC(4, 4)
+#undef GENEO_MTC
+  return GENEO_ERR_ARG;
+}
+
 // Shared memory of the resident-vector one-right-hand-side solve.
 template <typename T>
 size_t res_smem(int max_w, int max_n, int snb, int stages) {
@@ -970,6 +1544,24 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
+  }
+  // FP32 factors: tensor-core kernel, up to 32 columns per launch
+  if constexpr (sizeof(T) == 4) {
+    const int ring = next_pow2(max_w + 32);
+    if (mtc_smem(max_w, ring, 1, 2) <= 227 * 1024) {
+      for (int c0 = 0; c0 < nrhs; c0 += 32) {
+        const int kc = std::min(32, nrhs - c0);
+        int NT = (kc + 7) / 8;
+        while (NT > 1 && mtc_smem(max_w, ring, NT, 2) > 227 * 1024) --NT;
+        const int kk = std::min(kc, 8 * NT);
+        int stages = 4;
+        while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > 227 * 1024) --stages;
+        GENEO_TRY(launch_mtc(NT, stages, count, mtc_smem(max_w, ring, NT, stages), s, base, d_desc, xbase,
+                             xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
+        if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch
+      }
+      return GENEO_OK;
+    }
   }
   // register-tiled kernel: up to 32 (FP32) or 16 (FP64) columns per launch
   {

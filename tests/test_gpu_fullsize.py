@@ -53,7 +53,10 @@ def test_darcy_128_sampled_parity(c2, precision):
         info = sol.solve(b, x, tol=1e-8, maxit=2000)
         xr = x.cpu().numpy()
         res = np.linalg.norm(prob.b - prob.A @ xr) / np.linalg.norm(prob.b)
-        assert info["converged"] and res <= 1.01e-8
+        # stopping rule on the recursive residual; the true residual may drift
+        # from it by rounding (see test_gpu_parity.TRUE_RES_FACTOR)
+        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= 1.5e-8, \
+            (info["rel_residual"], res)
         assert 30 <= info["iterations"] <= 120
     finally:
         sol.close()

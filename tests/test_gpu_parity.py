@@ -2,9 +2,16 @@
 
 Tolerances (FP64 path): eigenvalues |lambda - lambda*| <= 1e-6 max(|lambda*|,
 1e-3 tau); partition of unity and D_j bit-exact; PCG iterations within +-2 of
-the oracle; final relative residual <= 1e-8; relative error <= 1e-7 against
-a direct solve, or the oracle's own error at the same tolerance times 10 when
-that is larger (the error a residual of 1e-8 implies depends on kappa(A)).
+the oracle; relative error <= 1e-7 against a direct solve, or the oracle's own
+error at the same tolerance times 10 when that is larger (the error a residual
+of 1e-8 implies depends on kappa(A)).
+
+Residuals: PCG stops when the recursive residual ||r_k|| / ||b|| (the one the
+iteration updates) reaches tol, so that is asserted <= tol.  The true residual
+||b - A x|| / ||b|| drifts from it by rounding in the recurrences; at contrast
+1e6 the oracle's own FP64 PCG on the 2D channel problem stops with a true /
+recursive ratio of 1.41, so the true residual is bounded by TRUE_RES_FACTOR *
+tol.
 """
 import numpy as np
 import pytest
@@ -14,6 +21,8 @@ import oracle
 from gpu_helpers import compare_setup, gpu_solve, oracle_reference_solution, run_gpu
 
 pytestmark = pytest.mark.gpu
+
+TRUE_RES_FACTOR = 1.5
 
 
 def _c1(contrast=1e6, seed=0):
@@ -34,7 +43,8 @@ def _full_check(prob, tau=0.3, nev=10, fixed=False, form="paper", tol=1e-8):
         xo, ito, _, kapo = orc.solve(tol=tol)
         xs = oracle_reference_solution(prob)
         res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and res <= 1.01 * tol
+        assert info["converged"] and info["rel_residual"] <= tol and res <= TRUE_RES_FACTOR * tol, \
+            (info["rel_residual"], res)
         assert abs(info["iterations"] - ito) <= 2, (info["iterations"], ito)
         err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
         err_o = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
@@ -156,7 +166,8 @@ def test_host_memory_path():
         x = np.zeros(prob.n)
         info = G.geneo_pcg_solve(h, np.ascontiguousarray(prob.b), x, tol=1e-8, mem=G.GENEO_MEM_HOST)
         res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and res <= 1.01e-8
+        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
+            (info["rel_residual"], res, info["iterations"])
     finally:
         G.geneo_destroy(h)
 
@@ -188,7 +199,8 @@ def test_mixed_precision_matches_oracle(case):
         x, info = gpu_solve(sol, prob)
         _, ito, _, _ = orc.solve(tol=1e-8)
         res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and res <= 1.01e-8
+        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
+            (info["rel_residual"], res, info["iterations"])
         assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
     finally:
         sol.close()
