@@ -194,6 +194,136 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
   }
 }
 
+// Right-looking factorisation of one large band over many SMs (the coarse
+// matrix A_H, whose FP64 work is too much for one SM): per panel of NB
+// columns one block factors the diagonal block and solves the panel rows
+// (k_band_panel), then a grid of 64 x 64 tiles applies the rank-NB update to
+// the trailing window (k_band_trail).  Two launches per panel; the stream
+// orders them.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_band_panel(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb, DevStatus* st) {
+  const BandDesc d = descs[0];
+  const int n = d.n, w = d.w;
+  const int64_t ld = d.ld;
+  T* L = base + d.off;
+  __shared__ T Dk[NB * (NB + 1)];
+  constexpr int DS = NB + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int b = min(NB, n - kb);
+  const int h = min(w, n - kb - b);
+  for (int idx = tid; idx < NB * NB; idx += nt) {
+    const int r = idx / NB, c = idx % NB;
+    T v = T(0);
+    if (r < b && c < b && r >= c && r - c <= w) v = L[bidx(kb + r, kb + c, w, ld)];
+    Dk[r * DS + c] = v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    for (int t = 0; t < b; ++t) {
+      if (lane == t) {
+        T dv = Dk[t * DS + t];
+        if (!finite_pos(dv)) {
+          record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)kb + t);
+          dv = T(1);
+        }
+        Dk[t * DS + t] = sqrt(dv);
+      }
+      __syncwarp();
+      const T piv = Dk[t * DS + t];
+      if (lane > t && lane < b) Dk[lane * DS + t] /= piv;
+      __syncwarp();
+      if (lane > t && lane < b) {
+        const T lrt = Dk[lane * DS + t];
+        for (int u = t + 1; u <= lane; ++u) Dk[lane * DS + u] -= lrt * Dk[u * DS + t];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB * NB; idx += nt) {
+    const int r = idx / NB, c = idx % NB;
+    if (r < b && c < b && r >= c && r - c <= w) L[bidx(kb + r, kb + c, w, ld)] = Dk[r * DS + c];
+  }
+  for (int i = tid; i < h; i += nt) {
+    const int rr = kb + b + i;
+    T x[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) x[t] = (t < b && rr - (kb + t) <= w) ? L[bidx(rr, kb + t, w, ld)] : T(0);
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      if (t < b) {
+        T v = x[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) v -= x[u] * Dk[t * DS + u];
+        x[t] = v / Dk[t * DS + t];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      if (t < b && rr - (kb + t) <= w) L[bidx(rr, kb + t, w, ld)] = x[t];
+  }
+}
+
+// Trailing update of panel kb: C(i, i') -= sum_t P(i, t) P(i', t) over the
+// h x h window below the panel, block (ti, tj) of 64 x 64 (ti >= tj), 4 x 4
+// register tiles, panel rows staged in shared memory.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_band_trail(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb) {
+  const BandDesc d = descs[0];
+  const int n = d.n, w = d.w;
+  const int64_t ld = d.ld;
+  T* L = base + d.off;
+  const int b = min(NB, n - kb);
+  const int h = min(w, n - kb - b);
+  // block index -> (ti, tj) in the lower triangle, row-major
+  const int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int i0 = 64 * ti, j0 = 64 * tj;
+  if (i0 >= h) return;
+  __shared__ T Pi[NB][64 + 1], Pj[NB][64 + 1];
+  for (int idx = threadIdx.x; idx < NB * 64; idx += blockDim.x) {
+    const int tt = idx / 64, r = idx % 64;
+    const int ii = i0 + r, jj = j0 + r;
+    Pi[tt][r] = (tt < b && ii < h && b + ii - tt <= w) ? L[bidx(kb + b + ii, kb + tt, w, ld)] : T(0);
+    Pj[tt][r] = (tt < b && jj < h && b + jj - tt <= w) ? L[bidx(kb + b + jj, kb + tt, w, ld)] : T(0);
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 16 x 16 threads, 4 x 4 each
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+  for (int tt = 0; tt < b; ++tt) {
+    T pr[4], pc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      pr[a] = Pi[tt][4 * ty + a];
+      pc[a] = Pj[tt][4 * tx + a];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] += pr[a] * pc[c];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + 4 * ty + a;
+    if (i >= h) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int jj = j0 + 4 * tx + c;
+      if (jj < h && jj <= i) L[bidx(kb + b + i, kb + b + jj, w, ld)] -= acc[a][c];
+    }
+  }
+}
+
 // Inverses M of the 16 x 16 diagonal blocks of a factored band (FP64
 // arithmetic, rounded to T), stored transposed (M(i, t) at 16 t + i): a
 // half-warp per block, lane c forms column c by forward substitution.  The solves apply these blocks as small products, so
@@ -1399,6 +1529,24 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
       }
       return GENEO_OK;
     }
+  }
+  // one large matrix (the coarse matrix): spread each panel's update over SMs
+  if (count == 1 && max_n > 256 && max_w >= 128) {
+    constexpr int PB = 32;
+    for (int kb = 0; kb < max_n; kb += PB) {
+      k_band_panel<T, PB><<<1, kThreads, 0, s>>>(base, d_desc, kb, st); note_launch();
+      const int b = std::min(PB, max_n - kb);
+      const int h = std::min(max_w, max_n - kb - b);
+      if (h > 0) {
+        const int T64 = (h + 63) / 64;
+        k_band_trail<T, PB><<<T64 * (T64 + 1) / 2, kThreads, 0, s>>>(base, d_desc, kb); note_launch();
+      }
+    }
+    GENEO_CUDA(cudaGetLastError());
+    const int nb = (max_n + 15) / 16;
+    k_band_dinv<T><<<dim3((nb + 15) / 16, 1), 256, 0, s>>>(base, d_desc); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
   }
   // the panel starts at a 16-byte boundary (diag block: 32 x 33 values) and
   // its row stride phmax is a multiple of 4
