@@ -577,12 +577,12 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
         for (int q = 0; q < 4; ++q)
           Red[((size_t)kq * 16 + nt * 4 + q) * 32 + lane] = (acc[nt][0][q] + acc[nt][1][q]) + acc[nt][2][q];
       __syncthreads();
-      // warps 0-3: n-tile wid; U = A - sum into the panel block (zero
-      // outside the lower band)
-      if (wid < 4) {
-        const int nt2 = wid;
+      // warp w: n-tile w & 3, outputs q of half w >> 2; U = A - sum into the
+      // panel block (zero outside the lower band)
+      {
+        const int nt2 = wid & 3, qh = wid >> 2;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 2 * qh; q < 2 * qh + 2; ++q) {
           float sum = 0.f;
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) sum += Red[((size_t)kk * 16 + nt2 * 4 + q) * 32 + lane];
@@ -597,28 +597,40 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
       }
       __syncthreads();
     }
-    // ---- factor the panel block: diagonal block in place by warp 0
+    // ---- factor the panel block: diagonal block by warp 0 in registers
+    // (lane r holds row r; column t is broadcast by shuffles)
     if (tid < 32) {
-      for (int t = 0; t < b; ++t) {
-        if (lane == t) {
-          float dv = Us[t * kUS + t];
-          if (!finite_pos(dv)) {
-            record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
-            dv = 1.f;
+      float a[kPB];
+#pragma unroll
+      for (int u = 0; u < kPB; ++u) a[u] = (lane < b && u <= lane) ? Us[lane * kUS + u] : 0.f;
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        if (t < b) {
+          float dtt = __shfl_sync(0xffffffffu, a[t], t);
+          if (!finite_pos(dtt)) {
+            if (lane == 0) record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
+            dtt = 1.f;
           }
-          Us[t * kUS + t] = sqrtf(dv);
+          const float ltt = sqrtf(dtt);
+          if (lane == t) a[t] = ltt;
+          else if (lane > t) a[t] = a[t] / ltt;
+#pragma unroll
+          for (int u = t + 1; u < kPB; ++u) {
+            const float lut = __shfl_sync(0xffffffffu, a[t], u);
+            if (lane >= u) a[u] -= a[t] * lut;
+          }
         }
-        __syncwarp();
-        const float piv = Us[t * kUS + t];
-        if (lane > t && lane < b) Us[lane * kUS + t] /= piv;
-        __syncwarp();
-        if (lane > t && lane < b) {
-          const float lrt = Us[lane * kUS + t];
-          for (int u = t + 1; u <= lane; ++u) Us[lane * kUS + u] -= lrt * Us[u * kUS + t];
-        }
-        __syncwarp();
       }
-      Dinv[lane] = lane < b ? 1.f / Us[lane * kUS + lane] : 0.f;
+      if (lane < b) {
+#pragma unroll
+        for (int u = 0; u < kPB; ++u)
+          if (u <= lane) Us[lane * kUS + u] = a[u];
+      }
+      float dl = 0.f;
+#pragma unroll
+      for (int u = 0; u < kPB; ++u)
+        if (u == lane) dl = a[u];
+      Dinv[lane] = lane < b ? 1.f / dl : 0.f;
     }
     __syncthreads();
     // rows below: x L_jj^T = u, one row per thread (stride kUS: no bank conflicts)

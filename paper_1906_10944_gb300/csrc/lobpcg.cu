@@ -154,12 +154,16 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRefT<SS> Src, Co
 template <typename S>
 __global__ void __launch_bounds__(kT, 2)
 k_gram_part(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym, double* __restrict__ Gp,
-            int ldg, int nsub, const int32_t* __restrict__ skip) {
+            int ldg, int nsub, const int32_t* __restrict__ skip, int only_wide = 0) {
   using C = S;
   const int j = blockIdx.y, rs = blockIdx.x;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
   const int p = cr_w(A, j), q = cr_w(B, j);
+  if (only_wide) {
+    const int tp0 = (p + 3) >> 2, tq0 = (q + 3) >> 2;
+    if ((sym ? tp0 * (tp0 + 1) / 2 : tp0 * tq0) <= kT && 4 * (tp0 + tq0) <= 128) return;  // done by k_gram_one
+  }
   double* G = Gp + ((int64_t)rs * nsub + j) * ldg * ldg;
   if (p <= 0 || q <= 0) return;
   const S* a = cr_ptr(A, d, j);
@@ -265,6 +269,149 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym
         if (r < p && c < q) G[(int64_t)c * ldg + r] = acc[u][z * 4 + y];
       }
   }
+}
+
+// Partial Gram matrices for the common case of at most kT 4 x 4 tiles and at
+// most 128 padded columns of A and B together: one tile per thread (row groups when there
+// are fewer tiles than threads), columns zero-padded to a multiple of four in
+// shared memory (no bounds tests in the inner loop), and the next chunk of
+// rows prefetched into registers while the current one is multiplied (one
+// barrier per chunk).  Subdomains with more tiles are left to k_gram_part
+// (mode 1); this kernel skips them, and k_gram_part in mode 1 skips the
+// others.  Same partial layout and summation order rules as k_gram_part.
+template <typename S>
+__global__ void __launch_bounds__(kT, 2)
+k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym, double* __restrict__ Gp,
+           int ldg, int nsub, const int32_t* __restrict__ skip) {
+  using C = S;
+  const int j = blockIdx.y, rs = blockIdx.x;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(B, j);
+  if (p <= 0 || q <= 0) return;
+  const int tp = (p + 3) >> 2, tq = (q + 3) >> 2;
+  const int ntiles = sym ? tp * (tp + 1) / 2 : tp * tq;
+  if (ntiles > kT || 4 * (tp + tq) > 128) return;  // left to k_gram_part
+  double* G = Gp + ((int64_t)rs * nsub + j) * ldg * ldg;
+  const S* a = cr_ptr(A, d, j);
+  const S* b = cr_ptr(B, d, j);
+  const int pp = 4 * tp, qp = 4 * tq;          // padded widths
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  C* buf = reinterpret_cast<C*>(gsm_raw);      // 2 x kRB x (pp + qp)
+  const int chunk = kRB * (pp + qp);
+  const int groups = kT / ntiles;
+  const int tx = (int)threadIdx.x;
+  const int g = tx / ntiles;
+  const int t = tx < groups * ntiles ? tx % ntiles : -1;
+  int ti = 0, tj = 0;
+  if (t >= 0) {
+    if (sym) {
+      int r = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+      while ((r + 1) * (r + 2) / 2 <= t) ++r;
+      while (r * (r + 1) / 2 > t) --r;
+      ti = r;
+      tj = t - r * (r + 1) / 2;
+    } else {
+      ti = t % tp;
+      tj = t / tp;
+    }
+  }
+  C acc[16];
+#pragma unroll
+  for (int z = 0; z < 16; ++z) acc[z] = 0;
+  const int r0 = (int)((int64_t)rs * d.nN / kRS), r1 = (int)((int64_t)(rs + 1) * d.nN / kRS);
+  // thread (lane, warp) handles row `lane` of a chunk and the combined
+  // [A | B] columns warp + 8 u (kRB = 32 rows, 8 warps, up to 128 columns);
+  // rows beyond the range and padded columns are zero
+  static_assert(kRB == 32 && kT == 256, "chunk mapping assumes 32 rows and 8 warps");
+  constexpr int kPre = 16;
+  const int lane = tx & 31, wq = tx >> 5;
+  C pre[kPre];
+  auto fetch = [&](int rb) {
+    const bool rowok = rb + lane < r1;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int cc = wq + 8 * u;
+      C v = 0;
+      if (rowok) {
+        if (cc < p) v = (C)a[(int64_t)cc * d.nN + rb + lane];
+        else if (cc >= pp && cc - pp < q) v = (C)b[(int64_t)(cc - pp) * d.nN + rb + lane];
+      }
+      pre[u] = v;
+    }
+  };
+  auto stash = [&](C* dst) {
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int cc = wq + 8 * u;
+      if (cc < pp + qp) dst[lane * (pp + qp) + cc] = pre[u];
+    }
+  };
+  int cur = 0;
+  if (r0 < r1) {
+    fetch(r0);
+    stash(buf);
+  }
+  __syncthreads();
+  for (int rb = r0; rb < r1; rb += kRB) {
+    const bool more = rb + kRB < r1;
+    if (more) fetch(rb + kRB);
+    const C* X = buf + (size_t)cur * chunk;
+    if (t >= 0) {
+      const int nr = min(kRB, r1 - rb);
+      for (int r = g; r < nr; r += groups) {
+        const C* row = X + r * (pp + qp);
+        C av[4], bv[4];
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+          av[z] = row[4 * ti + z];
+          bv[z] = row[pp + 4 * tj + z];
+        }
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[z * 4 + y] += av[z] * bv[y];
+      }
+    }
+    if (more) stash(buf + (size_t)(cur ^ 1) * chunk);
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (groups > 1) {
+    // sum the row groups' partials: group-major in shared memory
+    double* red = reinterpret_cast<double*>(gsm_raw);  // groups * ntiles * 16 <= kT * 16
+    if (t >= 0)
+#pragma unroll
+      for (int z = 0; z < 16; ++z) red[((size_t)g * ntiles + t) * 16 + z] = acc[z];
+    __syncthreads();
+    for (int o = threadIdx.x; o < ntiles * 16; o += kT) {
+      const int tt = o / 16, z = o % 16;
+      double sum = 0.0;
+      for (int gg = 0; gg < groups; ++gg) sum += red[((size_t)gg * ntiles + tt) * 16 + z];
+      int a0, b0;
+      if (sym) {
+        int r = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= tt) ++r;
+        while (r * (r + 1) / 2 > tt) --r;
+        a0 = r;
+        b0 = tt - r * (r + 1) / 2;
+      } else {
+        a0 = tt % tp;
+        b0 = tt / tp;
+      }
+      const int rr = 4 * a0 + z / 4, cc = 4 * b0 + z % 4;
+      if (rr < p && cc < q) G[(int64_t)cc * ldg + rr] = sum;
+    }
+    return;
+  }
+  if (t >= 0)
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int r = 4 * ti + z, c = 4 * tj + y;
+        if (r < p && c < q) G[(int64_t)c * ldg + r] = acc[z * 4 + y];
+      }
 }
 
 // G = sum of the row-split partials (fixed order); sym mirrors the lower part.
@@ -895,6 +1042,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const size_t nn_smem = sizeof(double) * W3 * W3;
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
+  // k_gram_one: two chunks of kRB rows x (p + q) padded columns (widths <= 64
+  // there, since wider subdomains go to k_gram_part), or the group partials
+  const size_t gram1_smem = sizeof(double) * std::max((size_t)2 * kRB * 128, (size_t)16 * kT);
+  GENEO_CUDA(cudaFuncSetAttribute(k_gram_one<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram1_smem));
+  GENEO_CUDA(cudaFuncSetAttribute(k_gram_one<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram1_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
   GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
@@ -998,7 +1150,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       }
     }
     const int pr = h->prof.begin(sizeof(S) == 4 ? GENEO_PROF_ORTHO32 : GENEO_PROF_GRAM, fl, by, st);
-    k_gram_part<S><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    k_gram_one<S><<<dim3(kRS, N), kT, gram1_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    if (W3 > 64) {
+      k_gram_part<S><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip, 1);
+      note_launch();
+    }
     k_gram_reduce<S><<<N, kT, 0, st>>>(h->dsub, A, B, sym, Gp, G, ldg, N, skip); note_launch();
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
