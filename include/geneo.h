@@ -133,9 +133,15 @@ typedef struct {
  *  eig_tol    relative residual ||B x - nu K x|| / (||B x|| + nu ||K x||)
  *             at which an eigenpair counts as converged (default 1e-6).
  *  eig_maxit  iteration cap of the block eigensolver (default 100).
- *  guard      extra block vectors beyond nev_max (default min(5, nev_max)).
+ *  guard      extra block vectors beyond the wanted pairs (default
+ *             min(3, nev_max): on 3D Darcy 128^3 a guard of 3 needs one more
+ *             iteration than 5 but less work in total).
  *  precision  geneo_precision_t (default GENEO_PREC_FP64).
  *  profile    0 (default) or 1, see geneo_coarse_info_t.prof_*.
+ *  first_nev  wanted pairs of the eigensolver's narrow first pass; a
+ *             subdomain whose first pass finds that many eigenvalues below
+ *             tau is solved again with nev_max (default -1: min(8, nev_max);
+ *             ignored with fixed_nev).
  *  seed       seed of the counter-based start vectors (SplitMix64).
  */
 typedef struct {
@@ -153,6 +159,7 @@ typedef struct {
                           and one synchronisation at the end of each call.
                           It creates CUDA events as it goes, so handles used
                           with geneo_pcg_solve_noalloc keep it at 0. */
+  int32_t first_nev;
   uint64_t seed;
 } geneo_options_t;
 

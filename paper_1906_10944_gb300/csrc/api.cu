@@ -144,6 +144,7 @@ void geneo_default_options(geneo_options_t* o) {
   o->guard = -1;
   o->precision = GENEO_PREC_FP64;
   o->profile = 0;
+  o->first_nev = -1;
   o->seed = 0x5EED5EEDull;
 }
 
@@ -169,7 +170,7 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   h->opt = o;
   h->fp32 = o.precision == GENEO_PREC_FP32;
   h->prof.on = o.profile != 0;
-  const int guard = o.guard >= 0 ? o.guard : std::min(5, o.nev_max);
+  const int guard = o.guard >= 0 ? o.guard : std::min(3, o.nev_max);
   h->s_block = std::min(o.nev_max + guard, 34);
   h->stream = (cudaStream_t)stream;
   if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||

@@ -1384,7 +1384,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   // below tau.  A subdomain whose narrow block fills with converged
   // eigenvalues below tau is solved again with the full width (pass 2).
   const int guard = s - nev;
-  const int nev1 = o.fixed_nev ? nev : std::min(nev, kFirstPassNev);
+  const int nev1 = o.fixed_nev ? nev : std::min(nev, o.first_nev > 0 ? o.first_nev : kFirstPassNev);
   {
     std::vector<int32_t> hs1(N), hn1(N, nev1);
     for (int j = 0; j < N; ++j) hs1[j] = std::min(nev1 + guard, h->hsub[j].nN);

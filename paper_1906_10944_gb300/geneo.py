@@ -55,7 +55,7 @@ class geneo_options_t(C.Structure):
         ("tau", C.c_double), ("sigma", C.c_double), ("eig_tol", C.c_double),
         ("nev_max", C.c_int32), ("fixed_nev", C.c_int32), ("eig_form", C.c_int32),
         ("eig_maxit", C.c_int32), ("guard", C.c_int32), ("precision", C.c_int32),
-        ("profile", C.c_int32), ("seed", C.c_uint64),
+        ("profile", C.c_int32), ("first_nev", C.c_int32), ("seed", C.c_uint64),
     ]
 
 
