@@ -58,10 +58,16 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   auto t_all = std::chrono::steady_clock::now();
   const bool host = p->mem == GENEO_MEM_HOST;
   DevMem tmp;
+  // on every exit: the aux stream (A_j factorisation) finishes before the
+  // temporaries it may read are freed
   struct Guard {
     DevMem& t;
-    ~Guard() { t.free_all(); }
-  } guard{tmp};
+    cudaStream_t a;
+    ~Guard() {
+      if (a) cudaStreamSynchronize(a);
+      t.free_all();
+    }
+  } guard{tmp, h->aux};
   h->n = p->n;
   h->nnz = p->nnz;
   h->N = p->n_sub;
@@ -122,6 +128,8 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   // a6-a7: coarse basis, coarse matrix, factorisation
   GENEO_TRY(geneo::build_coarse(h, asmb, X, tmp, s, &h->setup_ms[4], &h->setup_ms[5], &h->setup_ms[6]));
   GENEO_TRY(geneo::alloc_solver(h));
+  // join the A_j factorisation (aux stream) before the temporaries go
+  GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_afac, 0));
   GENEO_TRY(geneo::check_status(h, s));
   h->setup_ms[7] = ms_since(t_all);
   h->prof.collect();
@@ -175,7 +183,8 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   h->stream = (cudaStream_t)stream;
   if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_afac, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     geneo_destroy(h);
     return GENEO_ERR_CUDA;
@@ -290,6 +299,7 @@ void geneo_destroy(geneo_handle_t h) {
   h->mem.free_all();
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_afac) cudaEventDestroy(h->ev_afac);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->hpin) cudaFreeHost(h->hpin);
   delete h;

@@ -549,8 +549,10 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   }
   h->prof.end(pK, s);
   h->prof.end(pA, h->aux);
-  GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
-  GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+  // the A_j factors are only needed by the solves: their factorisation keeps
+  // running on the aux stream beside the eigensolver and is joined at the
+  // end of the setup
+  GENEO_CUDA(cudaEventRecord(h->ev_afac, h->aux));
   ev.stop();
   h->factor_ms = ev.ms;
   h->factor_flops = 0.0;

@@ -9,6 +9,7 @@ struct geneo_handle_s {
   cudaStream_t stream = 0;  // stream of the last synchronising call
   cudaStream_t aux = nullptr;       // second stream (coarse solve, concurrent factorisations)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_afac = nullptr;   // end of the A_j factorisation on the aux stream
   geneo_options_t opt{};
   bool fp32 = false;
 
