@@ -328,7 +328,11 @@ void geneo_free_host(void* p);
  * (all handles, all threads). */
 int64_t geneo_launch_count(void);
 
-/* Release all device memory of the handle (NULL is allowed). */
+/* Release all device memory of the handle (NULL is allowed).  Waits for the
+ * handle's work on the stream of its last call (setup, apply or solve),
+ * which must still exist, and returns the memory to the device's
+ * stream-ordered pool (the library allocates from that pool and keeps freed
+ * memory there for later handles). */
 void geneo_destroy(geneo_handle_t h);
 
 /* Static string describing a status code. */

@@ -58,6 +58,8 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   auto t_all = std::chrono::steady_clock::now();
   const bool host = p->mem == GENEO_MEM_HOST;
   DevMem tmp;
+  tmp.stream = s;
+  h->mem.stream = s;
   // on every exit: the aux stream (A_j factorisation) finishes before the
   // temporaries it may read are freed
   struct Guard {
@@ -173,6 +175,16 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
       (o.eig_form != GENEO_EIG_PAPER && o.eig_form != GENEO_EIG_FULL) ||
       (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32))
     return GENEO_ERR_ARG;
+  // keep freed device memory in the stream-ordered pool for the next setup
+  {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
   geneo_handle_s* h = new (std::nothrow) geneo_handle_s();
   if (!h) return GENEO_ERR_OOM;
   h->opt = o;
@@ -203,6 +215,7 @@ geneo_status_t geneo_apply(geneo_handle_t h, const double* r_dev, double* z_dev,
                            void* stream) {
   if (!h || !r_dev || !z_dev || nrhs < 0) return GENEO_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  h->mem.stream = s;  // the handle's last stream (see geneo_destroy)
   for (int i = 0; i < nrhs; ++i)
     GENEO_TRY(geneo::apply_prec(h, r_dev + (int64_t)i * h->n, z_dev + (int64_t)i * h->n, s));
   return GENEO_OK;
@@ -218,6 +231,7 @@ geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int
   geneo_status_t worst = GENEO_OK;
   double *db = nullptr, *dx = nullptr;
   DevMem tmp;
+  tmp.stream = s;
   if (mem == GENEO_MEM_HOST) {
     GENEO_TRY(tmp.get(&db, (size_t)n));
     GENEO_TRY(tmp.get(&dx, (size_t)n));
@@ -295,8 +309,12 @@ geneo_status_t geneo_get_subdomain(geneo_handle_t h, int32_t j, int32_t* n_neu, 
 
 void geneo_destroy(geneo_handle_t h) {
   if (!h) return;
+  // the handle's memory goes back to the pool in the order of the stream of
+  // its last call, after that call's work
   if (h->aux) cudaStreamSynchronize(h->aux);
+  cudaStreamSynchronize(h->mem.stream);
   h->mem.free_all();
+  cudaStreamSynchronize(h->mem.stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_afac) cudaEventDestroy(h->ev_afac);

@@ -235,9 +235,14 @@ inline double band_entries(double n, double w) {
 // --------------------------------------------------------------------------
 // Simple owning device buffer.
 // --------------------------------------------------------------------------
+// Device allocations from the stream-ordered pool: allocated and freed in
+// the order of `stream` (set by the owner before use), so a free does not
+// synchronise the device and concurrent handles on other streams keep
+// running; the pool keeps freed memory for the next allocation.
 struct DevMem {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
+  cudaStream_t stream = nullptr;
   geneo_status_t alloc(void** p, size_t n);
   template <typename T>
   geneo_status_t get(T** p, size_t count) {

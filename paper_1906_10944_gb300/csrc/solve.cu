@@ -293,6 +293,7 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
   const int gridv = nb;
   std::vector<double> ha(std::max(maxit, 1) + 1), hb(std::max(maxit, 1) + 1);
   if (h->hist_cap < (int)ha.size()) {
+    h->mem.stream = s;  // the handle's last stream (see geneo_destroy)
     if (h->hist) h->mem.release(h->hist);
     h->hist = nullptr;
     GENEO_TRY(h->mem.get(&h->hist, 2 * ha.size()));
@@ -459,6 +460,7 @@ thread_local double t_tri[2][kNoAllocMaxIt + 1];
 geneo_status_t pcg_noalloc(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
                            geneo_solve_info_t* info, cudaStream_t s) {
   if (maxit > kNoAllocMaxIt) return GENEO_ERR_ARG;
+  h->mem.stream = s;  // the handle's last stream (see geneo_destroy); no allocation
   double* scr = nullptr;
   GENEO_TRY(pcg_scratch(&scr));
   const int64_t n = h->n;

@@ -23,10 +23,10 @@ const std::string& last_cuda_error() { return g_last_cuda_error; }
 geneo_status_t DevMem::alloc(void** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 16;
-  cudaError_t e = cudaMalloc(p, n);
+  cudaError_t e = cudaMallocAsync(p, n, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
     *p = nullptr;
     return GENEO_ERR_OOM;
   }
@@ -38,7 +38,7 @@ geneo_status_t DevMem::alloc(void** p, size_t n) {
 void DevMem::release(void* p) {
   for (auto& q : ptrs) {
     if (q == p) {
-      cudaFree(q);
+      cudaFreeAsync(q, stream);
       q = nullptr;
     }
   }
@@ -46,7 +46,7 @@ void DevMem::release(void* p) {
 
 void DevMem::free_all() {
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, stream);
   ptrs.clear();
   bytes = 0;
 }
