@@ -260,6 +260,60 @@ def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
             "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
 
 
+# serving trace: seeded Darcy problems of mixed size (16^3-element subdomains,
+# overlap 2, nev <= 20, FP32 factors), 1..4 right-hand sides per request
+SERVE_SIZES = [(32, 32, 32), (48, 48, 48), (64, 64, 64)]
+SERVE_SEEDS = (11, 12)
+SERVE_WORKERS = 3
+SERVE_LOAD = 0.6
+
+
+def serve_measure(n_requests, warmup, tol):
+    """p50/p99 latency of a Poisson request trace at SERVE_LOAD of the
+    estimated capacity of SERVE_WORKERS concurrent streams."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_1906_10944_gb300 import geneo as G
+    from paper_1906_10944_gb300 import serve as S
+    problems, rhs, keep, sizes = [], [], [], []
+    for nel in SERVE_SIZES:
+        for seed in SERVE_SEEDS:
+            kap = gen.kappa_grf_layers_3d(nel, seed=seed)
+            prob = gen.darcy_problem(nel, kap, tuple(e // 16 for e in nel), 2)
+            dev = {k: torch.from_numpy(v).cuda() for k, v in G.problem_arrays(prob).items()}
+            keep.append(dev)
+            opts = G.geneo_default_options(nev_max=20, tau=0.3, precision=G.GENEO_PREC_FP32)
+            problems.append((G.make_problem(dev, prob.n, prob.n_sub, 8, 1, G.GENEO_MEM_DEVICE), opts, prob.n))
+            rng = np.random.default_rng(1000 + len(rhs))
+            b = rng.uniform(-1.0, 1.0, (4, prob.n))
+            b[:, prob.dirichlet != 0] = 0.0
+            rhs.append(torch.from_numpy(b.reshape(-1)).cuda())
+            sizes.append(prob.n)
+    torch.cuda.synchronize()
+    solve = S.library_solve_fn(problems, rhs, tol=tol)
+    make_stream = torch.cuda.Stream
+    # calibration: every problem once, alone (also the warm-up of each size)
+    cal = [S.Request(i, i, nrhs=1, arrival=0.0) for i in range(len(problems))]
+    S.Server(solve, workers=1, make_stream=make_stream).run(cal)
+    mean_service = sum(r.service for r in cal) / len(cal)
+    rate = SERVE_LOAD * SERVE_WORKERS / mean_service
+    trace = S.poisson_trace(n_requests + warmup, rate, seed=5, choices=len(problems))
+    reqs = [S.Request(i, k, nrhs=m, arrival=t) for i, (t, k, m) in enumerate(trace)]
+    S.Server(solve, workers=SERVE_WORKERS, make_stream=make_stream).run(reqs)
+    out = S.summarize(reqs, warmup=warmup)
+    bad = sum(1 for r in reqs if r.result and not all(i["converged"] for i in r.result))
+    out.update({"workers": SERVE_WORKERS, "offered_rps": rate, "load": SERVE_LOAD,
+                "calibrated_service_ms": 1e3 * mean_service, "unconverged": bad,
+                "trace": "%d requests after %d warm-up, Poisson arrivals (seed 5); 3D Darcy %s elements "
+                         "(dofs %s), two kappa seeds each, 16^3-element subdomains, overlap 2, nev<=20, "
+                         "FP32 factors; 1-4 right-hand sides per request; latency = arrival to last "
+                         "solution (setup + PCG rel-res %g + release)"
+                         % (n_requests, warmup, "/".join("%d^3" % e[0] for e in SERVE_SIZES),
+                            "/".join(str(n) for n in sizes[::2]), tol)})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,6 +329,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=3)
     ap.add_argument("--ref-pcg-iters", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
+    ap.add_argument("--serve-requests", type=int, default=150)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -421,6 +477,10 @@ def main():
                          "iterations" % (r["n_sample"], r["sample_s"], prob.n_sub,
                                          info_m["iterations"])}
 
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = serve_measure(args.serve_requests, 15, args.tol)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -437,6 +497,7 @@ def main():
             "e2e": e2e, "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
             "roofline": roofline, "cpu_baseline": cpu,
             "compare": compare,
+            "serve": serve,
             "detail": {"pcg_iterations": info_m["iterations"], "rel_residual_true": main_run["res"],
                        "kappa_estimate": info_m["kappa_estimate"], "dim_coarse": qm["dim_coarse"],
                        "eig_iterations": qm["eig_iterations"], "block_size": qm["block_size"],

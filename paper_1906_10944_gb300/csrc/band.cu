@@ -1532,7 +1532,7 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
   if constexpr (sizeof(T) == 4) {
     const size_t tc_smem = potrf_tc_smem(max_w);
     if (tc_smem <= 227 * 1024) {
-      GENEO_CUDA(cudaFuncSetAttribute(k_band_potrf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem));
+      GENEO_CUDA(allow_smem(k_band_potrf_tc));
       k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st); note_launch();
       GENEO_CUDA(cudaGetLastError());
       if (max_n > 0) {
@@ -1568,8 +1568,7 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
   const size_t panel = (size_t)phmax * kNB * sizeof(T);
   if (diag + panel <= kSmemCap) {
     auto kern = k_band_potrf<T, kNB, true>;
-    GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(diag + panel)));
+    GENEO_CUDA(allow_smem(kern));
     kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, phmax, st); note_launch();
   } else {
     auto kern = k_band_potrf<T, kNB, false>;
@@ -1605,7 +1604,7 @@ geneo_status_t launch_multi_t(int count, size_t smem, cudaStream_t s, const T* b
                               double* xbase, const int64_t* xoff, int c0, int kc,
                               const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
   auto kern = k_band_solve_multi<T, CT, kStages>;
-  GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GENEO_CUDA(allow_smem(kern));
   kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
@@ -1641,7 +1640,7 @@ geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float*
                             double* xbase, const int64_t* xoff, int c0, int kc,
                             const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
   auto kern = k_band_solve_mtc<NT, kStages>;
-  GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GENEO_CUDA(allow_smem(kern));
   kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
@@ -1689,7 +1688,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
       if (smem <= 227 * 1024) {
         auto kern = stages == 4 ? k_band_solve_res<T, 4>
                   : stages == 3 ? k_band_solve_res<T, 3> : k_band_solve_res<T, 2>;
-        GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GENEO_CUDA(allow_smem(kern));
         kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, nrhs_dev, skip_dev, st); note_launch();
         GENEO_CUDA(cudaGetLastError());
         return GENEO_OK;
@@ -1701,7 +1700,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
     const size_t smem = solve_smem<T>(max_w, 1, ring, snb, 2);
     if (smem > 227 * 1024) return GENEO_ERR_ARG;
     auto kern = snb == 16 ? k_band_solve<T, 16, 1, 2> : k_band_solve<T, 4, 1, 2>;
-    GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GENEO_CUDA(allow_smem(kern));
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
@@ -1752,7 +1751,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
   const size_t smem = solve_smem<T>(max_w, kmax, ring, snb, stg);
   if (smem > 227 * 1024) return GENEO_ERR_ARG;  // band too wide for the streamed solve
   auto kern = snb == 16 ? k_band_solve<T, 16, 8, stg> : k_band_solve<T, 4, 8, stg>;
-  GENEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GENEO_CUDA(allow_smem(kern));
   for (int c0 = 0; c0 < nrhs; c0 += kmax) {
     const int kc = std::min(kmax, nrhs - c0);
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st); note_launch();

@@ -252,6 +252,22 @@ struct DevMem {
   void free_all();
 };
 
+// Allow a kernel all the dynamic shared memory the device can give it (the
+// opt-in maximum less its static shared memory).  The limit belongs to the
+// kernel and is shared by every host thread, so it is not set to one
+// launch's size, which would race with concurrent launches of other sizes on
+// other streams; each launch still requests only what it uses.
+template <typename K>
+inline cudaError_t allow_smem(K kern) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  int dev = 0, v = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, v - (int)a.sharedSizeBytes);
+}
+
 // --------------------------------------------------------------------------
 // Kernel launchers implemented in the .cu files.
 // --------------------------------------------------------------------------

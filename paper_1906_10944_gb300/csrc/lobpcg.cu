@@ -1033,25 +1033,25 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const int wmax = W3;
   const size_t dense_smem = dense_smem_bytes<double>(wmax);
   const size_t dense_smem32 = dense_smem_bytes<float>(wmax);
-  GENEO_CUDA(cudaFuncSetAttribute(k_svqb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_svqb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem32));
-  GENEO_CUDA(cudaFuncSetAttribute(k_cholqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem));
+  GENEO_CUDA(allow_smem(k_svqb<double>));
+  GENEO_CUDA(allow_smem(k_svqb<float>));
+  GENEO_CUDA(allow_smem(k_cholqr));
+  GENEO_CUDA(allow_smem(k_rr));
   int32_t* redo = nullptr;
   GENEO_TRY(tmp.get(&redo, (size_t)N));
   const size_t nn_smem = sizeof(double) * W3 * W3;
   const size_t gram_smem = sizeof(double) * std::max(2 * kRB * (kMaxW + 1), 16 * kT);
-  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
+  GENEO_CUDA(allow_smem(k_gram_part<double>));
   // k_gram_one: two chunks of kRB rows x (p + q) padded columns (widths <= 64
   // there, since wider subdomains go to k_gram_part), or the group partials
   const size_t gram1_smem = sizeof(double) * std::max((size_t)2 * kRB * 128, (size_t)16 * kT);
-  GENEO_CUDA(cudaFuncSetAttribute(k_gram_one<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram1_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gram_one<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram1_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
-  GENEO_CUDA(cudaFuncSetAttribute(k_gemm32<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nn_smem));
+  GENEO_CUDA(allow_smem(k_gram_one<double>));
+  GENEO_CUDA(allow_smem(k_gram_one<float>));
+  GENEO_CUDA(allow_smem(k_gram_part<float>));
+  GENEO_CUDA(allow_smem(k_gemm_nn));
+  GENEO_CUDA(allow_smem(k_gemm32<float, float>));
+  GENEO_CUDA(allow_smem(k_gemm32<float, double>));
+  GENEO_CUDA(allow_smem(k_gemm32<double, double>));
 
   const bool f32 = h->fp32;
   // FP32 copies for the first orthogonalisation pass: [X, Q] and [KX, KQ]

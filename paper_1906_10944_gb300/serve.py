@@ -1,0 +1,150 @@
+"""Concurrent solve service over the C ABI.
+
+A request is one linear system family A x_i = b_i (i < nrhs): the GenEO
+setup of A (Sections 3 and 4), PCG for each right-hand side (Section 5) and
+the release of the handle.  Worker threads take requests first come, first
+served, each on its own CUDA stream, so the setups and solves of different
+requests overlap on the GPU (the library allocates from the stream-ordered
+pool, so no call synchronises the device).  Latency is measured from a
+request's arrival to its last solution.
+
+The arithmetic lives in the library; this module only queues, dispatches and
+records times.  `solve_fn` may be replaced (tests use a host stand-in).
+"""
+import math
+import queue
+import random
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Any, Callable, List, Optional
+
+
+@dataclass
+class Request:
+    """One request: `payload` is handed to the solve function."""
+    rid: int
+    payload: Any
+    nrhs: int = 1
+    arrival: float = 0.0          # seconds after the start of the trace
+    start: float = math.nan       # service start (same clock)
+    finish: float = math.nan      # last solution ready (same clock)
+    result: Any = None
+    error: Optional[str] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+    @property
+    def service(self) -> float:
+        return self.finish - self.start
+
+
+def poisson_trace(n: int, rate: float, seed: int, choices: int, max_nrhs: int = 4):
+    """Seeded arrival offsets (exponential gaps of mean 1 / rate), the index of
+    the problem each request uses and its number of right-hand sides."""
+    rng = random.Random(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.expovariate(rate)
+        out.append((t, rng.randrange(choices), 1 + rng.randrange(max_nrhs)))
+    return out
+
+
+def library_solve_fn(problems, rhs, tol=1e-8, maxit=2000):
+    """Solve function over the library: problems[k] = (geneo_problem_t,
+    geneo_options_t, n); rhs[k] = device tensor (n * max_nrhs) of right-hand
+    sides; the payload of a request is the index k.  Returns the list of
+    solve infos.  One output buffer per worker thread."""
+    import torch
+    from . import geneo as G
+    local = threading.local()
+
+    def solve(req: Request, stream):
+        k = req.payload
+        problem, opts, n = problems[k]
+        x = getattr(local, "x", None)
+        if x is None or x.numel() < n * req.nrhs:
+            with torch.cuda.stream(stream):
+                x = torch.empty(max(n * req.nrhs, 1), dtype=torch.float64, device="cuda")
+            local.x = x
+        h = G.geneo_setup(problem, opts, stream)
+        try:
+            infos = [G.geneo_pcg_solve(h, rhs[k][i * n:(i + 1) * n], x[i * n:(i + 1) * n], 1, tol, maxit,
+                                       G.GENEO_MEM_DEVICE, stream=stream) for i in range(req.nrhs)]
+        finally:
+            G.geneo_destroy(h)
+        return infos
+
+    return solve
+
+
+class Server:
+    """`workers` threads, each with its own stream (`make_stream()`), serving
+    requests first come, first served."""
+
+    def __init__(self, solve_fn: Callable, workers: int = 3, make_stream: Optional[Callable] = None):
+        self.solve_fn = solve_fn
+        self.workers = workers
+        self.make_stream = make_stream
+
+    def run(self, requests: List[Request]) -> List[Request]:
+        """Release each request at its arrival offset and return them all
+        with start, finish and result filled in."""
+        q: "queue.Queue[Optional[Request]]" = queue.Queue()
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+
+        def worker():
+            stream = self.make_stream() if self.make_stream else None
+            while True:
+                req = q.get()
+                if req is None:
+                    return
+                req.start = now()
+                try:
+                    req.result = self.solve_fn(req, stream)
+                except Exception as e:  # recorded, the service continues
+                    req.error = repr(e)
+                req.finish = now()
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
+        for th in threads:
+            th.start()
+        for req in sorted(requests, key=lambda r: r.arrival):
+            delay = req.arrival - now()
+            if delay > 0:
+                time.sleep(delay)
+            q.put(req)
+        for _ in threads:
+            q.put(None)
+        for th in threads:
+            th.join()
+        return requests
+
+
+def percentile(values, p):
+    """Nearest-rank percentile (p in [0, 100])."""
+    v = sorted(values)
+    if not v:
+        return math.nan
+    k = max(0, min(len(v) - 1, int(math.ceil(p / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def summarize(requests: List[Request], warmup: int = 0):
+    """Latency percentiles, throughput and solves per second over the
+    requests after the first `warmup` arrivals."""
+    done = sorted(requests, key=lambda r: r.arrival)[warmup:]
+    ok = [r for r in done if r.error is None]
+    lat = [r.latency for r in ok]
+    span = max(r.finish for r in ok) - min(r.arrival for r in ok) if ok else math.nan
+    return {
+        "requests": len(done), "errors": len(done) - len(ok),
+        "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+        "mean_service_ms": 1e3 * sum(r.service for r in ok) / max(len(ok), 1),
+        "achieved_rps": len(ok) / span if ok else math.nan,
+        "solves_per_s": sum(r.nrhs for r in ok) / span if ok else math.nan,
+    }
