@@ -143,6 +143,12 @@ typedef struct {
  *             tau is solved again with nev_max (default -1: min(8, nev_max);
  *             ignored with fixed_nev).
  *  seed       seed of the counter-based start vectors (SplitMix64).
+ *  fp32_pivot_tol  GENEO_PREC_FP32 only: a K_j or A_j whose FP32 Cholesky
+ *             meets a pivot <= this value (the bands are equilibrated to a
+ *             unit diagonal) is factored and solved in FP64 instead
+ *             (adaptive precision per subdomain; default 1e-4, in [0, 1)).
+ *             Those subdomains also orthogonalise their eigensolver blocks
+ *             in FP64.
  */
 typedef struct {
   double tau;
@@ -161,6 +167,7 @@ typedef struct {
                           with geneo_pcg_solve_noalloc keep it at 0. */
   int32_t first_nev;
   uint64_t seed;
+  double fp32_pivot_tol;
 } geneo_options_t;
 
 typedef struct geneo_handle_s* geneo_handle_t;
@@ -202,6 +209,8 @@ typedef struct {
   int32_t coarse_bandwidth;  /* half bandwidth of the banded A_H factor */
   int32_t eig_iterations;    /* block eigensolver iterations (max over batch) */
   int32_t block_size;        /* eigensolver block width s */
+  int32_t fp64_factors_K;    /* GENEO_PREC_FP32: K_j factored in FP64 */
+  int32_t fp64_factors_A;    /* GENEO_PREC_FP32: A_j factored in FP64 */
   int64_t device_bytes;      /* device memory held by the handle */
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse

@@ -129,9 +129,12 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   }
   // a6-a7: coarse basis, coarse matrix, factorisation
   GENEO_TRY(geneo::build_coarse(h, asmb, X, tmp, s, &h->setup_ms[4], &h->setup_ms[5], &h->setup_ms[6]));
-  GENEO_TRY(geneo::alloc_solver(h));
-  // join the A_j factorisation (aux stream) before the temporaries go
+  // join the A_j factorisation (aux stream) before the temporaries go; A_j
+  // whose FP32 factor had a weak pivot are factored again in FP64
   GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_afac, 0));
+  GENEO_TRY(geneo::check_status(h, s));
+  GENEO_TRY(geneo::refactor_weak_A(h, asmb, tmp, s));
+  GENEO_TRY(geneo::alloc_solver(h));
   GENEO_TRY(geneo::check_status(h, s));
   h->setup_ms[7] = ms_since(t_all);
   h->prof.collect();
@@ -155,6 +158,7 @@ void geneo_default_options(geneo_options_t* o) {
   o->precision = GENEO_PREC_FP64;
   o->profile = 0;
   o->first_nev = -1;
+  o->fp32_pivot_tol = 1e-4;
   o->seed = 0x5EED5EEDull;
 }
 
@@ -172,6 +176,7 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   geneo_default_options(&o);
   if (opt) o = *opt;
   if (o.nev_max < 0 || o.nev_max > 34 || !(o.sigma < 0.0) || !(o.eig_tol > 0.0) || o.eig_maxit < 1 ||
+      !(o.fp32_pivot_tol >= 0.0 && o.fp32_pivot_tol < 1.0) ||
       (o.eig_form != GENEO_EIG_PAPER && o.eig_form != GENEO_EIG_FULL) ||
       (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32))
     return GENEO_ERR_ARG;
@@ -264,6 +269,8 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->coarse_bandwidth = h->wH;
   info->eig_iterations = h->eig_iters;
   info->block_size = h->s_block;
+  info->fp64_factors_K = h->nK64;
+  info->fp64_factors_A = h->nA64;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->factor_flops = h->factor_flops;

@@ -280,33 +280,36 @@ __global__ void k_pencil(const SubDesc* __restrict__ sub, const double* __restri
   }
 }
 
+// Band entries of K_j / A_j for the batch `bd` (descriptor id = subdomain).
 template <typename T>
-__global__ void k_band_fill_K(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
-                              const int32_t* __restrict__ lcol, const double* __restrict__ lK,
-                              T* __restrict__ band) {
-  const SubDesc d = sub[blockIdx.x];
-  const int64_t ld = band_ld(d.wK);
-  T* L = band + d.bandK;
+__global__ void k_band_fill_K(const SubDesc* __restrict__ sub, const BandDesc* __restrict__ bd,
+                              const int64_t* __restrict__ lrow, const int32_t* __restrict__ lcol,
+                              const double* __restrict__ lK, T* __restrict__ band) {
+  const BandDesc b = bd[blockIdx.x];
+  const SubDesc d = sub[b.id];
+  const int64_t ld = b.ld;
+  T* L = band + b.off;
   for (int a = threadIdx.x; a < d.nN; a += blockDim.x)
     for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
-      const int b = lcol[e];
-      if (b <= a) L[(int64_t)a * ld + (b - a + d.wK)] = (T)lK[e];
+      const int c = lcol[e];
+      if (c <= a) L[(int64_t)a * ld + (c - a + b.w)] = (T)lK[e];
     }
 }
 
 template <typename T>
-__global__ void k_band_fill_A(const SubDesc* __restrict__ sub, const int32_t* __restrict__ dpos,
-                              const int32_t* __restrict__ nToD, const int64_t* __restrict__ lrow,
-                              const int32_t* __restrict__ lcol, const double* __restrict__ lA,
-                              T* __restrict__ band) {
-  const SubDesc d = sub[blockIdx.x];
-  const int64_t ld = band_ld(d.wA);
-  T* L = band + d.bandA;
+__global__ void k_band_fill_A(const SubDesc* __restrict__ sub, const BandDesc* __restrict__ bd,
+                              const int32_t* __restrict__ dpos, const int32_t* __restrict__ nToD,
+                              const int64_t* __restrict__ lrow, const int32_t* __restrict__ lcol,
+                              const double* __restrict__ lA, T* __restrict__ band) {
+  const BandDesc b = bd[blockIdx.x];
+  const SubDesc d = sub[b.id];
+  const int64_t ld = b.ld;
+  T* L = band + b.off;
   for (int i = threadIdx.x; i < d.nD; i += blockDim.x) {
     const int a = dpos[d.offN + i];
     for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e) {
       const int i2 = nToD[d.offN + lcol[e]];
-      if (i2 >= 0 && i2 <= i) L[(int64_t)i * ld + (i2 - i + d.wA)] = (T)lA[e];
+      if (i2 >= 0 && i2 <= i) L[(int64_t)i * ld + (i2 - i + b.w)] = (T)lA[e];
     }
   }
 }
@@ -315,6 +318,59 @@ inline int grid_for(int64_t m) { return (int)std::min<int64_t>(std::max<int64_t>
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Adaptive precision per subdomain: an FP32 factorisation with a weak pivot
+// (coefficient contrast beyond what FP32 resolves) is redone in FP64 from
+// the FP64 local matrix, and its FP32 descriptor gets n = 0 so the FP32
+// solves skip it.  Descriptor ids stay the subdomain indices, so the FP64
+// batch solves into the same vectors.
+struct Refactor {
+  double* band = nullptr;
+  BandDesc* desc = nullptr;
+  int count = 0, maxw = 0, maxn = 0;
+};
+
+geneo_status_t refactor_fp64(geneo_handle_s* h, const AssemblyOut& a, const int32_t* weak_dev, bool isK,
+                             std::vector<BandDesc>& hmain, BandDesc* dmain, DevMem& mem, cudaStream_t s,
+                             Refactor* r) {
+  const int N = h->N;
+  std::vector<int32_t> flag(N);
+  GENEO_CUDA(cudaMemcpyAsync(flag.data(), weak_dev, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  std::vector<BandDesc> rd;
+  int64_t tot = 0;
+  for (int j = 0; j < N; ++j) {
+    if (!flag[j]) continue;
+    const SubDesc& d = h->hsub[j];
+    const int n = isK ? d.nN : d.nD, w = isK ? d.wK : d.wA;
+    rd.push_back(BandDesc{tot, n, w, j, band_ld(w), 0, -1});
+    tot += (int64_t)n * band_ld(w);
+    r->maxw = std::max(r->maxw, w);
+    r->maxn = std::max(r->maxn, n);
+  }
+  r->count = (int)rd.size();
+  if (rd.empty()) return GENEO_OK;
+  int64_t dv = tot;
+  for (BandDesc& b : rd) {
+    b.dinv = dv;
+    dv += dinv_elems(b.n);
+  }
+  GENEO_TRY(mem.get(&r->band, (size_t)dv));
+  GENEO_TRY(mem.get(&r->desc, rd.size()));
+  GENEO_CUDA(cudaMemsetAsync(r->band, 0, sizeof(double) * tot, s));
+  GENEO_CUDA(cudaMemcpyAsync(r->desc, rd.data(), sizeof(BandDesc) * rd.size(), cudaMemcpyHostToDevice, s));
+  const int R = r->count;
+  if (isK)
+    k_band_fill_K<double><<<R, kT, 0, s>>>(h->dsub, r->desc, a.lrow, a.lcol, a.lK, r->band);
+  else
+    k_band_fill_A<double><<<R, kT, 0, s>>>(h->dsub, r->desc, h->dpos, h->nToD, a.lrow, a.lcol, a.lA, r->band);
+  note_launch();
+  GENEO_CUDA(cudaGetLastError());
+  GENEO_TRY(band_potrf<double>(r->band, r->desc, R, r->maxw, r->maxn, h->dstat, s));
+  for (const BandDesc& b : rd) hmain[b.id].n = 0;
+  GENEO_CUDA(cudaMemcpyAsync(dmain, hmain.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
+  return GENEO_OK;
 }
 
 }  // namespace
@@ -473,11 +529,15 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   // band storage, descriptors
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   // the inverted diagonal blocks follow all bands in the same allocation
+  // with FP32 factors the bands are equilibrated (S A S, s = diag^{-1/2}):
+  // FP32 Cholesky of the unscaled matrices breaks down at coefficient
+  // contrasts near 1e8; the row scalings follow the inverted blocks
+  const bool equil = h->fp32;
   int64_t dinvK_tot = 0, dinvA_tot = 0;
   int maxnK = 0;
   for (const SubDesc& d : h->hsub) {
-    dinvK_tot += dinv_elems(d.nN);
-    dinvA_tot += dinv_elems(d.nD);
+    dinvK_tot += dinv_elems(d.nN) + (equil ? scl_elems(d.nN) : 0);
+    dinvA_tot += dinv_elems(d.nD) + (equil ? scl_elems(d.nD) : 0);
     maxnK = std::max(maxnK, d.nN);
   }
   GENEO_TRY(tmp.alloc(&out.bandK, esz * (size_t)std::max<int64_t>(bandK_tot + dinvK_tot, 1)));
@@ -488,10 +548,10 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   int64_t dK = bandK_tot, dA = bandA_tot;
   for (int j = 0; j < N; ++j) {
     const SubDesc& d = h->hsub[j];
-    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, band_ld(d.wK), dK};
-    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, band_ld(d.wA), dA};
-    dK += dinv_elems(d.nN);
-    dA += dinv_elems(d.nD);
+    bk[j] = BandDesc{d.bandK, d.nN, d.wK, j, band_ld(d.wK), dK, equil ? dK + dinv_elems(d.nN) : -1};
+    ba[j] = BandDesc{d.bandA, d.nD, d.wA, j, band_ld(d.wA), dA, equil ? dA + dinv_elems(d.nD) : -1};
+    dK += dinv_elems(d.nN) + (equil ? scl_elems(d.nN) : 0);
+    dA += dinv_elems(d.nD) + (equil ? scl_elems(d.nD) : 0);
   }
   // largest factorisations first: blocks are dispatched in index order, so
   // this shortens the tail of the last wave (descriptors carry their id)
@@ -511,13 +571,21 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   GENEO_TRY(h->mem.get(&h->dbandA, (size_t)N));
   GENEO_CUDA(cudaMemcpyAsync(out.dbandK, bk.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandA, ba.data(), sizeof(BandDesc) * N, cudaMemcpyHostToDevice, s));
+  out.hbandK = bk;
+  out.hbandA = ba;
   if (h->fp32) {
-    k_band_fill_K<float><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (float*)out.bandK); note_launch();
-    k_band_fill_A<float><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
+    GENEO_TRY(tmp.get(&out.weak, (size_t)2 * N));
+    GENEO_CUDA(cudaMemsetAsync(out.weak, 0, sizeof(int32_t) * 2 * N, s));
+  }
+  if (h->fp32) {
+    k_band_fill_K<float><<<N, kT, 0, s>>>(h->dsub, out.dbandK, out.lrow, out.lcol, out.lK,
+                                          (float*)out.bandK); note_launch();
+    k_band_fill_A<float><<<N, kT, 0, s>>>(h->dsub, h->dbandA, h->dpos, h->nToD, out.lrow, out.lcol, lA,
                                           (float*)h->bandA); note_launch();
   } else {
-    k_band_fill_K<double><<<N, kT, 0, s>>>(h->dsub, out.lrow, out.lcol, out.lK, (double*)out.bandK); note_launch();
-    k_band_fill_A<double><<<N, kT, 0, s>>>(h->dsub, h->dpos, h->nToD, out.lrow, out.lcol, lA,
+    k_band_fill_K<double><<<N, kT, 0, s>>>(h->dsub, out.dbandK, out.lrow, out.lcol, out.lK,
+                                           (double*)out.bandK); note_launch();
+    k_band_fill_A<double><<<N, kT, 0, s>>>(h->dsub, h->dbandA, h->dpos, h->nToD, out.lrow, out.lcol, lA,
                                            (double*)h->bandA); note_launch();
   }
   GENEO_CUDA(cudaGetLastError());
@@ -541,8 +609,13 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   const int pK = h->prof.begin(GENEO_PROF_FACTOR, flK, byK, s);
   const int pA = h->prof.begin(GENEO_PROF_FACTOR, flA, byA, h->aux);
   if (h->fp32) {
-    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
-    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));
+    // a weak pivot flags the matrix for an FP64 factorisation instead of
+    // failing the setup
+    const float wt = (float)h->opt.fp32_pivot_tol;
+    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s, equil,
+                                out.weak, wt));
+    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux, equil,
+                                out.weak + N, wt));
   } else {
     GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
     GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));
@@ -559,7 +632,37 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   for (const SubDesc& d : h->hsub)
     h->factor_flops += band_factor_flops(d.nD, d.wA) + band_factor_flops(d.nN, d.wK);
   GENEO_TRY(check_status(h, s));
+  if (h->fp32) {
+    Refactor r;
+    GENEO_TRY(refactor_fp64(h, out, out.weak, true, out.hbandK, out.dbandK, tmp, s, &r));
+    out.bandK64 = r.band;
+    out.dbandK64 = r.desc;
+    out.nK64 = h->nK64 = r.count;
+    out.maxwK64 = r.maxw;
+    out.maxnK64 = r.maxn;
+    GENEO_TRY(check_status(h, s));
+  }
   *ms_factor = ms_since(t1);
+  return GENEO_OK;
+}
+
+geneo_status_t refactor_weak_A(geneo_handle_s* h, AssemblyOut& a, DevMem& tmp, cudaStream_t s) {
+  if (!h->fp32 || !a.weak) return GENEO_OK;
+  Refactor r;
+  GENEO_TRY(refactor_fp64(h, a, a.weak + h->N, false, a.hbandA, h->dbandA, h->mem, s, &r));
+  h->bandA64 = r.band;
+  h->dbandA64 = r.desc;
+  h->nA64 = r.count;
+  h->maxwA64 = r.maxw;
+  h->maxnA64 = r.maxn;
+  h->a64.assign(h->N, 0);
+  std::vector<BandDesc> rd(r.count);
+  if (r.count) {
+    GENEO_CUDA(cudaMemcpyAsync(rd.data(), r.desc, sizeof(BandDesc) * r.count, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+  }
+  for (const BandDesc& b : rd) h->a64[b.id] = 1;
+  (void)tmp;
   return GENEO_OK;
 }
 

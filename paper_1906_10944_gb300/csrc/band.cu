@@ -58,7 +58,7 @@ __device__ __forceinline__ int64_t bidx(int r, int c, int w, int64_t ld) {
 template <typename T, int NB, bool SMEMP>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
 k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax,
-             DevStatus* st) {
+             DevStatus* st, int32_t* __restrict__ weak, float weak_tol) {
   const BandDesc d = descs[blockIdx.x];
   const int n = d.n, w = d.w;
   const int64_t ld = d.ld;
@@ -86,7 +86,10 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
       for (int t = 0; t < b; ++t) {
         if (lane == t) {
           T dv = Dk[t * DS + t];
-          if (!finite_pos(dv)) {
+          if (weak) {
+            if (!(dv > T(weak_tol))) weak[d.id] = 1;
+            if (!finite_pos(dv)) dv = T(1);
+          } else if (!finite_pos(dv)) {
             record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)kb + t);
             dv = T(1);
           }
@@ -324,6 +327,56 @@ k_band_trail(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb) {
   }
 }
 
+// Equilibration of a band before its FP32 factorisation: s_r = a_rr^{-1/2}
+// (1 where a_rr is not positive: the factorisation reports it), then every
+// entry a_rc *= s_r s_c, so the factor is that of S A S (unit diagonal) and
+// A^{-1} = S (S A S)^{-1} S.  Grid: (row blocks, matrices).
+template <typename T>
+__global__ void k_band_equil_s(T* __restrict__ base, const BandDesc* __restrict__ descs) {
+  const BandDesc d = descs[blockIdx.y];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d.scl < 0 || r >= d.n) return;
+  const T a = base[d.off + (int64_t)r * d.ld + d.w];
+  base[d.scl + r] = a > T(0) ? T(1) / sqrt(a) : T(1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_band_equil_a(T* __restrict__ base, const BandDesc* __restrict__ descs) {
+  const BandDesc d = descs[blockIdx.y];
+  if (d.scl < 0) return;
+  const T* S = base + d.scl;
+  for (int i = 0; i < 16; ++i) {
+    const int r = blockIdx.x * 16 + i;
+    if (r >= d.n) return;
+    const T sr = S[r];
+    T* row = base + d.off + (int64_t)r * d.ld;
+    for (int off = max(0, d.w - r) + (int)threadIdx.x; off <= d.w; off += blockDim.x)
+      row[off] *= sr * S[r - d.w + off];
+  }
+}
+
+// x = s o x on columns [0, k) of the solve vectors (before and after the
+// solves that do not apply the scaling themselves)
+template <typename T>
+__global__ void k_band_scale_x(const T* __restrict__ base, const BandDesc* __restrict__ descs,
+                               double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0,
+                               int kcap, const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip) {
+  const BandDesc d = descs[blockIdx.y];
+  // vectors, counts and skip flags are indexed by the subdomain id (a
+  // batch may hold a subset of the subdomains)
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.y;
+  if (skip && skip[mi]) return;
+  if (d.scl < 0) return;
+  int k = kcap;
+  if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
+  const T* S = base + d.scl;
+  double* X = xbase + xoff[mi] + (int64_t)col0 * d.n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)k * d.n;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    X[idx] *= (double)S[idx % d.n];
+}
+
 // Inverses M of the 16 x 16 diagonal blocks of a factored band (FP64
 // arithmetic, rounded to T), stored transposed (M(i, t) at 16 t + i): a
 // half-warp per block, lane c forms column c by forward substitution.  The solves apply these blocks as small products, so
@@ -452,7 +505,8 @@ inline size_t potrf_tc_smem(int w) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, DevStatus* st) {
+k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, DevStatus* st,
+                int32_t* __restrict__ weak, float weak_tol) {
   const BandDesc d = descs[blockIdx.x];
   const int n = d.n, w = d.w;
   const int ld = d.ld;
@@ -617,7 +671,10 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
         }
         if (t < b) {
           float p = Us[t * kUS + t];
-          if (!finite_pos(p)) {
+          if (weak) {
+            if (tid == 0 && !(p > weak_tol)) weak[d.id] = 1;
+            if (!finite_pos(p)) p = 1.f;
+          } else if (!finite_pos(p)) {
             if (tid == 0) record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
             p = 1.f;
           }
@@ -681,12 +738,14 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
              double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
              const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
              DevStatus* st) {
-  const int mi = blockIdx.x;
+  const BandDesc d = descs[blockIdx.x];
+  // vectors, counts and skip flags are indexed by the subdomain id (a
+  // batch may hold a subset of the subdomains)
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
   int k = kcap;
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
-  const BandDesc d = descs[mi];
   const int n = d.n, w = d.w;
   if (n <= 0) return;
   const int ld = d.ld;
@@ -913,10 +972,12 @@ k_band_solve_res(const T* __restrict__ base, const BandDesc* __restrict__ descs,
                  double* __restrict__ xbase, const int64_t* __restrict__ xoff,
                  const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, DevStatus* st) {
   constexpr int SNB = 16;
-  const int mi = blockIdx.x;
+  const BandDesc d = descs[blockIdx.x];
+  // vectors, counts and skip flags are indexed by the subdomain id (a
+  // batch may hold a subset of the subdomains)
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
   if (nrhs_dev && nrhs_dev[mi] <= 0) return;
-  const BandDesc d = descs[mi];
   const int n = d.n, w = d.w;
   if (n <= 0) return;
   const int ld = d.ld;
@@ -952,7 +1013,8 @@ k_band_solve_res(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   int issued = 0;  // copies issued by thread 0
   if (tid == 0)
     for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
-  for (int i = tid; i < n; i += kThreads) vec[i] = (T)X[i];
+  const T* Sg = d.scl >= 0 ? base + d.scl : nullptr;  // equilibrated band: solve with S A S
+  for (int i = tid; i < n; i += kThreads) vec[i] = Sg ? (T)X[i] * Sg[i] : (T)X[i];
   __syncthreads();
   bool ok = true;
   int waited = 0;  // stages this thread has waited for
@@ -1034,7 +1096,7 @@ k_band_solve_res(const T* __restrict__ base, const BandDesc* __restrict__ descs,
     for (int v = waited; v < issued; ++v)
       mbar_wait_bounded(&bars[v % kStages], (uint32_t)((v / kStages) & 1), st, d.id, v);
   if (!ok) return;
-  for (int i = tid; i < n; i += kThreads) X[i] = (double)vec[i];
+  for (int i = tid; i < n; i += kThreads) X[i] = Sg ? (double)(vec[i] * Sg[i]) : (double)vec[i];
 }
 
 // Several right-hand sides (the eigensolver's K_j^{-1} blocks), at most
@@ -1059,12 +1121,14 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
   constexpr int SNB = 16;
   constexpr int KP = 2 * CT + 4;
   constexpr int NW = kThreads / 32;
-  const int mi = blockIdx.x;
+  const BandDesc d = descs[blockIdx.x];
+  // vectors, counts and skip flags are indexed by the subdomain id (a
+  // batch may hold a subset of the subdomains)
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
   int k = min(kcap, 2 * CT);
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
-  const BandDesc d = descs[mi];
   const int n = d.n, w = d.w;
   if (n <= 0) return;
   const int ld = d.ld;
@@ -1263,12 +1327,14 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
   constexpr int SNB = 16;
   constexpr int KP = MtcKP<NT>::v;
   constexpr int NW = kThreads / 32;
-  const int mi = blockIdx.x;
+  const BandDesc d = descs[blockIdx.x];
+  // vectors, counts and skip flags are indexed by the subdomain id (a
+  // batch may hold a subset of the subdomains)
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
   int k = min(kcap, 8 * NT);
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
-  const BandDesc d = descs[mi];
   const int n = d.n, w = d.w;
   if (n <= 0) return;
   const int ld = d.ld;
@@ -1310,15 +1376,23 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
   int issued = 0;
   if (tid == 0)
     for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
-  auto load_rows = [&](int r0, int cnt, float* out) {
+  const float* Sg = d.scl >= 0 ? base + d.scl : nullptr;  // equilibrated band: solve with S A S
+  // rows of the (16 x k) block of this thread; `scaled` multiplies by s
+  // (right-hand sides), the forward results re-entering the ring are not
+  auto load_rows = [&](int r0, int cnt, float* out, bool scaled) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
-      out[e] = (c < k && t < cnt) ? (float)X[(int64_t)c * n + r0 + t] : 0.f;
+      float v = 0.f;
+      if (c < k && t < cnt) {
+        v = (float)X[(int64_t)c * n + r0 + t];
+        if (scaled && Sg) v *= Sg[r0 + t];
+      }
+      out[e] = v;
     }
   };
   float xr[2];
-  load_rows(0, min(SNB, n), xr);
+  load_rows(0, min(SNB, n), xr, true);
   bool ok = true;
   int waited = 0;
   int lo = n;
@@ -1340,7 +1414,7 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
         const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
         if (c < k) zb[t * KP + c] = xr[e];
       }
-      if (v + 1 < nb) load_rows(kb + SNB, min(SNB, n - kb - SNB), xr);
+      if (v + 1 < nb) load_rows(kb + SNB, min(SNB, n - kb - SNB), xr, true);
       if (ok) {
         ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
         waited += ok ? 1 : 0;
@@ -1425,7 +1499,7 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
       // ---------------- backward
       const int nlo = max(0, kb - SNB - w);
       float er[2];
-      load_rows(nlo, lo - nlo, er);  // rows entering the ring (forward results)
+      load_rows(nlo, lo - nlo, er, false);  // rows entering the ring (forward results)
       if (ok) {
         ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
         waited += ok ? 1 : 0;
@@ -1440,7 +1514,7 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
             const int i = (t + j) & (SNB - 1);  // rotated: conflict-free reads of M
             if (i >= t && i < b) x += D[t * SNB + i] * win[(size_t)((kb + i) & rmask) * KP + c];
           }
-          X[(int64_t)c * n + kb + t] = (double)x;
+          X[(int64_t)c * n + kb + t] = Sg ? (double)(x * Sg[kb + t]) : (double)x;
         }
         zb[t * KP + c] = x;
       }
@@ -1525,15 +1599,20 @@ inline int next_pow2(int v) {
 
 template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
-                          DevStatus* st, cudaStream_t s) {
+                          DevStatus* st, cudaStream_t s, bool equil, int32_t* weak, float weak_tol) {
   if (count <= 0) return GENEO_OK;
+  if (equil && max_n > 0) {
+    k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
+    k_band_equil_a<T><<<dim3((max_n + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+  }
   // FP32: left-looking tensor-core kernel when a panel's rows and two chunk
   // buffers fit in shared memory
   if constexpr (sizeof(T) == 4) {
     const size_t tc_smem = potrf_tc_smem(max_w);
     if (tc_smem <= 227 * 1024) {
       GENEO_CUDA(allow_smem(k_band_potrf_tc));
-      k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st); note_launch();
+      k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st, weak, weak_tol); note_launch();
       GENEO_CUDA(cudaGetLastError());
       if (max_n > 0) {
         const int nb = (max_n + 15) / 16;
@@ -1544,7 +1623,7 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
     }
   }
   // one large matrix (the coarse matrix): spread each panel's update over SMs
-  if (count == 1 && max_n > 256 && max_w >= 128) {
+  if (count == 1 && max_n > 256 && max_w >= 128 && !weak) {
     constexpr int PB = 32;
     for (int kb = 0; kb < max_n; kb += PB) {
       k_band_panel<T, PB><<<1, kThreads, 0, s>>>(base, d_desc, kb, st); note_launch();
@@ -1569,10 +1648,10 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
   if (diag + panel <= kSmemCap) {
     auto kern = k_band_potrf<T, kNB, true>;
     GENEO_CUDA(allow_smem(kern));
-    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, phmax, st); note_launch();
+    kern<<<count, kThreads, diag + panel, s>>>(base, d_desc, phmax, st, weak, weak_tol); note_launch();
   } else {
     auto kern = k_band_potrf<T, kNB, false>;
-    kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st); note_launch();
+    kern<<<count, kThreads, diag, s>>>(base, d_desc, 0, st, weak, weak_tol); note_launch();
   }
   GENEO_CUDA(cudaGetLastError());
   if (max_n > 0) {
@@ -1667,33 +1746,13 @@ size_t res_smem(int max_w, int max_n, int snb, int stages) {
   return 128 + sizeof(T) * ((size_t)stages * (snb * ld + 256) + (size_t)((max_n + 3) & ~3) + snb);
 }
 
+// Solves with the kernels that do not apply a band's row scaling (the
+// caller scales the vectors around them).
 template <typename T>
-geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
-                          double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n) {
-  if (count <= 0 || nrhs <= 0) return GENEO_OK;
-  // One right-hand side (the preconditioner's local solves): two stages and
-  // one register slot per warp keep the block small enough for several
-  // blocks per SM, which hides the latency of the sequential sweep.
+geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count, int max_w,
+                                double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
+                                const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
   if (nrhs == 1) {
-    // whole vector resident in shared memory when it fits; the deepest
-    // pipeline (at most four stages) that keeps two blocks per SM for FP32
-    // batches (one for FP64 or a small batch) hides the latency of the
-    // factor stream
-    if (max_n > 0) {
-      const size_t budget = (sizeof(T) == 4 && count > 152) ? 112 * 1024 : 226 * 1024;
-      int stages = 4;
-      while (stages > 2 && res_smem<T>(max_w, max_n, 16, stages) > budget) --stages;
-      const size_t smem = res_smem<T>(max_w, max_n, 16, stages);
-      if (smem <= 227 * 1024) {
-        auto kern = stages == 4 ? k_band_solve_res<T, 4>
-                  : stages == 3 ? k_band_solve_res<T, 3> : k_band_solve_res<T, 2>;
-        GENEO_CUDA(allow_smem(kern));
-        kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, nrhs_dev, skip_dev, st); note_launch();
-        GENEO_CUDA(cudaGetLastError());
-        return GENEO_OK;
-      }
-    }
     int snb = 16;
     if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16, 2) > kSmemCap) snb = 4;
     const int ring = next_pow2(max_w + 2 * snb);
@@ -1704,24 +1763,6 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
-  }
-  // FP32 factors: tensor-core kernel, up to 32 columns per launch
-  if constexpr (sizeof(T) == 4) {
-    const int ring = next_pow2(max_w + 32);
-    if (mtc_smem(max_w, ring, 1, 2) <= 227 * 1024) {
-      for (int c0 = 0; c0 < nrhs; c0 += 32) {
-        const int kc = std::min(32, nrhs - c0);
-        int NT = (kc + 7) / 8;
-        while (NT > 1 && mtc_smem(max_w, ring, NT, 2) > 227 * 1024) --NT;
-        const int kk = std::min(kc, 8 * NT);
-        int stages = 4;
-        while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > 227 * 1024) --stages;
-        GENEO_TRY(launch_mtc(NT, stages, count, mtc_smem(max_w, ring, NT, stages), s, base, d_desc, xbase,
-                             xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
-        if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch
-      }
-      return GENEO_OK;
-    }
   }
   // register-tiled kernel: up to 32 (FP32) or 16 (FP64) columns per launch
   {
@@ -1760,10 +1801,72 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
   return GENEO_OK;
 }
 
+template <typename T>
+geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
+                          double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n) {
+  if (count <= 0 || nrhs <= 0) return GENEO_OK;
+  // One right-hand side (the preconditioner's local solves): two stages and
+  // one register slot per warp keep the block small enough for several
+  // blocks per SM, which hides the latency of the sequential sweep.
+  if (nrhs == 1) {
+    // whole vector resident in shared memory when it fits; the deepest
+    // pipeline (at most four stages) that keeps two blocks per SM for FP32
+    // batches (one for FP64 or a small batch) hides the latency of the
+    // factor stream
+    if (max_n > 0) {
+      const size_t budget = (sizeof(T) == 4 && count > 152) ? 112 * 1024 : 226 * 1024;
+      int stages = 4;
+      while (stages > 2 && res_smem<T>(max_w, max_n, 16, stages) > budget) --stages;
+      const size_t smem = res_smem<T>(max_w, max_n, 16, stages);
+      if (smem <= 227 * 1024) {
+        auto kern = stages == 4 ? k_band_solve_res<T, 4>
+                  : stages == 3 ? k_band_solve_res<T, 3> : k_band_solve_res<T, 2>;
+        GENEO_CUDA(allow_smem(kern));
+        kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, nrhs_dev, skip_dev, st); note_launch();
+        GENEO_CUDA(cudaGetLastError());
+        return GENEO_OK;
+      }
+    }
+  }
+  // FP32 factors: tensor-core kernel, up to 32 columns per launch
+  if constexpr (sizeof(T) == 4) {
+    const int ring = next_pow2(max_w + 32);
+    if (mtc_smem(max_w, ring, 1, 2) <= 227 * 1024) {
+      for (int c0 = 0; c0 < nrhs; c0 += 32) {
+        const int kc = std::min(32, nrhs - c0);
+        int NT = (kc + 7) / 8;
+        while (NT > 1 && mtc_smem(max_w, ring, NT, 2) > 227 * 1024) --NT;
+        const int kk = std::min(kc, 8 * NT);
+        int stages = 4;
+        while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > 227 * 1024) --stages;
+        GENEO_TRY(launch_mtc(NT, stages, count, mtc_smem(max_w, ring, NT, stages), s, base, d_desc, xbase,
+                             xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
+        if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch
+      }
+      return GENEO_OK;
+    }
+  }
+  // other kernels: the vectors are scaled around the solve where the bands
+  // are equilibrated (FP32 factors)
+  if constexpr (sizeof(T) == 4) {
+    const int gx = std::max(1, std::min(64, (max_n > 0 ? max_n : 4096) * nrhs / 256));
+    k_band_scale_x<T><<<dim3(gx, count), 256, 0, s>>>(base, d_desc, xbase, xoff, 0, nrhs, nrhs_dev, skip_dev);
+    note_launch();
+    GENEO_TRY(band_solve_plain<T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s));
+    k_band_scale_x<T><<<dim3(gx, count), 256, 0, s>>>(base, d_desc, xbase, xoff, 0, nrhs, nrhs_dev, skip_dev);
+    note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  } else {
+    return band_solve_plain<T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s);
+  }
+}
+
 template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, int, DevStatus*,
-                                           cudaStream_t);
+                                           cudaStream_t, bool, int32_t*, float);
 template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, int, DevStatus*,
-                                          cudaStream_t);
+                                          cudaStream_t, bool, int32_t*, float);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
                                            DevStatus*, cudaStream_t, int);

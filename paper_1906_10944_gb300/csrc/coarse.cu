@@ -256,7 +256,7 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   *ms_matrix = ms_since(t1);
 
   auto t2 = std::chrono::steady_clock::now();
-  BandDesc bh{0, h->dimH, wH, -2, band_ld(wH), (int64_t)h->dimH * band_ld(wH)};
+  BandDesc bh{0, h->dimH, wH, -2, band_ld(wH), (int64_t)h->dimH * band_ld(wH), -1};
   GENEO_TRY(h->mem.get(&h->dbandH, 1));
   GENEO_CUDA(cudaMemcpyAsync(h->dbandH, &bh, sizeof(BandDesc), cudaMemcpyHostToDevice, s));
   const int pf = h->prof.begin(GENEO_PROF_FACTOR, band_factor_flops(h->dimH, wH),

@@ -149,14 +149,20 @@ struct SubDesc {
 struct BandDesc {
   int64_t off;     // element offset of the band (a multiple of 4)
   int32_t n, w;
-  int32_t id;      // reported in errors
+  int32_t id;      // reported in errors; the solves index vectors, counts and
+                   // skip flags by id when it is >= 0 (subdomain index), by
+                   // the position in the batch otherwise
   int32_t ld;      // row stride
   int64_t dinv;    // element offset of the inverted diagonal blocks
+  int64_t scl;     // element offset of the row scaling s = diag^{-1/2} of an
+                   // equilibrated band (the factor is that of S A S), or -1
 };
 
 __host__ __device__ __forceinline__ int band_ld(int w) { return (w + 4) & ~3; }
 // elements of the inverted diagonal blocks of an order-n band
 __host__ __device__ __forceinline__ int64_t dinv_elems(int n) { return (int64_t)((n + 15) / 16) * 256; }
+// elements of the row scaling of an order-n band (a multiple of 4)
+__host__ __device__ __forceinline__ int64_t scl_elems(int n) { return (int64_t)((n + 3) & ~3); }
 
 // --------------------------------------------------------------------------
 // Device helpers.
@@ -276,13 +282,21 @@ geneo_status_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, in
                                   DevMem& tmp, cudaStream_t st);
 
 // band.cu
+// Batched Cholesky.  equil: factor S A S (s = diag^{-1/2}) and keep s.
+// weak (may be NULL): instead of reporting GENEO_ERR_NOT_SPD, matrix d sets
+// weak[d.id] = 1 when one of its pivots is not above weak_tol (relative to
+// the unit diagonal of an equilibrated band); the caller factors those
+// matrices again in FP64.
 template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
-                          DevStatus* st, cudaStream_t s);
+                          DevStatus* st, cudaStream_t s, bool equil = false,
+                          int32_t* weak = nullptr, float weak_tol = 0.f);
 // Solve L L^T X = X in place for `nrhs` columns per matrix (column-major,
-// leading dimension = matrix n, column stride = n); X for matrix i starts
-// at xbase + xoff[i]; nrhs_dev (may be NULL) gives per-matrix column counts
-// capped by nrhs; skip_dev (may be NULL) skips matrices with a non-zero flag.
+// leading dimension = matrix n, column stride = n); X for matrix i (i = the
+// descriptor's id when >= 0, else its batch position) starts at
+// xbase + xoff[i]; nrhs_dev (may be NULL) gives per-matrix column counts
+// capped by nrhs; skip_dev (may be NULL) skips matrices with a non-zero flag;
+// a descriptor with n = 0 is skipped.
 // max_n (largest matrix order, 0 if unknown) enables the one-right-hand-side
 // solve with the vector resident in shared memory.
 template <typename T>

@@ -41,6 +41,13 @@ struct geneo_handle_s {
   geneo::BandDesc* dbandA = nullptr;
   int maxwA = 0;
   int maxnD = 0;                   // largest Dirichlet dof count
+  // FP32 mode: A_j whose FP32 factorisation had a weak pivot, factored in
+  // FP64 (their FP32 descriptors get n = 0)
+  double* bandA64 = nullptr;
+  geneo::BandDesc* dbandA64 = nullptr;
+  int nA64 = 0, maxwA64 = 0, maxnA64 = 0;
+  std::vector<uint8_t> a64;        // [N] 1: A_j factored in FP64
+  int nK64 = 0;                    // the same count for K_j (setup only)
 
   // coarse space
   int dimH = 0, wH = 0;
@@ -94,12 +101,21 @@ struct AssemblyOut {
   void* bandK = nullptr;
   BandDesc* dbandK = nullptr;
   int maxwK = 0;
+  std::vector<BandDesc> hbandK, hbandA;  // host copies of the solve descriptors
+  int32_t* weak = nullptr;  // [2N] FP32 factorisations with a weak pivot (K_j, A_j)
+  // K_j factored again in FP64
+  double* bandK64 = nullptr;
+  BandDesc* dbandK64 = nullptr;
+  int nK64 = 0, maxwK64 = 0, maxnK64 = 0;
 };
 geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& a,
                                DevMem& tmp, cudaStream_t s);
 geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& out,
                               DevMem& tmp, cudaStream_t s, double* ms_assembly,
                               double* ms_factor);
+// FP32 mode, after the A_j factorisation has finished: factor in FP64 the A_j
+// flagged weak (adaptive precision per subdomain).
+geneo_status_t refactor_weak_A(geneo_handle_s* h, AssemblyOut& a, DevMem& tmp, cudaStream_t s);
 
 // lobpcg.cu
 geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& a, DevMem& tmp, cudaStream_t s,

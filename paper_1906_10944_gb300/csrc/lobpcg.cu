@@ -982,6 +982,24 @@ __global__ void k_set_i32(int32_t* __restrict__ dst, const int32_t* __restrict__
   if (j < n && !(skip && skip[j])) dst[j] = src[j];
 }
 
+// Skip flags of the two orthogonalisation flavours with FP32 factors:
+// skip32 = done or o64 (FP32 first pass), skip64 = done or not o64 (FP64
+// first pass for the subdomains whose K_j needed FP64).
+__global__ void k_split_skip(const int32_t* __restrict__ done, const int32_t* __restrict__ o64,
+                             int32_t* __restrict__ skip32, int32_t* __restrict__ skip64, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    skip32[j] = done[j] || o64[j];
+    skip64[j] = done[j] || !o64[j];
+  }
+}
+
+// f[j] = f[j] and not o64[j] (FP32-arithmetic flags of k_gemm32)
+__global__ void k_and_not(int32_t* __restrict__ f, const int32_t* __restrict__ o64, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && o64[j]) f[j] = 0;
+}
+
 inline double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -1054,6 +1072,23 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(allow_smem(k_gemm32<double, double>));
 
   const bool f32 = h->fp32;
+  // Subdomains whose K_j was factored in FP64 (a weak FP32 pivot: coefficient
+  // contrast beyond FP32) also orthogonalise in FP64: their K-norms span
+  // that contrast, which FP32 Gram matrices and corrections do not resolve.
+  // o64 / ok32: per-subdomain flags; n64 of them set.
+  int n64 = 0;
+  int32_t *o64 = nullptr, *ok32 = nullptr, *skip32 = nullptr, *skip64 = nullptr;
+  if (f32) {
+    std::vector<int32_t> ho(N, 0), hk(N, 1);
+    for (int j = 0; j < N; ++j)
+      if ((int)asmb.hbandK.size() == N && asmb.hbandK[j].n == 0) { ho[j] = 1; hk[j] = 0; ++n64; }
+    GENEO_TRY(tmp.get(&o64, (size_t)N));
+    GENEO_TRY(tmp.get(&ok32, (size_t)N));
+    GENEO_TRY(tmp.get(&skip32, (size_t)N));
+    GENEO_TRY(tmp.get(&skip64, (size_t)N));
+    GENEO_CUDA(cudaMemcpyAsync(o64, ho.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    GENEO_CUDA(cudaMemcpyAsync(ok32, hk.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+  }
   // FP32 copies for the first orthogonalisation pass: [X, Q] and [KX, KQ]
   // (same layout as S and KS) and the values of K
   float *S32 = nullptr, *KS32 = nullptr, *lK32 = nullptr;
@@ -1078,9 +1113,14 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   h->eig_flops = 0.0;
   auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip,
                         int kmax) -> geneo_status_t {
-    if (f32)
-      return band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
-                               ncols, skip, h->dstat, st, maxn);
+    if (f32) {
+      GENEO_TRY(band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
+                                  ncols, skip, h->dstat, st, maxn));
+      if (asmb.nK64)  // the K_j factored in FP64 (their FP32 descriptors have n = 0)
+        GENEO_TRY(band_solve<double>(asmb.bandK64, asmb.dbandK64, asmb.nK64, asmb.maxwK64, S, xoff, kmax,
+                                     ncols, skip, h->dstat, st, asmb.maxnK64));
+      return GENEO_OK;
+    }
     return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
                               kmax, ncols, skip, h->dstat, st, maxn);
   };
@@ -1098,7 +1138,8 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     for (int j = 0; j < N; ++j)
       if (!hk[j] && hc[j] > 0) {
         fl += kflops[j] * hc[j];
-        by += 2.0 * esz * band_entries(h->hsub[j].nN, h->hsub[j].wK) + 16.0 * h->hsub[j].nN * hc[j];
+        const bool k64 = f32 && (int)asmb.hbandK.size() == N && asmb.hbandK[j].n == 0;  // factored in FP64
+        by += 2.0 * (k64 ? 8.0 : esz) * band_entries(h->hsub[j].nN, h->hsub[j].wK) + 16.0 * h->hsub[j].nN * hc[j];
       }
     h->eig_flops += fl;
     const int pr = h->prof.begin(GENEO_PROF_EIG_SOLVE, fl, by, st);
@@ -1309,36 +1350,53 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // With FP32 factors the first pass runs on FP32 copies of X, Q and KX
       // (it removes the bulk of the X components); the second, FP64 pass sets
       // the final K-orthonormality that Rayleigh-Ritz relies on.
+      // with FP32 factors, the FP32 flavour skips s32 and the FP64 one s64
+      const int32_t* s32 = done;
+      const int32_t* s64 = nullptr;
+      if (f32 && n64 > 0) {
+        k_split_skip<<<ceil_div(N, 128), 128, 0, st>>>(done, o64, skip32, skip64, N); note_launch();
+        s32 = skip32;
+        s64 = skip64;
+      }
+      const bool any32 = f32 && n64 < N;
       for (int pass = 0; pass < 2; ++pass) {
         if (f32 && pass == 0) {
-          cvt(Sr, Sr32, done);
-          cvt(KXr, KXr32, done);
-          GENEO_TRY(gram(KXr32, Qr32, 0, done));
-          GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr32, -1.0, 1.0, done, 0));
-          spmm(true, false, Qr32, KQr32, KQr32, done);
-          GENEO_TRY(gram(Qr32, KQr32, 1, done));
-          {
-            const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
-            k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax); note_launch();
-            h->prof.end(prs, st);
+          if (any32) {
+            cvt(Sr, Sr32, s32);
+            cvt(KXr, KXr32, s32);
+            GENEO_TRY(gram(KXr32, Qr32, 0, s32));
+            GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr32, -1.0, 1.0, s32, 0));
+            spmm(true, false, Qr32, KQr32, KQr32, s32);
+            GENEO_TRY(gram(Qr32, KQr32, 1, s32));
+            {
+              const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
+              k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, s32, wmax); note_launch();
+              h->prof.end(prs, st);
+            }
+            // Q = Q32 T straight into the FP64 block (no aliasing: T acts on the copy)
+            GENEO_TRY(gemm32(Qr32, Tm, 0, nullptr, cref(S, W3, 0, sj, 0, rj), 1.0, 0.0, s32, 1));
+            k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, s32); note_launch();
+            GENEO_CUDA(cudaGetLastError());
           }
-          // Q = Q32 T straight into the FP64 block (no aliasing: T acts on the copy)
-          GENEO_TRY(gemm32(Qr32, Tm, 0, nullptr, cref(S, W3, 0, sj, 0, rj), 1.0, 0.0, done, 1));
-          k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
-          GENEO_CUDA(cudaGetLastError());
-          continue;
+          if (!s64) continue;
         }
-        GENEO_TRY(gram(KXr, Qr, 0, done));
+        // FP64 pass (the first pass of the o64 subdomains when pass == 0)
+        const int32_t* sp = (f32 && pass == 0) ? s64 : done;
+        GENEO_TRY(gram(KXr, Qr, 0, sp));
         // after an FP32 first pass X G is a small correction: FP32 product,
         // subtracted in FP64
-        if (f32) GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr, -1.0, 1.0, done, 1));
-        else GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, done));
-        spmm(true, false, Qr, KQr, KQr, done);
-        GENEO_TRY(gram(Qr, KQr, 1, done));
+        if (f32 && pass == 1) {
+          if (any32) GENEO_TRY(gemm32(Xr32, G, 0, nullptr, Qr, -1.0, 1.0, s32, 1));
+          if (s64) GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, s64));
+        } else {
+          GENEO_TRY(gemm(Xr, G, 0, nullptr, Qr, -1.0, 1.0, sp));
+        }
+        spmm(true, false, Qr, KQr, KQr, sp);
+        GENEO_TRY(gram(Qr, KQr, 1, sp));
         {
           const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
           if (pass == 0) {
-            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, done, wmax);
+            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, sp, wmax);
             note_launch();
           } else {
             // the block is nearly K-orthonormal: Cholesky QR, SVQB where a
@@ -1347,18 +1405,19 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
             k_cholqr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, rj, 1e-12, done, wmax); note_launch();
             k_mark_fallback<<<ceil_div(N, 128), 128, 0, st>>>(rj, done, redo, N); note_launch();
             k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, redo, wmax); note_launch();
+            if (f32 && n64 > 0) { k_and_not<<<ceil_div(N, 128), 128, 0, st>>>(redo, o64, N); note_launch(); }
           }
           h->prof.end(prs, st);
         }
         // second pass with FP32 factors: T = D L^{-T} is near I where
         // Cholesky QR succeeded (redo[j] == 1): Q T = Q + Q (T - I) with an
-        // FP32 product; the SVQB fallback subdomains stay FP64
+        // FP32 product; the SVQB fallback and o64 subdomains stay FP64
         if (pass == 1 && f32)
           GENEO_TRY(gemm32(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done, 1, 1, redo));
         else
-          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, done));
-        k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, done); note_launch();
-        k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, done); note_launch();
+          GENEO_TRY(gemm(Qr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, sp));
+        k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(qj, rj, N, sp); note_launch();
+        k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, qj), Qr, sp); note_launch();
         GENEO_CUDA(cudaGetLastError());
       }
       // Rayleigh-Ritz on S = [X, Q]; BX from the residual step is current,
@@ -1368,7 +1427,8 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wmax); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       // P only spans the next search block: FP32 arithmetic with FP32 factors
-      if (f32) GENEO_TRY(gemm32(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, 0));
+      if (f32) GENEO_TRY(gemm32(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, 0, 0,
+                                n64 > 0 ? ok32 : nullptr));
       else GENEO_TRY(gemm(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done));
       k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(spj, sj, N, done); note_launch();
       GENEO_TRY(gemm(Sr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, done));

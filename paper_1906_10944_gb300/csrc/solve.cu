@@ -231,11 +231,13 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
   h->red_blocks = kRedBlocks;
   // algorithmic work of one apply
-  const double esz = h->fp32 ? 4.0 : 8.0;
+  // bytes per factor entry: 4 with FP32 factors, 8 for those factored in FP64
+  auto esz_of = [&](int j) { return h->fp32 && !(j < (int)h->a64.size() && h->a64[j]) ? 4.0 : 8.0; };
   double fl = 0.0, by = 0.0, sumD = 0.0;
-  for (const SubDesc& d : h->hsub) {
+  for (int j = 0; j < h->N; ++j) {
+    const SubDesc& d = h->hsub[j];
     fl += band_solve_flops(d.nD, d.wA) + 4.0 * (double)d.nD * d.m;
-    by += 2.0 * esz * band_entries(d.nD, d.wA) + 2.0 * 8.0 * (double)d.nD * d.m;
+    by += 2.0 * esz_of(j) * band_entries(d.nD, d.wA) + 2.0 * 8.0 * (double)d.nD * d.m;
     sumD += d.nD;
   }
   fl += band_solve_flops(h->dimH, h->wH);
@@ -244,9 +246,10 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   h->apply_flops = fl;
   h->apply_bytes = by;
   double lfl = 0.0, lby = 0.0;
-  for (const SubDesc& d : h->hsub) {
+  for (int j = 0; j < h->N; ++j) {
+    const SubDesc& d = h->hsub[j];
     lfl += band_solve_flops(d.nD, d.wA);
-    lby += 2.0 * esz * band_entries(d.nD, d.wA) + 8.0 * 2.0 * d.nD;  // factor twice; u in and out once
+    lby += 2.0 * esz_of(j) * band_entries(d.nD, d.wA) + 8.0 * 2.0 * d.nD;  // factor twice; u in and out once
   }
   h->local_solve_flops = lfl;
   h->local_solve_bytes = lby;
@@ -271,10 +274,13 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
     GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   }
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
-  if (h->fp32)
+  if (h->fp32) {
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
                                 nullptr, nullptr, h->dstat, s, h->maxnD));
-  else
+    if (h->nA64)  // the A_j factored in FP64 (their FP32 descriptors have n = 0)
+      GENEO_TRY(band_solve<double>(h->bandA64, h->dbandA64, h->nA64, h->maxwA64, h->u, h->uoff, 1,
+                                   nullptr, nullptr, h->dstat, s, h->maxnA64));
+  } else
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
                                  nullptr, nullptr, h->dstat, s, h->maxnD));
   h->prof.end(pl, s);

@@ -212,3 +212,37 @@ def test_uneven_batch_darcy_3d():
     batch mixes subdomain sizes and band widths; FP64 parity as above."""
     prob = gen.uneven_darcy_problem((24, 20, 18), 24, 3, 8, seed=3)
     _full_check(prob, nev=8)
+
+
+@pytest.mark.parametrize("pivot_tol", [1e-4, 0.999])
+def test_mixed_precision_fp64_refactor(pivot_tol):
+    """Adaptive precision per subdomain: an FP32 factorisation with a pivot
+    at or below fp32_pivot_tol (equilibrated bands, unit diagonal) is redone
+    in FP64 and solved by the FP64 kernels into the same vectors.  With
+    0.999 every K_j and A_j goes to FP64 (every factorisation has a pivot
+    below its unit diagonal), which exercises the FP64 batch end to end; the
+    default keeps FP32 where FP32 suffices.  Uneven k-d boxes with inclusions
+    of contrast up to 1e8; parity as in the mixed-precision test."""
+    prob = gen.uneven_darcy_problem((24, 20, 18), 24, 3, 8, seed=3)
+    nev = 8
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=nev))
+    sol, _ = run_gpu(prob, nev_max=nev, precision=1, fp32_pivot_tol=pivot_tol)
+    try:
+        q = sol.query()
+        if pivot_tol > 0.5:
+            assert q["fp64_factors_K"] == prob.n_sub and q["fp64_factors_A"] == prob.n_sub, q
+        else:
+            assert 0 <= q["fp64_factors_K"] <= prob.n_sub and 0 <= q["fp64_factors_A"] <= prob.n_sub
+        for j in range(prob.n_sub):
+            g = sol.subdomain(j)
+            m = min(g["m"], orc.ms[j])
+            lo = orc.lams[j][:m]
+            assert np.all(np.abs(g["lambda"][:m] - lo) <= 1e-6 * np.maximum(np.abs(lo), 3e-4)), j
+        x, info = gpu_solve(sol, prob)
+        _, ito, _, _ = orc.solve(tol=1e-8)
+        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
+        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
+            (info["rel_residual"], res, info["iterations"])
+        assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
+    finally:
+        sol.close()
