@@ -211,6 +211,10 @@ typedef struct {
   int32_t block_size;        /* eigensolver block width s */
   int32_t fp64_factors_K;    /* GENEO_PREC_FP32: K_j factored in FP64 */
   int32_t fp64_factors_A;    /* GENEO_PREC_FP32: A_j factored in FP64 */
+  int32_t fp64_ortho;        /* GENEO_PREC_FP32: subdomains whose eigensolver
+                                blocks were orthogonalised in FP64 (K_j in
+                                FP64, or a residual that stopped halving in
+                                the FP32 first passes) */
   int64_t device_bytes;      /* device memory held by the handle */
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse

@@ -271,6 +271,7 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->block_size = h->s_block;
   info->fp64_factors_K = h->nK64;
   info->fp64_factors_A = h->nA64;
+  info->fp64_ortho = h->eig_o64;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->factor_flops = h->factor_flops;

@@ -60,6 +60,7 @@ struct geneo_handle_s {
   int s_block = 0;
   int eig_iters = 0;
   int eig_second_pass = 0;         // subdomains solved again with the full block
+  int eig_o64 = 0;                 // FP32 mode: subdomains orthogonalised in FP64
 
   // apply / PCG work
   double* u = nullptr;             // [sumD] local solutions

@@ -39,6 +39,8 @@ constexpr int kRS = 4;          // row splits of the Gram kernel
 constexpr int kRB = 32;         // rows per shared-memory chunk in the Gram kernel
 constexpr int kMaxSweeps = 40;  // bound of the Jacobi sweep loop
 constexpr int kFirstPassNev = 8; // wanted pairs of the narrow first pass
+constexpr int kStallIts = 6;     // FP32 first passes: iterations without halving the residual
+constexpr int kStallFrom = 12;   // ... counted from this iteration of a pass on
 
 // A multivector operand: columns [c0 + c0d[j], + width) of a buffer holding W
 // columns per subdomain (rows = nN_j, column-major, ld = nN_j), storage S
@@ -878,7 +880,8 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
         const int32_t* __restrict__ spj, int32_t* __restrict__ aj, int32_t* __restrict__ qj,
         int32_t* __restrict__ done, int32_t* __restrict__ iters, int32_t* __restrict__ notdone,
         double* __restrict__ rn_out, double tol, double tau, double sigma, const int32_t* __restrict__ nevj, int fixed,
-        int it) {
+        int it, double* __restrict__ best, int32_t* __restrict__ stall, int32_t* __restrict__ o64,
+        int32_t* __restrict__ ok32, int stall_lim) {
   const int j = blockIdx.x;
   if (done[j]) return;
   const SubDesc d = sub[j];
@@ -932,6 +935,26 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
       done[j] = 1;
     } else {
       atomicAdd(notdone, 1);
+    }
+    // FP32 first passes: a subdomain whose largest wanted residual has not
+    // halved in stall_lim iterations (counted after iteration kStallFrom of
+    // the pass) switches to FP64 orthogonalisation (notdone[1] counts the
+    // switches)
+    if (best && !fin && !o64[j]) {
+      double r = 0.0;
+      for (int i = 0; i < min(nev, s); ++i) {
+        r = fmax(r, rn[i]);
+        const double lam = nu[i] > 0.0 ? sigma + 1.0 / nu[i] : INFINITY;
+        if (!fixed && lam >= tau) break;
+      }
+      if (it <= kStallFrom || r < 0.5 * best[j]) {
+        best[j] = r;
+        stall[j] = 0;
+      } else if (++stall[j] >= stall_lim) {
+        o64[j] = 1;
+        ok32[j] = 0;
+        atomicAdd(notdone + 1, 1);
+      }
     }
     iters[j] = it;
     aj[j] = fin ? 0 : k;
@@ -1037,7 +1060,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_TRY(tmp.get(&spj, (size_t)N));
   GENEO_TRY(tmp.get(&done, (size_t)N));
   GENEO_TRY(tmp.get(&iters, (size_t)N));
-  GENEO_TRY(tmp.get(&notdone, 1));
+  GENEO_TRY(tmp.get(&notdone, 2));
   GENEO_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * rows * W3, st));
   GENEO_CUDA(cudaMemsetAsync(P, 0, sizeof(double) * rows * s, st));
   GENEO_CUDA(cudaMemsetAsync(nu, 0, sizeof(double) * N * s, st));
@@ -1078,7 +1101,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   // o64 / ok32: per-subdomain flags; n64 of them set.
   int n64 = 0;
   int32_t *o64 = nullptr, *ok32 = nullptr, *skip32 = nullptr, *skip64 = nullptr;
+  double* best = nullptr;        // per subdomain: smallest wanted residual so far
+  int32_t* stall = nullptr;      // iterations since it last halved
   if (f32) {
+    GENEO_TRY(tmp.get(&best, (size_t)N));
+    GENEO_TRY(tmp.get(&stall, (size_t)N));
     std::vector<int32_t> ho(N, 0), hk(N, 1);
     for (int j = 0; j < N; ++j)
       if ((int)asmb.hbandK.size() == N && asmb.hbandK[j].n == 0) { ho[j] = 1; hk[j] = 0; ++n64; }
@@ -1327,13 +1354,16 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     int remaining = N;
     for (int it = 0; it < o.eig_maxit; ++it, ++total_it) {
       spmm(true, true, Xr, KXr, BXr, done);
-      GENEO_CUDA(cudaMemsetAsync(notdone, 0, sizeof(int32_t), st));
+      GENEO_CUDA(cudaMemsetAsync(notdone, 0, 2 * sizeof(int32_t), st));
       k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
                                 spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nevj,
-                                o.fixed_nev, it); note_launch();
+                                o.fixed_nev, it, f32 ? best : nullptr, stall, o64, ok32, kStallIts); note_launch();
       GENEO_CUDA(cudaGetLastError());
-      GENEO_CUDA(cudaMemcpyAsync(&remaining, notdone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      int32_t cnt[2] = {0, 0};
+      GENEO_CUDA(cudaMemcpyAsync(cnt, notdone, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       GENEO_CUDA(cudaStreamSynchronize(st));
+      remaining = cnt[0];
+      n64 += cnt[1];
       if (remaining == 0) break;
       // W = K^{-1} R (active columns start at column s_j)
       std::vector<int32_t> hsj(N);
@@ -1489,6 +1519,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   }
   const int it = total_it;
   h->eig_iters = it;
+  h->eig_o64 = n64;
   h->setup_ms[3] = ms_since(t0);
   // eigenvalues lambda = sigma + 1/nu (ascending in lambda = descending nu)
   std::vector<double> hnu((size_t)N * s);
