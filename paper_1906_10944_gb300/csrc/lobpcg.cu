@@ -132,6 +132,151 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-single SpMM for the FP32 mode.  GB300 issues FP64 at 1/64 of the
+// FP32 rate, so the FP64 products with K_j and B_j are the eigensolver's
+// largest cost.  Here every value is a pair of floats (hi + lo, hi = the
+// value rounded to FP32), and each product is formed with Dekker's exact
+// product by fused multiply-add plus the two cross terms and accumulated with
+// Knuth's two-sum (Dekker 1971; Knuth, TAOCP vol. 2): about 46 significant
+// bits relative to sum |a x|, against the 53 of FP64 and far below the
+// eigensolver's residual tolerance.  The explicit _rn intrinsics keep the
+// compiler from fusing the additions of the two-sum.
+// ---------------------------------------------------------------------------
+struct DS {
+  float h, l;
+};
+
+// acc += a * x for double-single a, x, acc
+__device__ __forceinline__ void ds_fma(DS& acc, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = __fmaf_rn(ah, xh, -p);          // p + e = ah xh exactly
+  e = __fmaf_rn(ah, xl, e);
+  e = __fmaf_rn(al, xh, e);
+  const float s = __fadd_rn(acc.h, p);      // two-sum of acc.h and p
+  const float bv = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
+// FP64 values rounded to FP32 (the first pass's copy of K)
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// FP64 column block -> (hi, lo) float pairs, hi = fl32(v), lo = fl32(v - hi):
+// X2 has X's layout (same W and columns)
+__global__ void k_split_cols(const SubDesc* __restrict__ sub, ColRef X, ColRefT<float2> X2,
+                             const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int w = cr_w(X, j);
+  const double* x = cr_ptr(X, d, j);
+  float2* x2 = cr_ptr(X2, d, j);
+  for (int c = 0; c < w; ++c) {
+    const double v = x[(int64_t)c * d.nN + a];
+    const float h = (float)v;
+    x2[(int64_t)c * d.nN + a] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// Longest row of the local CSR matrices (all subdomains).
+__global__ void k_max_rowlen(const int64_t* __restrict__ lrow, int64_t rows, int32_t* __restrict__ out) {
+  int m = 0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)(lrow[r + 1] - lrow[r]));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Local K and B in a padded column-major row layout (ELLPACK) for the
+// double-single SpMM: subdomain j's block starts at offN * L, entry t of row
+// a at t * nN + a, so a warp's loads of entry t of 32 consecutive rows are
+// contiguous.  Short rows are padded with column a and value 0.
+__global__ void k_build_ell(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
+                            const int32_t* __restrict__ lcol, const double* __restrict__ vK,
+                            const double* __restrict__ vB, int L, int32_t* __restrict__ ecol,
+                            float2* __restrict__ eK, float2* __restrict__ eB) {
+  const int j = blockIdx.y;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int64_t e0 = lrow[d.offN + a], e1 = lrow[d.offN + a + 1];
+  const int64_t base = d.offN * (int64_t)L + a;
+  for (int t = 0; t < L; ++t) {
+    const int64_t e = e0 + t;
+    const int64_t o = base + (int64_t)t * d.nN;
+    if (e < e1) {
+      ecol[o] = lcol[e];
+      const double k = vK[e], b = vB[e];
+      const float kh = (float)k, bh = (float)b;
+      eK[o] = make_float2(kh, (float)(k - (double)kh));
+      eB[o] = make_float2(bh, (float)(b - (double)bh));
+    } else {
+      ecol[o] = a;
+      eK[o] = make_float2(0.f, 0.f);
+      eB[o] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// Y1 = V1 X (and Y2 = V2 X when v2 is given) in double-single arithmetic from
+// the ELLPACK layout, results stored in FP64; one row per thread, four
+// columns per pass.  Each entry and operand value is one 8-byte (hi, lo) load.
+__global__ void __launch_bounds__(kT)
+k_spmm_ds(const SubDesc* __restrict__ sub, int L, const int32_t* __restrict__ ecol,
+          const float2* __restrict__ v1, const float2* __restrict__ v2, ColRefT<float2> X2, ColRef Y1,
+          ColRef Y2, const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d.nN) return;
+  const int w = cr_w(X2, j);
+  const float2* x2 = cr_ptr(X2, d, j);
+  double* y1 = cr_ptr(Y1, d, j);
+  double* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
+  const int64_t nn = d.nN;
+  const int64_t base = d.offN * (int64_t)L + a;
+  for (int c = 0; c < w; c += 4) {
+    const int nc = min(4, w - c);
+    DS s1[4], s2[4];
+#pragma unroll
+    for (int z = 0; z < 4; ++z) s1[z] = s2[z] = DS{0.f, 0.f};
+    const float2* xc = x2 + (int64_t)c * nn;
+    for (int t = 0; t < L; ++t) {
+      const int64_t o = base + (int64_t)t * nn;
+      const int col = ecol[o];
+      const float2 va = v1[o];
+      const float2 vb = v2 ? v2[o] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        if (z < nc) {
+          const float2 xv = xc[z * nn + col];
+          ds_fma(s1[z], va.x, va.y, xv.x, xv.y);
+          if (v2) ds_fma(s2[z], vb.x, vb.y, xv.x, xv.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      if (z < nc) {
+        y1[(c + z) * nn + a] = (double)s1[z].h + (double)s1[z].l;
+        if (v2) y2[(c + z) * nn + a] = (double)s2[z].h + (double)s2[z].l;
+      }
+    }
+  }
+}
+
 // Y = X columnwise copy (with conversion between storage types)
 template <typename SS, typename SD>
 __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRefT<SS> Src, ColRefT<SD> Dst,
@@ -983,10 +1128,6 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
   }
 }
 
-__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
-}
 
 __global__ void k_sub_nnz(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
                           int64_t* __restrict__ out, int n) {
@@ -1012,8 +1153,9 @@ __global__ void k_split_skip(const int32_t* __restrict__ done, const int32_t* __
                              int32_t* __restrict__ skip32, int32_t* __restrict__ skip64, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) {
-    skip32[j] = done[j] || o64[j];
-    skip64[j] = done[j] || !o64[j];
+    const int dj = done ? done[j] : 0;  // done may be NULL (nothing skipped)
+    skip32[j] = dj || o64[j];
+    skip64[j] = dj || !o64[j];
   }
 }
 
@@ -1118,12 +1260,37 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   }
   // FP32 copies for the first orthogonalisation pass: [X, Q] and [KX, KQ]
   // (same layout as S and KS) and the values of K
+  // With FP32 factors the FP64 products with K and B run in double-single
+  // arithmetic (k_spmm_ds): K and B as (hi, lo) float pairs in ELLPACK
+  // layout, the operand split into pairs in X2, which overlays S32 and KS32
+  // (dead at every such product) first.
+  // Subdomains orthogonalised in FP64 (o64) keep FP64 products: their
+  // contrast makes K x cancel beyond double-single accuracy.
   float *S32 = nullptr, *KS32 = nullptr, *lK32 = nullptr;
+  float2 *eK2 = nullptr, *eB2 = nullptr, *X2 = nullptr;
+  int32_t *ecol = nullptr, *dsk1 = nullptr, *dsk2 = nullptr;
+  int ell = 0;  // ELLPACK row length (longest local row)
   if (f32) {
-    GENEO_TRY(tmp.get(&S32, (size_t)rows * W3));
-    GENEO_TRY(tmp.get(&KS32, (size_t)rows * W3));
-    GENEO_TRY(tmp.get(&lK32, (size_t)std::max<int64_t>(asmb.lnnz, 1)));
-    k_to_f32<<<(unsigned)std::min<int64_t>((asmb.lnnz + kT - 1) / kT, 152 * 16), kT, 0, st>>>(asmb.lK, lK32, asmb.lnnz);
+    const size_t nz = (size_t)std::max<int64_t>(asmb.lnnz, 1);
+    // S32 and KS32 adjoin: X2 (rows x W3 pairs) overlays both
+    GENEO_TRY(tmp.get(&S32, (size_t)rows * W3 * 2));
+    KS32 = S32 + (size_t)rows * W3;
+    X2 = reinterpret_cast<float2*>(S32);
+    GENEO_TRY(tmp.get(&lK32, nz));
+    GENEO_TRY(tmp.get(&dsk1, (size_t)N));
+    GENEO_TRY(tmp.get(&dsk2, (size_t)N));
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((asmb.lnnz + kT - 1) / kT, 152 * 16));
+    k_to_f32<<<g, kT, 0, st>>>(asmb.lK, lK32, asmb.lnnz); note_launch();
+    int32_t* dl = dsk1;
+    GENEO_CUDA(cudaMemsetAsync(dl, 0, sizeof(int32_t), st));
+    k_max_rowlen<<<152 * 4, kT, 0, st>>>(asmb.lrow, rows, dl); note_launch();
+    GENEO_CUDA(cudaMemcpyAsync(&ell, dl, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    const size_t ne = (size_t)std::max<int64_t>(rows * (int64_t)ell, 1);
+    GENEO_TRY(tmp.get(&ecol, ne));
+    GENEO_TRY(tmp.get(&eK2, ne));
+    GENEO_TRY(tmp.get(&eB2, ne));
+    k_build_ell<<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, asmb.lK, asmb.lB, ell, ecol, eK2, eB2);
     note_launch();
     GENEO_CUDA(cudaGetLastError());
   }
@@ -1292,12 +1459,33 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       vK = asmb.lK;
       vB = asmb.lB;
     }
+    const int32_t* sk = skip;  // subdomains left for the plain kernel
+    if constexpr (sizeof(S) == 8) {
+      if (f32 && X.W == W3 && n64 < N) {
+        const int32_t* sds = skip;
+        if (n64 > 0) {
+          k_split_skip<<<ceil_div(N, 128), 128, 0, st>>>(skip, o64, dsk1, dsk2, N); note_launch();
+          sds = dsk1;
+          sk = dsk2;
+        }
+        const ColRefT<float2> Xs{X2, X.W, X.c0, X.c0d, X.w, X.wd, X.wd2};
+        k_split_cols<<<gridR, kT, 0, st>>>(h->dsub, X, Xs, sds); note_launch();
+        const bool both = withK && withB;
+        k_spmm_ds<<<gridR, kT, 0, st>>>(h->dsub, ell, ecol, withK ? eK2 : eB2, both ? eB2 : nullptr, Xs,
+                                        withK ? YK : YB, YB, sds);
+        note_launch();
+        if (n64 == 0) {
+          h->prof.end(pr, st);
+          return;
+        }
+      }
+    }
     if (withK && withB) {
-      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, vB, X, YK, YB, skip);
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, vB, X, YK, YB, sk);
     } else if (withK) {
-      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, nullptr, X, YK, YK, skip);
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vK, nullptr, X, YK, YK, sk);
     } else {
-      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vB, nullptr, X, YB, YB, skip);
+      k_spmm<S><<<gridR, kT, 0, st>>>(h->dsub, asmb.lrow, asmb.lcol, vB, nullptr, X, YB, YB, sk);
     }
     note_launch();
     h->prof.end(pr, st);
