@@ -166,8 +166,62 @@ __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out,
     out[i] = (float)in[i];
 }
 
-// FP64 column block -> (hi, lo) float pairs, hi = fl32(v), lo = fl32(v - hi):
-// X2 has X's layout (same W and columns)
+// FP64 -> (hi, lo) floats with integer operations only (the FP64 pipe,
+// which also executes conversions, is the scarce unit): hi keeps the sign,
+// the exponent and the top 23 mantissa bits (truncation), lo the next 23
+// of the remaining 29 bits, so hi + lo = x to 2^-46 relative.  Outside
+// 2^-80 <= |x| < 2^128 the plain conversion is used and lo = 0 (below 2^-126
+// both are 0).
+__device__ __forceinline__ float2 split_bits(double x) {
+  const uint32_t hi32 = (uint32_t)__double2hiint(x), lo32 = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 943 || e > 1150) return make_float2(e >= 897 ? (float)x : 0.f, 0.f);
+  const uint32_t mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | mh);
+  const uint32_t r = (lo32 & 0x1fffffffu) >> 6;                     // < 2^23
+  const float f = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.0f);  // r exactly
+  const float sc = __uint_as_float(sign | ((uint32_t)(e - 942) << 23));     // +-2^(e - 1069)
+  return make_float2(h, __fmul_rn(f, sc));
+}
+
+// Exact float -> double and round-to-nearest double -> float with integer
+// operations for normal numbers and zero (the same results as the
+// conversions, which run on the FP64 pipe); anything else converts.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e == 0 || e == 255) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+__device__ __forceinline__ float d2f_bits(double x) {
+  const uint32_t hi32 = (uint32_t)__double2hiint(x), lo32 = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 897 || e > 1150) {
+    if ((hi32 & 0x7fffffffu) == 0 && lo32 == 0) return __uint_as_float(sign);
+    return (float)x;
+  }
+  uint32_t b = sign | ((uint32_t)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const uint32_t rem = lo32 & 0x1fffffffu;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (b & 1u))) ++b;  // nearest, ties to even
+  return __uint_as_float(b);
+}
+template <typename D, typename S>
+__device__ __forceinline__ D cv(S v) {
+  if constexpr (std::is_same_v<D, S>) return v;
+  else if constexpr (std::is_same_v<D, float>) return d2f_bits(v);
+  else return f2d_bits(v);
+}
+
+// value of an accumulator (double-single pairs summed in FP64)
+__device__ __forceinline__ double acc_value(const DS& v) { return f2d_bits(v.h) + f2d_bits(v.l); }
+__device__ __forceinline__ double acc_value(double v) { return v; }
+__device__ __forceinline__ double acc_value(float v) { return f2d_bits(v); }
+
+// FP64 column block -> (hi, lo) float pairs (split_bits): X2 has X's layout
+// (same W and columns)
 __global__ void k_split_cols(const SubDesc* __restrict__ sub, ColRef X, ColRefT<float2> X2,
                              const int32_t* __restrict__ skip) {
   const int j = blockIdx.y;
@@ -178,11 +232,7 @@ __global__ void k_split_cols(const SubDesc* __restrict__ sub, ColRef X, ColRefT<
   const int w = cr_w(X, j);
   const double* x = cr_ptr(X, d, j);
   float2* x2 = cr_ptr(X2, d, j);
-  for (int c = 0; c < w; ++c) {
-    const double v = x[(int64_t)c * d.nN + a];
-    const float h = (float)v;
-    x2[(int64_t)c * d.nN + a] = make_float2(h, (float)(v - (double)h));
-  }
+  for (int c = 0; c < w; ++c) x2[(int64_t)c * d.nN + a] = split_bits(x[(int64_t)c * d.nN + a]);
 }
 
 // Longest row of the local CSR matrices (all subdomains).
@@ -270,8 +320,8 @@ k_spmm_ds(const SubDesc* __restrict__ sub, int L, const int32_t* __restrict__ ec
 #pragma unroll
     for (int z = 0; z < 4; ++z) {
       if (z < nc) {
-        y1[(c + z) * nn + a] = (double)s1[z].h + (double)s1[z].l;
-        if (v2) y2[(c + z) * nn + a] = (double)s2[z].h + (double)s2[z].l;
+        y1[(c + z) * nn + a] = acc_value(s1[z]);
+        if (v2) y2[(c + z) * nn + a] = acc_value(s2[z]);
       }
     }
   }
@@ -289,7 +339,7 @@ __global__ void k_copy_cols(const SubDesc* __restrict__ sub, ColRefT<SS> Src, Co
   const int w = cr_w(Src, j);
   const SS* s = cr_ptr(Src, d, j);
   SD* t = cr_ptr(Dst, d, j);
-  for (int c = 0; c < w; ++c) t[(int64_t)c * d.nN + a] = (SD)s[(int64_t)c * d.nN + a];
+  for (int c = 0; c < w; ++c) t[(int64_t)c * d.nN + a] = cv<SD>(s[(int64_t)c * d.nN + a]);
 }
 
 // Partial Gram matrices G = A^T B over a row split; ld of G is ldg.
@@ -426,11 +476,15 @@ k_gram_part(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym
 // barrier per chunk).  Subdomains with more tiles are left to k_gram_part
 // (mode 1); this kernel skips them, and k_gram_part in mode 1 skips the
 // others.  Same partial layout and summation order rules as k_gram_part.
-template <typename S>
+template <typename S, bool DSM = false>
 __global__ void __launch_bounds__(kT, 2)
 k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym, double* __restrict__ Gp,
            int ldg, int nsub, const int32_t* __restrict__ skip) {
   using C = S;
+  // DSM (S = double): the chunk is staged as (hi, lo) float pairs and the
+  // products accumulate in double-single arithmetic (ds_fma)
+  using E = std::conditional_t<DSM, float2, C>;   // staged element
+  using Acc = std::conditional_t<DSM, DS, C>;
   const int j = blockIdx.y, rs = blockIdx.x;
   if (skip && skip[j]) return;
   const SubDesc d = sub[j];
@@ -444,7 +498,7 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
   const S* b = cr_ptr(B, d, j);
   const int pp = 4 * tp, qp = 4 * tq;          // padded widths
   extern __shared__ __align__(16) unsigned char gsm_raw[];
-  C* buf = reinterpret_cast<C*>(gsm_raw);      // 2 x kRB x (pp + qp)
+  E* buf = reinterpret_cast<E*>(gsm_raw);      // 2 x kRB x (pp + qp)
   const int chunk = kRB * (pp + qp);
   const int groups = kT / ntiles;
   const int tx = (int)threadIdx.x;
@@ -463,9 +517,9 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
       tj = t / tp;
     }
   }
-  C acc[16];
+  Acc acc[16];
 #pragma unroll
-  for (int z = 0; z < 16; ++z) acc[z] = 0;
+  for (int z = 0; z < 16; ++z) acc[z] = Acc{};
   const int r0 = (int)((int64_t)rs * d.nN / kRS), r1 = (int)((int64_t)(rs + 1) * d.nN / kRS);
   // thread (lane, warp) handles row `lane` of a chunk and the combined
   // [A | B] columns warp + 8 u (kRB = 32 rows, 8 warps, up to 128 columns);
@@ -487,11 +541,17 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
       pre[u] = v;
     }
   };
-  auto stash = [&](C* dst) {
+  auto stash = [&](E* dst) {
 #pragma unroll
     for (int u = 0; u < kPre; ++u) {
       const int cc = wq + 8 * u;
-      if (cc < pp + qp) dst[lane * (pp + qp) + cc] = pre[u];
+      if (cc < pp + qp) {
+        if constexpr (DSM) {
+          dst[lane * (pp + qp) + cc] = split_bits(pre[u]);
+        } else {
+          dst[lane * (pp + qp) + cc] = pre[u];
+        }
+      }
     }
   };
   int cur = 0;
@@ -503,12 +563,12 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
   for (int rb = r0; rb < r1; rb += kRB) {
     const bool more = rb + kRB < r1;
     if (more) fetch(rb + kRB);
-    const C* X = buf + (size_t)cur * chunk;
+    const E* X = buf + (size_t)cur * chunk;
     if (t >= 0) {
       const int nr = min(kRB, r1 - rb);
       for (int r = g; r < nr; r += groups) {
-        const C* row = X + r * (pp + qp);
-        C av[4], bv[4];
+        const E* row = X + r * (pp + qp);
+        E av[4], bv[4];
 #pragma unroll
         for (int z = 0; z < 4; ++z) {
           av[z] = row[4 * ti + z];
@@ -517,7 +577,10 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
 #pragma unroll
         for (int z = 0; z < 4; ++z)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[z * 4 + y] += av[z] * bv[y];
+          for (int y = 0; y < 4; ++y) {
+            if constexpr (DSM) ds_fma(acc[z * 4 + y], av[z].x, av[z].y, bv[y].x, bv[y].y);
+            else acc[z * 4 + y] += av[z] * bv[y];
+          }
       }
     }
     if (more) stash(buf + (size_t)(cur ^ 1) * chunk);
@@ -529,7 +592,7 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
     double* red = reinterpret_cast<double*>(gsm_raw);  // groups * ntiles * 16 <= kT * 16
     if (t >= 0)
 #pragma unroll
-      for (int z = 0; z < 16; ++z) red[((size_t)g * ntiles + t) * 16 + z] = acc[z];
+      for (int z = 0; z < 16; ++z) red[((size_t)g * ntiles + t) * 16 + z] = acc_value(acc[z]);
     __syncthreads();
     for (int o = threadIdx.x; o < ntiles * 16; o += kT) {
       const int tt = o / 16, z = o % 16;
@@ -557,7 +620,7 @@ k_gram_one(const SubDesc* __restrict__ sub, ColRefT<S> A, ColRefT<S> B, int sym,
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const int r = 4 * ti + z, c = 4 * tj + y;
-        if (r < p && c < q) G[(int64_t)c * ldg + r] = acc[z * 4 + y];
+        if (r < p && c < q) G[(int64_t)c * ldg + r] = acc_value(acc[z * 4 + y]);
       }
 }
 
@@ -668,10 +731,10 @@ k_gemm32(const SubDesc* __restrict__ sub, ColRefT<SA> A, const double* __restric
   if (wide) {
     for (int c = 0; c < q; ++c) {
       double acc = 0.0;
-      for (int i = 0; i < p; ++i) acc += (double)a[(int64_t)i * d.nN + a_row] * Td[i * q + c];
+      for (int i = 0; i < p; ++i) acc += cv<double>(a[(int64_t)i * d.nN + a_row]) * Td[i * q + c];
       SO* o = cm + (int64_t)c * d.nN + a_row;
-      const double v = acc + (addI ? (double)a[(int64_t)c * d.nN + a_row] : 0.0);
-      *o = (SO)((beta == 0.0 ? 0.0 : beta * (double)*o) + alpha * v);
+      const double v = acc + (addI ? cv<double>(a[(int64_t)c * d.nN + a_row]) : 0.0);
+      *o = cv<SO>((beta == 0.0 ? 0.0 : beta * cv<double>(*o)) + alpha * v);
     }
     return;
   }
@@ -681,7 +744,7 @@ k_gemm32(const SubDesc* __restrict__ sub, ColRefT<SA> A, const double* __restric
 #pragma unroll
     for (int z = 0; z < 32; ++z) acc[z] = 0.f;
     for (int i = 0; i < p; ++i) {
-      const float av = (float)a[(int64_t)i * d.nN + a_row];
+      const float av = cv<float>(a[(int64_t)i * d.nN + a_row]);
       const float* tr = Ts + i * qp + c0;
 #pragma unroll
       for (int z4 = 0; z4 < 8; ++z4) {
@@ -700,8 +763,8 @@ k_gemm32(const SubDesc* __restrict__ sub, ColRefT<SA> A, const double* __restric
         const int c = c0 + z;
         SO* o = cm + (int64_t)c * d.nN + a_row;
         if (corr || sizeof(SO) == 8) {
-          const double v = (double)acc[z] + (addI ? (double)a[(int64_t)c * d.nN + a_row] : 0.0);
-          *o = (SO)((beta == 0.0 ? 0.0 : beta * (double)*o) + alpha * v);
+          const double v = f2d_bits(acc[z]) + (addI ? cv<double>(a[(int64_t)c * d.nN + a_row]) : 0.0);
+          *o = cv<SO>((beta == 0.0 ? 0.0 : beta * cv<double>(*o)) + alpha * v);
         } else {
           *o = (SO)((beta == 0.0 ? 0.f : (float)beta * (float)*o) + (float)alpha * acc[z]);
         }
@@ -1229,6 +1292,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   // there, since wider subdomains go to k_gram_part), or the group partials
   const size_t gram1_smem = sizeof(double) * std::max((size_t)2 * kRB * 128, (size_t)16 * kT);
   GENEO_CUDA(allow_smem(k_gram_one<double>));
+  GENEO_CUDA(allow_smem(k_gram_one<double, true>));
   GENEO_CUDA(allow_smem(k_gram_one<float>));
   GENEO_CUDA(allow_smem(k_gram_part<float>));
   GENEO_CUDA(allow_smem(k_gemm_nn));
@@ -1385,7 +1449,29 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       }
     }
     const int pr = h->prof.begin(sizeof(S) == 4 ? GENEO_PROF_ORTHO32 : GENEO_PROF_GRAM, fl, by, st);
-    k_gram_one<S><<<dim3(kRS, N), kT, gram1_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    // FP32 mode: double-single products (FP64 where the subdomain is o64)
+    bool one_done = false;
+    if constexpr (sizeof(S) == 8) {
+      if (f32 && n64 < N) {
+        const int32_t* sds = skip;
+        const int32_t* s64 = nullptr;
+        if (n64 > 0) {
+          k_split_skip<<<ceil_div(N, 128), 128, 0, st>>>(skip, o64, dsk1, dsk2, N); note_launch();
+          sds = dsk1;
+          s64 = dsk2;
+        }
+        k_gram_one<double, true><<<dim3(kRS, N), kT, gram1_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, sds);
+        note_launch();
+        if (s64) {
+          k_gram_one<double, false><<<dim3(kRS, N), kT, gram1_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, s64);
+          note_launch();
+        }
+        one_done = true;
+      }
+    }
+    if (!one_done) {
+      k_gram_one<S><<<dim3(kRS, N), kT, gram1_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip); note_launch();
+    }
     if (W3 > 64) {
       k_gram_part<S><<<dim3(kRS, N), kT, gram_smem, st>>>(h->dsub, A, B, sym, Gp, ldg, N, skip, 1);
       note_launch();
