@@ -688,6 +688,55 @@ k_gemm_nn(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ 
   }
 }
 
+// The same product in double-single arithmetic (FP32 mode): T staged as
+// (hi, lo) pairs, each A value split once per sixteen output columns, FP64
+// epilogue.
+__global__ void __launch_bounds__(kT)
+k_gemm_ds(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ Tm, int ldg,
+          int t0, const int32_t* __restrict__ t0d, ColRef Cout, double alpha, double beta,
+          const int32_t* __restrict__ skip) {
+  const int j = blockIdx.y;
+  if (skip && skip[j]) return;
+  const SubDesc d = sub[j];
+  const int p = cr_w(A, j), q = cr_w(Cout, j);
+  if (q <= 0) return;
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  float2* Ts = reinterpret_cast<float2*>(ts_raw);  // p x q, Ts[i*q + c]
+  const double* T = Tm + (int64_t)j * ldg * ldg + t0 + (t0d ? t0d[j] : 0);
+  for (int idx = threadIdx.x; idx < p * q; idx += blockDim.x) {
+    const int i = idx % p, c = idx / p;
+    Ts[i * q + c] = split_bits(T[(int64_t)c * ldg + i]);
+  }
+  __syncthreads();
+  const int a_row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a_row >= d.nN) return;
+  const double* a = cr_ptr(A, d, j);
+  double* cm = cr_ptr(Cout, d, j);
+  constexpr int CB = 16;
+  for (int c0 = 0; c0 < q; c0 += CB) {
+    DS acc[CB];
+#pragma unroll
+    for (int z = 0; z < CB; ++z) acc[z] = DS{0.f, 0.f};
+    for (int i = 0; i < p; ++i) {
+      const float2 av = split_bits(a[(int64_t)i * d.nN + a_row]);
+#pragma unroll
+      for (int z = 0; z < CB; ++z)
+        if (c0 + z < q) {
+          const float2 tv = Ts[i * q + c0 + z];
+          ds_fma(acc[z], av.x, av.y, tv.x, tv.y);
+        }
+    }
+#pragma unroll
+    for (int z = 0; z < CB; ++z) {
+      const int c = c0 + z;
+      if (c < q) {
+        double* o = cm + (int64_t)c * d.nN + a_row;
+        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc_value(acc[z]);
+      }
+    }
+  }
+}
+
 // FP32-arithmetic GEMM.  A has storage SA, C storage SO; each A value is
 // read (and converted) once per 32 output columns; T rows are read as
 // four-wide vectors.  Epilogue:
@@ -1296,6 +1345,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(allow_smem(k_gram_one<float>));
   GENEO_CUDA(allow_smem(k_gram_part<float>));
   GENEO_CUDA(allow_smem(k_gemm_nn));
+  GENEO_CUDA(allow_smem(k_gemm_ds));
   GENEO_CUDA(allow_smem(k_gemm32<float, float>));
   GENEO_CUDA(allow_smem(k_gemm32<float, double>));
   GENEO_CUDA(allow_smem(k_gemm32<double, double>));
@@ -1502,7 +1552,21 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     double fl, by;
     GENEO_TRY(gemm_cost(A, C, beta, skip, 8.0, fl, by));
     const int pr = h->prof.begin(GENEO_PROF_GEMM, fl, by, st);
-    k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, skip); note_launch();
+    const int32_t* sk = skip;  // subdomains left for the FP64 kernel
+    bool all_ds = false;
+    if (f32 && n64 < N) {  // double-single arithmetic except for the o64 subdomains
+      const int32_t* sds = skip;
+      if (n64 > 0) {
+        k_split_skip<<<ceil_div(N, 128), 128, 0, st>>>(skip, o64, dsk1, dsk2, N); note_launch();
+        sds = dsk1;
+        sk = dsk2;
+      }
+      k_gemm_ds<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, sds); note_launch();
+      all_ds = n64 == 0;
+    }
+    if (!all_ds) {
+      k_gemm_nn<<<gridR, kT, nn_smem, st>>>(h->dsub, A, Tmat, ldg, t0, t0d, C, alpha, beta, sk); note_launch();
+    }
     h->prof.end(pr, st);
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
