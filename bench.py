@@ -235,10 +235,24 @@ FAMILY_BOUND = {
 }
 
 
+# with FP32 factors the eigensolver's FP64 block products (SpMM, Gram, GEMM)
+# run in double-single arithmetic on the FP32 pipe
+DS_FAMILIES = ("spmm", "gram", "gemm")
+
+
+def ds_peak():
+    """Double-single multiply-add peak in FP64-equivalent flops: one
+    double-single multiply-add is 12 FP32-pipe instructions (1 FMUL, 3 FFMA,
+    8 FADD), 128 FP32 lanes per clock per SM, 152 SMs, 2070 MHz, 2 flop."""
+    return 152 * 128 / 12 * 2 * 2070e6
+
+
 def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
     bound = FAMILY_BOUND.get(name, "alu-fp64")
     if bound == "tensor" and precision != "mixed":
         bound = "alu-fp64"
+    if precision == "mixed" and name in DS_FAMILIES:
+        bound = "alu-ds"
     ms = rec["ms"] if ms is None else ms
     if bound == "hbm":
         ach = rec["bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
@@ -246,12 +260,33 @@ def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
                 "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src,
                 "algorithmic_bytes_per_launch": rec["bytes"] / max(rec["launches"], 1)}
     ach = rec["flops"] / (ms / 1e3) if ms > 0 else 0.0
+    if bound == "tensor" and rec["bytes"] > 0:
+        # roofline: the attainable rate is min(tensor peak, intensity x HBM);
+        # the band solves and the factorisation stream their factors, so at
+        # their arithmetic intensity HBM is usually the lower roof
+        peak_t, _ = tf32_peak()
+        intensity = rec["flops"] / rec["bytes"]
+        if intensity * hbm_peak * 1e9 < peak_t / 3.0:  # three TF32 passes per product
+            bound = "hbm"
+    if bound == "hbm":
+        ach_b = rec["bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"bound": "hbm", "kernel": name, "achieved": ach_b, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach_b / hbm_peak, "traffic": None, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": rec["bytes"] / max(rec["launches"], 1),
+                "flop_per_byte": rec["flops"] / rec["bytes"] if rec["bytes"] > 0 else None}
     if bound == "tensor":
         peak, src = tf32_peak()
         return {"bound": "tensor", "kernel": name, "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src,
                 "note": "achieved counts the algorithmic FP32 flops; each product runs as three "
                         "TF32 MMA passes on the warp-level MMA path",
+                "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
+    if bound == "alu-ds":
+        peak = ds_peak()
+        return {"bound": "alu", "kernel": name, "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: double-single multiply-add = 12 FP32 instructions; "
+                               "152 SMs x 128 lanes / 12 x 2 flop x 2070 MHz",
                 "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
     peak = fp64_peak()
     return {"bound": "alu", "kernel": name, "achieved": ach / 1e12, "peak": peak / 1e12,
