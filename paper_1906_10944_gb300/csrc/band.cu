@@ -651,44 +651,46 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
       }
       __syncthreads();
     }
-    // ---- factor the panel block: diagonal block by the whole block, one
-    // barrier per column.  Phase t: thread 0 records pivot t (final now; a
-    // pivot that is not positive is reported and replaced by 1), the
-    // trailing update of column t uses the unscaled column t and 1 / pivot,
-    // and column t - 1 is scaled with the pivot recorded in the previous
-    // phase (no thread reads it any more).
-    {
-      float* Pv = Red;  // kPB recorded pivots (the partial-sum buffer is idle here)
-      for (int t = 0; t <= b; ++t) {
-        if (t >= 1) {
-          const float pt = Pv[t - 1];
-          const float inv = rsqrtf(pt);
-          for (int r = t + tid; r < b; r += kThreads) Us[r * kUS + (t - 1)] *= inv;
-          if (tid == 0) {
-            Us[(t - 1) * kUS + (t - 1)] = pt * inv;   // sqrt(pivot)
-            Dinv[t - 1] = inv;
-          }
-        }
-        if (t < b) {
-          float p = Us[t * kUS + t];
+    // ---- factor the panel's diagonal block in warp 0: lane r holds row r in
+    // registers; step t takes pivot t from lane t (a pivot that is not
+    // positive is reported and replaced by 1), scales column t and updates
+    // the trailing part with shuffled column-t values (no block barriers).
+    if (wid == 0) {
+      float a[kPB];
+#pragma unroll
+      for (int u = 0; u < kPB; ++u) a[u] = (lane < b && u <= lane) ? Us[lane * kUS + u] : 0.f;
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        if (t < b) {  // uniform over the warp
+          float p = __shfl_sync(0xffffffffu, a[t], t);
           if (weak) {
-            if (tid == 0 && !(p > weak_tol)) weak[d.id] = 1;
+            if (lane == 0 && !(p > weak_tol)) weak[d.id] = 1;
             if (!finite_pos(p)) p = 1.f;
           } else if (!finite_pos(p)) {
-            if (tid == 0) record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
+            if (lane == 0) record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
             p = 1.f;
           }
-          if (tid == 0) Pv[t] = p;
-          const float ip = 1.f / p;
-          const int m = b - t - 1;
-          for (int idx = tid; idx < m * m; idx += kThreads) {
-            const int r = t + 1 + idx % m, u = t + 1 + idx / m;
-            if (u <= r) Us[r * kUS + u] -= Us[r * kUS + t] * Us[u * kUS + t] * ip;
+          const float inv = rsqrtf(p);
+          if (lane == t) {
+            a[t] = p * inv;  // sqrt(pivot)
+            Dinv[t] = inv;
+          } else if (lane > t) {
+            a[t] *= inv;
+          }
+#pragma unroll
+          for (int u = t + 1; u < kPB; ++u) {
+            const float lut = __shfl_sync(0xffffffffu, a[t], u);
+            if (lane >= u) a[u] -= a[t] * lut;
           }
         }
-        __syncthreads();
       }
-      if (tid >= b && tid < kPB) Dinv[tid] = 0.f;
+      if (lane < b) {
+#pragma unroll
+        for (int u = 0; u < kPB; ++u)
+          if (u <= lane) Us[lane * kUS + u] = a[u];
+      } else {
+        Dinv[lane] = 0.f;
+      }
     }
     __syncthreads();
     // rows below: x L_jj^T = u, one row per thread (stride kUS: no bank conflicts)

@@ -41,6 +41,7 @@ constexpr int kMaxSweeps = 40;  // bound of the Jacobi sweep loop
 constexpr int kFirstPassNev = 8; // wanted pairs of the narrow first pass
 constexpr int kStallIts = 6;     // FP32 first passes: iterations without halving the residual
 constexpr int kStallFrom = 12;   // ... counted from this iteration of a pass on
+constexpr int kForce64From = 30; // FP32 mode: subdomains still iterating here switch to FP64
 
 // A multivector operand: columns [c0 + c0d[j], + width) of a buffer holding W
 // columns per subdomain (rows = nN_j, column-major, ld = nN_j), storage S
@@ -1211,7 +1212,8 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
     }
     // FP32 first passes: a subdomain whose largest wanted residual has not
     // halved in stall_lim iterations (counted after iteration kStallFrom of
-    // the pass) switches to FP64 orthogonalisation (notdone[1] counts the
+    // the pass), or that is still iterating at iteration kForce64From,
+    // switches to FP64 products and orthogonalisation (notdone[1] counts the
     // switches)
     if (best && !fin && !o64[j]) {
       double r = 0.0;
@@ -1220,7 +1222,11 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
         const double lam = nu[i] > 0.0 ? sigma + 1.0 / nu[i] : INFINITY;
         if (!fixed && lam >= tau) break;
       }
-      if (it <= kStallFrom || r < 0.5 * best[j]) {
+      if (it >= kForce64From) {  // a straggler: FP64 from here on
+        o64[j] = 1;
+        ok32[j] = 0;
+        atomicAdd(notdone + 1, 1);
+      } else if (it <= kStallFrom || r < 0.5 * best[j]) {
         best[j] = r;
         stall[j] = 0;
       } else if (++stall[j] >= stall_lim) {
