@@ -1139,7 +1139,7 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
         int32_t* __restrict__ done, int32_t* __restrict__ iters, int32_t* __restrict__ notdone,
         double* __restrict__ rn_out, double tol, double tau, double sigma, const int32_t* __restrict__ nevj, int fixed,
         int it, double* __restrict__ best, int32_t* __restrict__ stall, int32_t* __restrict__ o64,
-        int32_t* __restrict__ ok32, int stall_lim, int lowp) {
+        int32_t* __restrict__ ok32, int stall_lim) {
   const int j = blockIdx.x;
   if (done[j]) return;
   const SubDesc d = sub[j];
@@ -1157,28 +1157,12 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
     const double* bc = bx + (int64_t)c * d.nN;
     const double* kc = kx + (int64_t)c * d.nN;
     const double nc = nu[c];
-    if (lowp) {
-      // FP32 mode: the residual vector in FP64, the three norms (a
-      // convergence test, 1e-5 relative is plenty) in FP32
-      float r2f = 0.f, b2f = 0.f, k2f = 0.f;
-      for (int a = lane; a < d.nN; a += 32) {
-        const double bv = bc[a], kv = kc[a];
-        const float rf = d2f_bits(bv - nc * kv), bf = d2f_bits(bv), kf = d2f_bits(kv);
-        r2f = fmaf(rf, rf, r2f);
-        b2f = fmaf(bf, bf, b2f);
-        k2f = fmaf(kf, kf, k2f);
-      }
-      r2 = f2d_bits(r2f);
-      b2 = f2d_bits(b2f);
-      k2 = f2d_bits(k2f);
-    } else {
-      for (int a = lane; a < d.nN; a += 32) {
-        const double bv = bc[a], kv = kc[a];
-        const double rv = bv - nc * kv;
-        r2 += rv * rv;
-        b2 += bv * bv;
-        k2 += kv * kv;
-      }
+    for (int a = lane; a < d.nN; a += 32) {
+      const double bv = bc[a], kv = kc[a];
+      const double rv = bv - nc * kv;
+      r2 += rv * rv;
+      b2 += bv * bv;
+      k2 += kv * kv;
     }
     r2 = warp_sum(r2);
     b2 = warp_sum(b2);
@@ -1222,14 +1206,16 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
         const double lam = nu[i] > 0.0 ? sigma + 1.0 / nu[i] : INFINITY;
         if (!fixed && lam >= tau) break;
       }
+      bool sw = false;
       if (it >= kForce64From) {  // a straggler: FP64 from here on
-        o64[j] = 1;
-        ok32[j] = 0;
-        atomicAdd(notdone + 1, 1);
+        sw = true;
       } else if (it <= kStallFrom || r < 0.5 * best[j]) {
         best[j] = r;
         stall[j] = 0;
       } else if (++stall[j] >= stall_lim) {
+        sw = true;
+      }
+      if (sw) {
         o64[j] = 1;
         ok32[j] = 0;
         atomicAdd(notdone + 1, 1);
@@ -1717,7 +1703,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       GENEO_CUDA(cudaMemsetAsync(notdone, 0, 2 * sizeof(int32_t), st));
       k_resid<<<N, kT, 0, st>>>(h->dsub, cref(S, W3, 0, nullptr, 0, nullptr), BXr, KXr, Pr, nu, s, sj,
                                 spj, aj, qj, done, iters, notdone, rn, o.eig_tol, o.tau, o.sigma, nevj,
-                                o.fixed_nev, it, f32 ? best : nullptr, stall, o64, ok32, kStallIts, f32 ? 1 : 0); note_launch();
+                                o.fixed_nev, it, f32 ? best : nullptr, stall, o64, ok32, kStallIts); note_launch();
       GENEO_CUDA(cudaGetLastError());
       int32_t cnt[2] = {0, 0};
       GENEO_CUDA(cudaMemcpyAsync(cnt, notdone, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
