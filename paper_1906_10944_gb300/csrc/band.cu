@@ -501,7 +501,7 @@ constexpr int kUS = kPB + 1;  // row stride of the panel block in shared memory
 // Shared memory of the tensor-core factorisation for half-bandwidth w.
 inline size_t potrf_tc_smem(int w) {
   const size_t ld = (size_t)band_ld(w);
-  return 128 + sizeof(float) * ((kPB + 2 * kMC) * ld + (size_t)(w + kPB) * kUS + kPB + 8 * 16 * 32);
+  return 128 + sizeof(float) * ((kPB + 2 * kMC) * ld + (size_t)(w + kPB) * kUS + kPB + 2 * 8 * 16 * 32);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -517,7 +517,7 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
   float* Rs = Cs + (size_t)kPB * ld;                                       // 2 x kMC x ld
   float* Us = Rs + (size_t)2 * kMC * ld;                                   // (w + kPB) x kUS panel block
   float* Dinv = Us + (size_t)(w + kPB) * kUS;                              // kPB reciprocal pivots
-  float* Red = Dinv + kPB;                                                 // 8 warps x 16 x 32 partials
+  float* Red = Dinv + kPB;                                                 // 2 x 8 warps x 16 x 32 partials
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int g = lane >> 2, tg = lane & 3;
   if (tid == 0) {
@@ -557,12 +557,38 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
       load_rows(1, Rs, j, min(kMC, R));
     }
     wait_bar(0, j);
+    // One block barrier per chunk: the partial tiles of chunk ch go to
+    // Red[ch & 1] and are summed in the next iteration (or after the loop),
+    // with the A values each thread needs captured in registers before the
+    // chunk's rows are overwritten; the next chunk's copy is issued after the
+    // barrier, when no warp still reads the buffer it refills.
+    const int nt2 = wid & 3, qh = wid >> 2;   // this thread's two reduce outputs
+    float pa[2] = {0.f, 0.f};                 // A values of the pending chunk
+    int prow = -1;                            // first row of the pending chunk (-1: none)
+    auto reduce_pending = [&]() {
+      if (prow < 0) return;
+      const float* Rp = Red + (size_t)(((prow - j) / kMC) & 1) * (8 * 16 * 32);
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int q = 2 * qh + h2;
+        float sum = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) sum += Rp[((size_t)kk * 16 + nt2 * 4 + q) * 32 + lane];
+        const int r = prow + g + ((q & 2) ? 8 : 0);  // c0,c1: row g; c2,c3: row g+8
+        const int cl = 8 * nt2 + 2 * tg + (q & 1), c = j + cl;
+        if (r < j + R) {
+          float u = 0.f;
+          if (cl < b && c <= r && r - c <= w) u = pa[h2] - sum;
+          Us[(size_t)(r - j) * kUS + cl] = u;
+        }
+      }
+    };
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
       const int r0 = j + ch * kMC;
+      wait_bar(1 + buf, (int64_t)j * 1024 + ch);
       if (tid == 0 && ok && ch + 1 < nch)
         load_rows(1 + (buf ^ 1), Rs + (size_t)(buf ^ 1) * kMC * ld, r0 + kMC, min(kMC, R - (ch + 1) * kMC));
-      wait_bar(1 + buf, (int64_t)j * 1024 + ch);
       const float* Rb = Rs + (size_t)buf * kMC * ld;
       // warp kq: rows r0 .. r0 + 15, all 32 panel columns, over the kq-th
       // eighth of the k-steps of the tile's range
@@ -625,32 +651,28 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
         }
       }
       // partial sums of this eighth (small terms first), lane-contiguous
+      float* Rw = Red + (size_t)buf * (8 * 16 * 32);
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          Red[((size_t)kq * 16 + nt * 4 + q) * 32 + lane] = (acc[nt][0][q] + acc[nt][1][q]) + acc[nt][2][q];
-      __syncthreads();
+          Rw[((size_t)kq * 16 + nt * 4 + q) * 32 + lane] = (acc[nt][0][q] + acc[nt][1][q]) + acc[nt][2][q];
       // warp w: n-tile w & 3, outputs q of half w >> 2; U = A - sum into the
-      // panel block (zero outside the lower band)
-      {
-        const int nt2 = wid & 3, qh = wid >> 2;
+      // panel block (zero outside the lower band), for the previous chunk
+      reduce_pending();
+      // capture this chunk's A values for its reduction in the next iteration
 #pragma unroll
-        for (int q = 2 * qh; q < 2 * qh + 2; ++q) {
-          float sum = 0.f;
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) sum += Red[((size_t)kk * 16 + nt2 * 4 + q) * 32 + lane];
-          const int r = r0 + g + ((q & 2) ? 8 : 0);  // c0,c1: row g; c2,c3: row g+8
-          const int cl = 8 * nt2 + 2 * tg + (q & 1), c = j + cl;
-          if (r < j + R) {
-            float u = 0.f;
-            if (cl < b && c <= r && r - c <= w) u = Rb[(size_t)(r - r0) * ld + (c - r + w)] - sum;
-            Us[(size_t)(r - j) * kUS + cl] = u;
-          }
-        }
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int q = 2 * qh + h2;
+        const int r = r0 + g + ((q & 2) ? 8 : 0);
+        const int cl = 8 * nt2 + 2 * tg + (q & 1), c = j + cl;
+        pa[h2] = (r < j + R && cl < b && c <= r && r - c <= w) ? Rb[(size_t)(r - r0) * ld + (c - r + w)] : 0.f;
       }
-      __syncthreads();
+      prow = r0;
     }
+    __syncthreads();
+    reduce_pending();
+    __syncthreads();
     // ---- factor the panel's diagonal block in warp 0: lane r holds row r in
     // registers; step t takes pivot t from lane t (a pivot that is not
     // positive is reported and replaced by 1), scales column t and updates
