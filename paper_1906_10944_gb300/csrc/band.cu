@@ -463,13 +463,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 //   U(r, c) = A(r, c) - sum_k L(r, k) L(c, k),
 // an (R x w) x (w x 32) product whose operands are whole band rows: the
 // panel's own rows (staged once per panel) and the rows r (streamed in
-// chunks of 32 by bulk copies, two buffers).  Each warp owns one 16 x 8 tile
-// of a chunk's 32 x 32 block and accumulates it with m16n8k8 TF32 MMAs in
-// three passes (hi*hi + hi*lo + lo*hi with x = hi + lo, hi = tf32(x)), which
-// keeps about FP32 accuracy.  Then the panel is factored as in the
-// right-looking kernel: the 32 x 32 diagonal block by one warp, the rows
-// below by substitution, one row per thread.  Only the panel columns are
-// written; the trailing window is never rewritten.
+// chunks of 16 by bulk copies, two buffers).  For each chunk's 16 x 32 tile
+// every warp takes an eighth of the k range and accumulates it with m16n8k8
+// TF32 MMAs in three passes (hi*hi + hi*lo + lo*hi with x = hi + lo,
+// hi = tf32(x)), which keeps about FP32 accuracy; the eight partial tiles go
+// to one of two shared buffers and are summed in a fixed order while the next
+// chunk multiplies (one block barrier per chunk).  Then the 32 x 32 diagonal
+// block is factored by one warp in registers and the rows below by
+// substitution, one row per thread.  Only the panel columns are written; the
+// trailing window is never rewritten.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
   uint32_t r;
