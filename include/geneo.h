@@ -147,8 +147,9 @@ typedef struct {
  *             meets a pivot <= this value (the bands are equilibrated to a
  *             unit diagonal) is factored and solved in FP64 instead
  *             (adaptive precision per subdomain; default 1e-4, in [0, 1)).
- *             Those subdomains also orthogonalise their eigensolver blocks
- *             in FP64.
+ *             Those subdomains also run the eigensolver's block products
+ *             and orthogonalisation in FP64 (the others in double-single
+ *             arithmetic and, for the first pass, FP32).
  */
 typedef struct {
   double tau;
@@ -212,9 +213,10 @@ typedef struct {
   int32_t fp64_factors_K;    /* GENEO_PREC_FP32: K_j factored in FP64 */
   int32_t fp64_factors_A;    /* GENEO_PREC_FP32: A_j factored in FP64 */
   int32_t fp64_ortho;        /* GENEO_PREC_FP32: subdomains whose eigensolver
-                                blocks were orthogonalised in FP64 (K_j in
-                                FP64, or a residual that stopped halving in
-                                the FP32 first passes) */
+                                products and orthogonalisation ran in FP64
+                                (K_j factored in FP64, a residual that stopped
+                                halving, or still iterating at iteration 30);
+                                the others use double-single products */
   int64_t device_bytes;      /* device memory held by the handle */
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse
