@@ -81,21 +81,48 @@ def library_solve_fn(problems, rhs, tol=1e-8, maxit=2000):
     return solve
 
 
+def footprint_by_dofs(problems, bytes_per_dof: float, bytes_per_rhs_dof: float = 16.0):
+    """Device-memory estimate of a library request: problems[k] = (problem,
+    options, n); a handle holds about bytes_per_dof per dof (measured on the
+    128^3 Darcy workload with FP32 factors: 2.8 KB per dof, setup
+    temporaries included), and each right-hand side adds its solution and
+    right-hand-side vectors."""
+    def fp(req: Request) -> float:
+        n = problems[req.payload][2]
+        return bytes_per_dof * n + bytes_per_rhs_dof * n * req.nrhs
+    return fp
+
+
 class Server:
     """`workers` threads, each with its own stream (`make_stream()`), serving
-    requests first come, first served."""
+    requests first come, first served.
 
-    def __init__(self, solve_fn: Callable, workers: int = 3, make_stream: Optional[Callable] = None):
+    Admission control (optional): with `hbm_budget` bytes and `footprint(req)`
+    an estimate of a request's device memory, a request is admitted, in
+    arrival order, only when its footprint fits next to the footprints of the
+    admitted requests that have not finished; the head of the queue waits for
+    memory (no overtaking), and a request larger than the whole budget is
+    admitted alone.  `peak_bytes` records the largest admitted total."""
+
+    def __init__(self, solve_fn: Callable, workers: int = 3, make_stream: Optional[Callable] = None,
+                 hbm_budget: Optional[float] = None, footprint: Optional[Callable] = None):
         self.solve_fn = solve_fn
         self.workers = workers
         self.make_stream = make_stream
+        self.hbm_budget = hbm_budget
+        self.footprint = footprint
+        self.peak_bytes = 0.0
 
     def run(self, requests: List[Request]) -> List[Request]:
-        """Release each request at its arrival offset and return them all
-        with start, finish and result filled in."""
+        """Release each request at its arrival offset (and, with a budget,
+        once it fits) and return them all with start, finish and result
+        filled in."""
         q: "queue.Queue[Optional[Request]]" = queue.Queue()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
+        cond = threading.Condition()
+        state = {"bytes": 0.0, "inflight": 0}
+        fp = (lambda r: float(self.footprint(r))) if self.footprint else (lambda r: 0.0)
 
         def worker():
             stream = self.make_stream() if self.make_stream else None
@@ -109,6 +136,11 @@ class Server:
                 except Exception as e:  # recorded, the service continues
                     req.error = repr(e)
                 req.finish = now()
+                if self.hbm_budget is not None:
+                    with cond:
+                        state["bytes"] -= fp(req)
+                        state["inflight"] -= 1
+                        cond.notify_all()
 
         threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.workers)]
         for th in threads:
@@ -117,6 +149,14 @@ class Server:
             delay = req.arrival - now()
             if delay > 0:
                 time.sleep(delay)
+            if self.hbm_budget is not None:
+                need = fp(req)
+                with cond:
+                    while state["inflight"] > 0 and state["bytes"] + need > self.hbm_budget:
+                        cond.wait()
+                    state["bytes"] += need
+                    state["inflight"] += 1
+                    self.peak_bytes = max(self.peak_bytes, state["bytes"])
             q.put(req)
         for _ in threads:
             q.put(None)

@@ -51,3 +51,54 @@ def test_server_records_errors_and_continues():
     S.Server(solve, workers=1).run(reqs)
     assert reqs[1].error and reqs[0].result == 0 and reqs[2].result == 2
     assert S.summarize(reqs)["errors"] == 1
+
+
+def test_admission_keeps_footprint_under_budget_and_order():
+    # six requests arrive together; footprints 4, 4, 4, 2, 2, 2 under a budget
+    # of 8 with three workers: at most two of the large ones run together
+    fps = [4.0, 4.0, 4.0, 2.0, 2.0, 2.0]
+    live = {"bytes": 0.0, "peak": 0.0}
+    import threading
+    lock = threading.Lock()
+
+    def solve(req, stream):
+        with lock:
+            live["bytes"] += fps[req.rid]
+            live["peak"] = max(live["peak"], live["bytes"])
+        time.sleep(0.04)
+        with lock:
+            live["bytes"] -= fps[req.rid]
+        return req.rid
+
+    reqs = [S.Request(i, None, arrival=0.0) for i in range(6)]
+    srv = S.Server(solve, workers=3, hbm_budget=8.0, footprint=lambda r: fps[r.rid])
+    srv.run(reqs)
+    assert [r.result for r in reqs] == list(range(6))
+    assert live["peak"] <= 8.0 and srv.peak_bytes <= 8.0
+    # first come, first served: starts are in arrival (id) order
+    starts = [r.start for r in reqs]
+    assert starts == sorted(starts)
+    # request 2 had to wait for one of the first two to finish
+    assert reqs[2].start >= min(reqs[0].finish, reqs[1].finish) - 1e-3
+
+
+def test_admission_lets_an_oversized_request_run_alone():
+    def solve(req, stream):
+        time.sleep(0.02)
+        return req.rid
+
+    reqs = [S.Request(i, None, arrival=0.0) for i in range(3)]
+    fps = [1.0, 100.0, 1.0]
+    srv = S.Server(solve, workers=2, hbm_budget=10.0, footprint=lambda r: fps[r.rid])
+    srv.run(reqs)
+    assert [r.result for r in reqs] == [0, 1, 2]
+    # the oversized request starts after request 0 finished, and request 2 after it
+    assert reqs[1].start >= reqs[0].finish - 1e-3
+    assert reqs[2].start >= reqs[1].finish - 1e-3
+
+
+def test_footprint_by_dofs():
+    problems = [(None, None, 1000), (None, None, 8000)]
+    fp = S.footprint_by_dofs(problems, 2800.0)
+    assert fp(S.Request(0, 1, nrhs=2)) == 2800.0 * 8000 + 16.0 * 8000 * 2
+    assert fp(S.Request(1, 0, nrhs=1)) == 2800.0 * 1000 + 16.0 * 1000
