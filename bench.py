@@ -38,11 +38,11 @@ METRIC = "time-to-solution & DOF/s at rel-res 1e-8, mixed vs FP64; serve p50/p99
 UNIT = "DOF/s"
 
 WORKLOADS = {
-    "darcy3d_128": dict(nel=(128, 128, 128), parts=(8, 8, 8), overlap=2, nev=20, tau=0.3,
+    "darcy3d_128": dict(nel=(128, 128, 128), parts=(8, 8, 8), overlap=2, nev=20, tau=0.3, pcg_iters=60,
                         desc="3D Darcy Q1 128^3 elements (2,146,689 dofs), 8x8x8 subdomains of "
                              "16^3 elements, overlap 2, kappa=exp(GRF l=0.1 s2=4) x 1e6 slabs, "
                              "nev<=20, tau=0.3, PCG rel-res 1e-8"),
-    "darcy3d_64": dict(nel=(64, 64, 64), parts=(4, 4, 4), overlap=2, nev=20, tau=0.3,
+    "darcy3d_64": dict(nel=(64, 64, 64), parts=(4, 4, 4), overlap=2, nev=20, tau=0.3, pcg_iters=54,
                        desc="3D Darcy Q1 64^3 elements (274,625 dofs), 4x4x4 subdomains of 16^3 "
                             "elements, overlap 2, kappa=exp(GRF) x 1e6 slabs, nev<=20, tau=0.3 "
                             "(profiling case: same subdomain size as the 128^3 workload)"),
@@ -180,7 +180,7 @@ def run_reference(args):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     w = WORKLOADS[args.workload]
     prob = make_problem(args.workload)
-    iters = args.ref_pcg_iters
+    iters = args.ref_pcg_iters if args.ref_pcg_iters is not None else w.get("pcg_iters", 40)
     vals = []
     for step in range(args.warmup + args.steps):
         r = oracle_sample(prob, w["nev"], w["tau"], args.ref_sample, iters)
@@ -362,7 +362,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison steps")
     ap.add_argument("--no-profile", action="store_true", help="skip the profiled step")
     ap.add_argument("--ref-sample", type=int, default=3)
-    ap.add_argument("--ref-pcg-iters", type=int, default=40)
+    ap.add_argument("--ref-pcg-iters", type=int, default=None,
+                    help="PCG iterations the reference arm extrapolates to (default: the "
+                         "workload's measured count, GPU and oracle agree within 2; else 40)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--serve-requests", type=int, default=150)
