@@ -343,6 +343,14 @@ void geneo_free_host(void* p);
  * (all handles, all threads). */
 int64_t geneo_launch_count(void);
 
+/*
+ * Sizes in bytes of geneo_problem_t, geneo_options_t, geneo_solve_info_t and
+ * geneo_coarse_info_t as compiled into the library, written to out[0..3]
+ * (at most n of them), so a binding can check its struct layouts.  Host
+ * only; returns the number written.
+ */
+int32_t geneo_struct_sizes(int64_t* out, int32_t n);
+
 /* Release all device memory of the handle (NULL is allowed).  Waits for the
  * handle's work on the stream of its last call (setup, apply or solve),
  * which must still exist, and returns the memory to the device's

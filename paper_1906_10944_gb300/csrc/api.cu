@@ -293,6 +293,15 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
 
 int64_t geneo_launch_count(void) { return geneo::launch_count(); }
 
+int32_t geneo_struct_sizes(int64_t* out, int32_t n) {
+  const int64_t sz[4] = {(int64_t)sizeof(geneo_problem_t), (int64_t)sizeof(geneo_options_t),
+                         (int64_t)sizeof(geneo_solve_info_t), (int64_t)sizeof(geneo_coarse_info_t)};
+  if (!out || n <= 0) return 0;
+  const int32_t k = n < 4 ? n : 4;
+  for (int32_t i = 0; i < k; ++i) out[i] = sz[i];
+  return k;
+}
+
 geneo_status_t geneo_get_subdomain(geneo_handle_t h, int32_t j, int32_t* n_neu, int32_t* n_dir,
                                    int32_t* m, int32_t* s, int32_t* dir_dofs, int64_t dir_cap,
                                    double* pu, int64_t pu_cap, double* lambda, int64_t lambda_cap,

@@ -37,6 +37,7 @@ EXPORTED = [
     "geneo_default_options", "geneo_setup", "geneo_apply", "geneo_pcg_solve", "geneo_query",
     "geneo_get_subdomain", "geneo_grow_partition", "geneo_free_host", "geneo_destroy",
     "geneo_status_str", "geneo_last_error", "geneo_launch_count", "geneo_pcg_solve_noalloc",
+    "geneo_struct_sizes",
 ]
 
 
@@ -126,6 +127,8 @@ def load_library(path: str = LIB_PATH):
     lib.geneo_last_error.restype = I32
     lib.geneo_pcg_solve_noalloc.argtypes = [VP, VP, VP, D, I32, P(geneo_solve_info_t), VP]
     lib.geneo_pcg_solve_noalloc.restype = I32
+    lib.geneo_struct_sizes.argtypes = [VP, I32]
+    lib.geneo_struct_sizes.restype = I32
     lib.geneo_launch_count.argtypes = []
     lib.geneo_launch_count.restype = I64
     _lib = lib
@@ -359,3 +362,12 @@ class GenEO:
             self.close()
         except Exception:
             pass
+
+
+def geneo_struct_sizes():
+    """Struct sizes compiled into the library (problem, options, solve info,
+    coarse info), for layout checks."""
+    lib = load_library()
+    out = np.zeros(4, dtype=np.int64)
+    k = lib.geneo_struct_sizes(_ptr(out), 4)
+    return [int(v) for v in out[:k]]

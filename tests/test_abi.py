@@ -85,3 +85,13 @@ def test_option_limits_rejected_without_gpu():
         o = geneo.geneo_default_options(**kw)
         h = C.c_void_p()
         assert lib.geneo_setup(C.byref(prob), C.byref(o), None, C.byref(h)) == 1, kw
+
+
+def test_binding_struct_layouts_match_the_library():
+    import ctypes
+    geneo, _ = _lib()
+    sizes = geneo.geneo_struct_sizes()
+    assert sizes == [ctypes.sizeof(geneo.geneo_problem_t), ctypes.sizeof(geneo.geneo_options_t),
+                     ctypes.sizeof(geneo.geneo_solve_info_t), ctypes.sizeof(geneo.geneo_coarse_info_t)]
+    o = geneo.geneo_default_options()
+    assert (o.first_nev, o.guard, o.fp32_pivot_tol, o.precision) == (-1, -1, 1e-4, geneo.GENEO_PREC_FP64)
