@@ -11,6 +11,7 @@ from .geneo_oracle import (  # noqa: F401
     subdomain_sets,
     element_multiplicity,
     partition_of_unity,
+    sarkis_partition_of_unity,
     dirichlet_matrix,
     neumann_matrix,
     overlap_matrix,

@@ -32,10 +32,14 @@ is used):
       identity on them.
   R7  Basis vectors are X_j p / ||X_j p||_2 with the sign chosen so that the
       entry of largest magnitude is positive (first such entry on ties).
-  R8  PCG starts from x0 = 0 and stops when ||r_k||_2 <= tol ||b||_2 with the
-      recursively updated residual (Section 5.3 states a residual reduction).
+  R8  PCG starts from x0 = 0 and stops when ||r_k||_2 <= tol ||b||_2
+      (Section 5.3 states a residual reduction): the recursively updated
+      residual is tested first, then the true residual b - A x, which
+      replaces the recursive one when it is still above tol.
   R9  The condition number reported by the paper is estimated from the CG
       coefficients (Lanczos tridiagonal matrix).
+  R11 The smooth partition of unity Section 3 shows (Sarkis) is the ratio of
+      element-layer distances to the inner subdomain boundaries.
 """
 from __future__ import annotations
 
@@ -107,6 +111,54 @@ def partition_of_unity(prob, sets):
         x[s["dpos"]] = 1.0 / c[s["D"]]
         xs.append(x)
     return c, xs
+
+
+def sarkis_partition_of_unity(prob, sets):
+    """Smooth (Sarkis) partition of unity, the second example of Section 3
+    (Fig. 2, right), read as R11: d_j(k) is the number of element layers
+    between dof k and the inner boundary of Omega_j (the dofs of N_j that
+    are not in D_j, i.e. that touch an element outside Omega_j), measured as
+    breadth-first distance over the elements of Omega_j (two dofs are
+    neighbours when one element holds both); X_j(k) = d_j(k) / sum_i d_i(k).
+    X_j vanishes on the inner boundary and ramps up linearly across the
+    overlap.  A subdomain without inner boundary takes d_j = 1 everywhere.
+    Returns (sum_i d_i, [X_j on N_j])."""
+    dist = []
+    for j, s in enumerate(sets):
+        N = s["N"]
+        el = prob.sub_elems(j)
+        ed = prob.elem_dofs[el]
+        loc = np.searchsorted(N, ed)
+        loc = np.where(loc < N.size, loc, 0)
+        valid = N[loc] == ed
+        k = ed.shape[1]
+        rows = np.repeat(loc, k, axis=1)[np.repeat(valid, k, axis=1) & np.tile(valid, (1, k))]
+        cols = np.tile(loc, (1, k))[np.repeat(valid, k, axis=1) & np.tile(valid, (1, k))]
+        G = sp.csr_matrix((np.ones(rows.size), (rows, cols)), shape=(N.size, N.size))
+        d = np.full(N.size, -1, dtype=np.int64)
+        inner = np.ones(N.size, dtype=bool)
+        inner[s["dpos"]] = False
+        if not inner.any():
+            dist.append(np.ones(N.size))
+            continue
+        d[inner] = 0
+        frontier = np.nonzero(inner)[0]
+        level = 0
+        while frontier.size:
+            level += 1
+            reach = np.unique(G[frontier].indices)
+            frontier = reach[d[reach] < 0]
+            d[frontier] = level
+        dist.append(d.astype(np.float64))
+    total = np.zeros(prob.n)
+    for s, d in zip(sets, dist):
+        total[s["N"]] += d
+    xs = []
+    for s, d in zip(sets, dist):
+        x = np.zeros(s["N"].size)
+        x[s["dpos"]] = d[s["dpos"]] / total[s["D"]]
+        xs.append(x)
+    return total, xs
 
 
 # ----------------------------------------------------------------------------
@@ -240,8 +292,19 @@ def lanczos_condition_estimate(alphas, betas):
     return float(ev[-1] / ev[0])
 
 
-def pcg(A, b, apply_M, tol=1e-8, maxit=1000, x0=None):
-    """Textbook preconditioned conjugate gradients (R8)."""
+def pcg(A, b, apply_M, tol=1e-8, maxit=1000, x0=None, max_replace=5):
+    """Textbook preconditioned conjugate gradients (R8).
+
+    The iteration updates the residual recursively; when that recursive
+    residual reaches tol, the true residual b - A x is formed.  If it is
+    still above tol, it replaces the recursive residual and CG restarts from
+    the current x (p = M^{-1} r), at most max_replace times; the solve stops
+    unconverged when a replacement did not at least halve the true residual
+    (the rounding floor of x in FP64 is reached).  A replacement breaks the
+    Lanczos relation of the CG coefficients, so the condition estimate uses
+    the coefficients up to the first replacement.  hist holds the recursive
+    residuals ||r_k|| / ||b||.
+    """
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - A @ x
     bn = np.linalg.norm(b)
@@ -253,7 +316,10 @@ def pcg(A, b, apply_M, tol=1e-8, maxit=1000, x0=None):
     hist = [np.linalg.norm(r) / bn]
     alphas, betas = [], []
     it = 0
-    while hist[-1] > tol and it < maxit:
+    replaced = 0
+    n_lanczos = None
+    last_true = np.inf
+    while it < maxit:
         q = A @ p
         pq = p @ q
         if pq <= 0:
@@ -263,13 +329,27 @@ def pcg(A, b, apply_M, tol=1e-8, maxit=1000, x0=None):
         r -= alpha * q
         it += 1
         hist.append(np.linalg.norm(r) / bn)
-        alphas.append(alpha)
+        if n_lanczos is None:
+            alphas.append(alpha)
         if hist[-1] <= tol:
-            break
+            r_true = b - A @ x
+            rel_true = np.linalg.norm(r_true) / bn
+            if rel_true <= tol or replaced >= max_replace or rel_true > 0.5 * last_true:
+                break
+            last_true = rel_true
+            replaced += 1
+            if n_lanczos is None:
+                n_lanczos = len(alphas)
+            r = r_true
+            z = apply_M(r)
+            rz = r @ z
+            p = z.copy()
+            continue
         z = apply_M(r)
         rz_new = r @ z
         beta = rz_new / rz
-        betas.append(beta)
+        if n_lanczos is None:
+            betas.append(beta)
         rz = rz_new
         p = z + beta * p
     return x, it, hist, lanczos_condition_estimate(alphas, betas)
@@ -283,38 +363,68 @@ def theorem1_bound(k0, H_over_delta):
 # ----------------------------------------------------------------------------
 # The whole method.
 # ----------------------------------------------------------------------------
-class GenEOOracle:
-    """Setup and application of M^{-1}_{AS,2} (Section 3, Definition 2)."""
+# state handed to forked worker processes (see GenEOOracle, workers > 1)
+_WORK = None
 
-    def __init__(self, prob, opts=None, subdomains=None):
+
+def _local_part(j):
+    """Eigenproblem, selection and coarse vectors of subdomain j (the
+    per-subdomain steps of Sections 4.3 and 4.4)."""
+    prob, sets, xs, e_tau, o, guard = _WORK
+    if o.nev_max <= 0:
+        return j, np.zeros(0), 0, np.zeros((sets[j]["N"].size, 0))
+    At, B = geneo_pencil(prob, j, sets, xs, e_tau, o.eig_form)
+    lam, P = local_eigenpairs(At, B, o.nev_max + guard, o.sigma, o.dense_max, o.arpack_tol)
+    m = select_count(lam, o.tau, o.nev_max, o.fixed_nev)
+    return j, lam, m, coarse_vectors(P, xs[j], m)
+
+
+class GenEOOracle:
+    """Setup and application of M^{-1}_{AS,2} (Section 3, Definition 2).
+
+    pu: None (the standard partition of unity of Section 4.3), "sarkis"
+    (R11), or a list of weight vectors X_j on N_j given by the caller (any
+    weights of Definition 3).  workers > 1 runs the independent
+    per-subdomain eigenproblems in that many processes of the given
+    multiprocessing start method ("fork" shares the problem without copying
+    it; use it only in a process that has not initialised CUDA)."""
+
+    def __init__(self, prob, opts=None, subdomains=None, pu=None, workers=1, mp_context="fork"):
+        global _WORK
         self.prob = prob
         self.opts = opts or OracleOptions()
         o = self.opts
         A = prob.A
         self.sets = subdomain_sets(prob)
         self.e_tau = element_multiplicity(prob)
-        self.c, self.xs = partition_of_unity(prob, self.sets)
+        if pu is None:
+            self.c, self.xs = partition_of_unity(prob, self.sets)
+        elif isinstance(pu, str) and pu == "sarkis":
+            self.c, self.xs = sarkis_partition_of_unity(prob, self.sets)
+        else:
+            self.c, self.xs = None, [np.asarray(x, dtype=np.float64) for x in pu]
         guard = o.guard if o.guard >= 0 else min(10, o.nev_max)
-        sel = range(prob.n_sub) if subdomains is None else subdomains
+        sel = list(range(prob.n_sub) if subdomains is None else subdomains)
         self.local_lu = {}
         self.lams, self.ms, self.Zloc = {}, {}, {}
-        for j in sel:
-            s = self.sets[j]
-            Aj = dirichlet_matrix(A, s["D"])
-            self.local_lu[j] = spla.splu(Aj.tocsc())
-            if o.nev_max > 0:
-                At, B = geneo_pencil(prob, j, self.sets, self.xs, self.e_tau, o.eig_form)
-                lam, P = local_eigenpairs(At, B, o.nev_max + guard, o.sigma, o.dense_max,
-                                          o.arpack_tol)
-                m = select_count(lam, o.tau, o.nev_max, o.fixed_nev)
-                self.lams[j] = lam
-                self.ms[j] = m
-                self.Zloc[j] = coarse_vectors(P, self.xs[j], m)
+        _WORK = (prob, self.sets, self.xs, self.e_tau, o, guard)
+        try:
+            if workers > 1 and len(sel) > 1:
+                import multiprocessing as mp
+                with mp.get_context(mp_context).Pool(workers) as pool:
+                    parts = pool.map(_local_part, sel, chunksize=1)
             else:
-                self.lams[j] = np.zeros(0)
-                self.ms[j] = 0
-                self.Zloc[j] = np.zeros((s["N"].size, 0))
-        self.subdomains = list(sel)
+                parts = [_local_part(j) for j in sel]
+        finally:
+            _WORK = None
+        for j, lam, m, Z in parts:
+            self.lams[j] = lam
+            self.ms[j] = m
+            self.Zloc[j] = Z
+        for j in sel:
+            Aj = dirichlet_matrix(A, self.sets[j]["D"])
+            self.local_lu[j] = spla.splu(Aj.tocsc())
+        self.subdomains = sel
         if subdomains is None:
             self._build_coarse()
 
