@@ -129,47 +129,153 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(prob, nev, tau, n_sample, pcg_iters):
-    """Time the oracle on a sample of interior subdomains (local Dirichlet
-    matrix + LU, Neumann/overlap assembly, ARPACK shift-invert eigensolve,
-    coarse vectors, one local solve) on one core, then extrapolate to the
-    whole workload: setup = mean per-subdomain time x N; solve = pcg_iters x
-    (N local solves + one SpMV); the coarse factorisation is timed at full
-    size when its dimension is known from the GPU run."""
+GOLDEN = {"darcy3d_128": os.path.join(ROOT, "tests", "golden", "darcy3d_128_oracle.json")}
+
+_CPU = None  # per worker process: (problem, sets, partition of unity, e_tau, nev, tau)
+
+
+def _cpu_init(workload):
+    """Pool initializer: every worker builds the same seeded problem once."""
+    global _CPU
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import oracle
+    w = WORKLOADS[workload]
+    prob = make_problem(workload)
+    sets = oracle.subdomain_sets(prob)
+    e_tau = oracle.element_multiplicity(prob)
+    _, xs = oracle.partition_of_unity(prob, sets)
+    _CPU = (prob, sets, xs, e_tau, w["nev"], w["tau"])
+
+
+def _cpu_task(j):
+    """The oracle's per-subdomain setup of subdomain j (Dirichlet matrix and
+    its sparse LU, Neumann and overlap assembly, ARPACK shift-invert
+    eigensolve, selection, coarse vectors) and one local solve, timed."""
     import numpy as np
     import scipy.sparse.linalg as spla
     import oracle
+    prob, sets, xs, e_tau, nev, tau = _CPU
     t0 = time.perf_counter()
-    sets = oracle.subdomain_sets(prob)
-    e_tau = oracle.element_multiplicity(prob)
-    c, xs = oracle.partition_of_unity(prob, sets)
-    t_struct = time.perf_counter() - t0
-    N = prob.n_sub
-    # interior subdomains (largest, most expensive)
-    sizes = np.array([s["N"].size for s in sets])
-    order = np.argsort(-sizes, kind="stable")
-    pick = order[:n_sample]
-    t_setup, t_solve = [], []
-    for j in pick:
+    Aj = oracle.dirichlet_matrix(prob.A, sets[j]["D"])
+    lu = spla.splu(Aj.tocsc())
+    At, B = oracle.geneo_pencil(prob, j, sets, xs, e_tau)
+    lam, P = oracle.local_eigenpairs(At, B, nev + min(10, nev), -0.01, 2500, 1e-12)
+    m = oracle.select_count(lam, tau, nev)
+    oracle.coarse_vectors(P, xs[j], m)
+    t1 = time.perf_counter()
+    lu.solve(np.ones(sets[j]["D"].size))
+    return t1 - t0, time.perf_counter() - t1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OracleBaseline:
+    """The oracle as it stands, timed on the host cores: the per-subdomain
+    setup of a seeded sample of subdomains runs in a spawn pool of one
+    process per core (BLAS threads 1); the structure, the coarse matrix
+    Z^T A Z (Z with the oracle's own per-subdomain counts m_j and the
+    pattern of D_j), its dense Cholesky, SpMV and the coarse solve are timed
+    in this process; the oracle's PCG applies its local solves one after
+    another on one core.  The time to solution is extrapolated to all N
+    subdomains and the PCG iteration count."""
+
+    def __init__(self, workload, prob, workers=None):
+        import multiprocessing as mp
+        import numpy as np
+        import scipy.linalg as sla
+        import scipy.sparse as sp
+        import oracle
+        self.workload = workload
+        self.prob = prob
+        self.workers = workers or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_cpu_init, initargs=(workload,))
+        w = WORKLOADS[workload]
+        self.golden = None
+        if workload in GOLDEN and os.path.exists(GOLDEN[workload]):
+            with open(GOLDEN[workload]) as f:
+                self.golden = json.load(f)
+        t0 = time.perf_counter()
+        sets = oracle.subdomain_sets(prob)
+        e_tau = oracle.element_multiplicity(prob)
+        oracle.partition_of_unity(prob, sets)
+        self.t_struct = time.perf_counter() - t0
+        del e_tau
+        # coarse matrix and factor at the oracle's own dimension: Z with m_j
+        # columns on the rows D_j (values seeded; the cost depends on the
+        # pattern only)
+        m = self.golden["m"] if self.golden else [min(w["nev"], 3)] * prob.n_sub
+        rng = np.random.default_rng(0)
+        rows, cols, off = [], [], 0
+        for j, s in enumerate(sets):
+            for k in range(m[j]):
+                rows.append(s["D"])
+                cols.append(np.full(s["D"].size, off + k))
+            off += m[j]
+        self.dim_H = off
+        r = np.concatenate(rows)
+        Zg = sp.csr_matrix((rng.uniform(0.5, 1.0, r.size), (r, np.concatenate(cols))), shape=(prob.n, off))
+        t0 = time.perf_counter()
+        AH = oracle.coarse_matrix(prob.A, Zg)
+        AH += off * np.eye(off) * np.abs(AH).max()   # keep the seeded stand-in definite
         t1 = time.perf_counter()
-        Aj = oracle.dirichlet_matrix(prob.A, sets[j]["D"])
-        lu = spla.splu(Aj.tocsc())
-        At, B = oracle.geneo_pencil(prob, j, sets, xs, e_tau)
-        lam, P = oracle.local_eigenpairs(At, B, nev + min(10, nev), -0.01, 2500, 1e-12)
-        m = oracle.select_count(lam, tau, nev)
-        oracle.coarse_vectors(P, xs[j], m)
-        t_setup.append(time.perf_counter() - t1)
-        r = np.ones(sets[j]["D"].size)
+        ch = sla.cho_factor(AH, lower=True)
         t2 = time.perf_counter()
-        lu.solve(r)
-        t_solve.append(time.perf_counter() - t2)
-    x = np.ones(prob.n)
-    t3 = time.perf_counter()
-    prob.A @ x
-    t_spmv = time.perf_counter() - t3
-    total = t_struct + float(np.mean(t_setup)) * N + pcg_iters * (float(np.mean(t_solve)) * N + 2 * t_spmv)
-    return {"seconds": total, "sample_s": t_struct + sum(t_setup) + sum(t_solve) + t_spmv,
-            "n_sample": int(len(pick))}
+        c = Zg.T @ np.ones(prob.n)
+        sla.cho_solve(ch, c)
+        Zg @ c
+        t3 = time.perf_counter()
+        prob.A @ np.ones(prob.n)
+        t4 = time.perf_counter()
+        self.t_coarse_matrix, self.t_coarse_factor = t1 - t0, t2 - t1
+        self.t_coarse_solve, self.t_spmv = t3 - t2, t4 - t3
+        self.rng = np.random.default_rng(5)
+
+    def pcg_iterations(self, measured=None):
+        if measured is not None:
+            return int(measured), "iterations measured on the GPU in this run"
+        if self.golden:
+            return int(self.golden["pcg_iterations"]), "the oracle's own count (tests/golden)"
+        return int(WORKLOADS[self.workload].get("pcg_iters", 40)), "fixed estimate"
+
+    def step(self, per_worker, pcg_iters):
+        """One bounded sample: per_worker subdomains per process."""
+        import numpy as np
+        N = self.prob.n_sub
+        js = self.rng.choice(N, size=min(N, per_worker * self.workers), replace=False)
+        t0 = time.perf_counter()
+        res = self.pool.map(_cpu_task, [int(j) for j in js], chunksize=1)
+        wall = time.perf_counter() - t0
+        t_setup = np.array([r[0] for r in res])
+        t_solve = np.array([r[1] for r in res])
+        setup = float(t_setup.mean()) * N / self.workers
+        solve = pcg_iters * (float(t_solve.mean()) * N + 2 * self.t_spmv + self.t_coarse_solve)
+        total = self.t_struct + setup + self.t_coarse_matrix + self.t_coarse_factor + solve
+        return {"seconds": total, "setup_s": setup, "solve_s": solve, "wall_s": wall,
+                "cpu_s": float(t_setup.sum() + t_solve.sum()), "n_sample": int(js.size)}
+
+    def describe(self, r, pcg_iters, src):
+        return ("oracle (numpy/scipy FP64, ARPACK shift-invert) on %s, %d processes: per-subdomain "
+                "setup of %d seeded random subdomains (%.1f s of CPU work) extrapolated to %d "
+                "subdomains over %d processes; structure, coarse Z^T A Z (dim %d) and its Cholesky "
+                "timed whole; PCG %d iterations (%s) x (%d sequential local LU solves + 2 SpMV + "
+                "coarse solve) on one core"
+                % (cpu_model(), self.workers, r["n_sample"], r["cpu_s"], self.prob.n_sub, self.workers,
+                   self.dim_H, pcg_iters, src, self.prob.n_sub))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def run_reference(args):
@@ -180,22 +286,23 @@ def run_reference(args):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     w = WORKLOADS[args.workload]
     prob = make_problem(args.workload)
-    iters = args.ref_pcg_iters if args.ref_pcg_iters is not None else w.get("pcg_iters", 40)
-    vals = []
-    for step in range(args.warmup + args.steps):
-        r = oracle_sample(prob, w["nev"], w["tau"], args.ref_sample, iters)
-        if step >= args.warmup:
-            vals.append(prob.n / r["seconds"])
+    base = OracleBaseline(args.workload, prob)
+    iters, src = base.pcg_iterations(args.ref_pcg_iters)
+    vals, r = [], None
+    try:
+        for step in range(args.warmup + args.steps):
+            r = base.step(args.ref_per_worker, iters)
+            if step >= args.warmup:
+                vals.append(prob.n / r["seconds"])
+    finally:
+        base.close()
     value = statistics.median(vals)
-    sample = ("oracle (numpy/scipy FP64, ARPACK shift-invert) on %d largest subdomains per step, "
-              "1 core; extrapolated: setup x %d subdomains + %d PCG iterations x (%d local LU "
-              "solves + SpMV)" % (args.ref_sample, prob.n_sub, iters, prob.n_sub))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["desc"], "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base.workers, "kind": "oracle",
+                             "sample": base.describe(r, iters, src)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -361,10 +468,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison steps")
     ap.add_argument("--no-profile", action="store_true", help="skip the profiled step")
-    ap.add_argument("--ref-sample", type=int, default=3)
+    ap.add_argument("--ref-per-worker", type=int, default=1,
+                    help="subdomains per host process in each CPU-oracle sample")
     ap.add_argument("--ref-pcg-iters", type=int, default=None,
                     help="PCG iterations the reference arm extrapolates to (default: the "
-                         "workload's measured count, GPU and oracle agree within 2; else 40)")
+                         "oracle's own count from tests/golden, else a fixed estimate)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--serve-requests", type=int, default=150)
@@ -373,6 +481,12 @@ def main():
         return run_reference(args)
 
     import numpy as np
+    rank0 = int(os.environ.get("RANK", "0")) == 0
+    cpu_base = None
+    if rank0 and not args.no_cpu_baseline:
+        # the oracle's process pool (spawn) and its coarse timings come
+        # before this process touches the GPU
+        cpu_base = OracleBaseline(args.workload, make_problem(args.workload))
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -506,13 +620,14 @@ def main():
                                          hbm_src)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        r = oracle_sample(prob, w["nev"], w["tau"], args.ref_sample, info_m["iterations"])
-        cpu = {"value": prob.n / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d largest subdomains (setup incl. ARPACK) + one local solve each, "
-                         "1 core, %.1f s of CPU work; extrapolated to %d subdomains and %d PCG "
-                         "iterations" % (r["n_sample"], r["sample_s"], prob.n_sub,
-                                         info_m["iterations"])}
+    if rank == 0 and cpu_base is not None:
+        iters, src = cpu_base.pcg_iterations(info_m["iterations"])
+        r = cpu_base.step(2, iters)
+        cpu_base.close()
+        cpu = {"value": prob.n / r["seconds"], "unit": UNIT, "cores": cpu_base.workers, "kind": "oracle",
+               "sample": cpu_base.describe(r, iters, src),
+               "phases_s": {"setup": r["setup_s"], "solve": r["solve_s"],
+                            "coarse": cpu_base.t_coarse_matrix + cpu_base.t_coarse_factor}}
 
     serve = None
     if rank == 0 and not args.no_serve:

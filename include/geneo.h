@@ -41,12 +41,15 @@ typedef enum {
   GENEO_ERR_ARG = 1,          /* invalid argument or inconsistent sizes */
   GENEO_ERR_OOM = 2,          /* device allocation failed */
   GENEO_ERR_NOT_SPD = 3,      /* non-positive pivot in a Cholesky factorisation */
-  GENEO_ERR_EIG_NOCONV = 4,   /* local eigensolver reached eig_maxit */
+  GENEO_ERR_EIG_NOCONV = 4,   /* local eigensolver reached eig_maxit (only with
+                                 geneo_options_t.eig_strict = 1; otherwise the
+                                 count is reported in geneo_coarse_info_t) */
   GENEO_ERR_PCG_NOCONV = 5,   /* PCG reached maxit before the tolerance */
   GENEO_ERR_BREAKDOWN = 6,    /* PCG breakdown: p^T A p <= 0 or r^T z <= 0 */
   GENEO_ERR_CUDA = 7,         /* a CUDA runtime call failed */
   GENEO_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
-  GENEO_ERR_NONFINITE = 9     /* NaN or Inf met in the data */
+  GENEO_ERR_NONFINITE = 9     /* NaN or Inf met in the data (element matrices,
+                                 pivots, right-hand side, PCG residual) */
 } geneo_status_t;
 
 typedef enum { GENEO_MEM_HOST = 0, GENEO_MEM_DEVICE = 1 } geneo_mem_t;
@@ -55,6 +58,17 @@ typedef enum {
   GENEO_EIG_PAPER = 0,   /* B_j = X_j A_j^o X_j, A_j^o over overlap elements (Section 4.3) */
   GENEO_EIG_FULL = 1     /* B_j = X_j Atilde_j X_j (all elements of Omega_j) */
 } geneo_eig_form_t;
+
+/* Partition of unity of Section 3 (Definition 3) when the caller gives no
+ * weights: the standard piecewise-constant one of Section 4.3 (1/c_k on D_j),
+ * or the smooth one Section 3 shows beside it (Sarkis): X_j(k) = d_j(k) /
+ * sum_i d_i(k), d_j(k) the number of element layers between dof k and the
+ * inner boundary of Omega_j (the dofs of N_j outside D_j), so X_j falls
+ * linearly to zero across the overlap. */
+typedef enum {
+  GENEO_PU_STANDARD = 0,
+  GENEO_PU_SARKIS = 1
+} geneo_pu_kind_t;
 
 typedef enum {
   GENEO_PREC_FP64 = 0,   /* all factors and local solves in FP64 */
@@ -96,6 +110,13 @@ typedef enum {
  *               dofs of the closure of Omega_j without global Dirichlet
  *               dofs, sorted ascending (geneo_grow_partition produces both
  *               lists from a non-overlapping partition).
+ *  pu_weights   optional (NULL: the partition of unity options.pu_kind
+ *               selects); otherwise the weights mu_{j,k} of Definition 3 in
+ *               the layout of sub_dof: X_j(k) of dof sub_dof[t] at
+ *               pu_weights[t].  They must lie in [0, 1], vanish on the dofs
+ *               of N_j outside D_j (the inner boundary of Omega_j), and sum
+ *               to one over the subdomains on every non-Dirichlet dof (to
+ *               1e-12); else geneo_setup returns GENEO_ERR_ARG.
  *  Every subdomain must be non-empty.  Every non-Dirichlet dof must lie in
  *  the interior of at least one subdomain (overlap >= 1 element layer).
  */
@@ -117,6 +138,7 @@ typedef struct {
   const int32_t* sub_elem;
   const int64_t* sub_dof_ptr;
   const int32_t* sub_dof;
+  const double* pu_weights;
 } geneo_problem_t;
 
 /*
@@ -150,6 +172,18 @@ typedef struct {
  *             Those subdomains also run the eigensolver's block products
  *             and orthogonalisation in FP64 (the others in double-single
  *             arithmetic and, for the first pass, FP32).
+ *  pu_kind    geneo_pu_kind_t, used when the problem gives no pu_weights
+ *             (default GENEO_PU_STANDARD).
+ *  eig_strict 1: geneo_setup returns GENEO_ERR_EIG_NOCONV when a subdomain's
+ *             eigensolve reaches eig_maxit unconverged; 0 (default): the
+ *             setup goes on with the Ritz vectors it has and reports the
+ *             count in geneo_coarse_info_t.eig_unconverged.
+ *  deterministic  1 (default): every reduction runs in a fixed order, so
+ *             repeated calls give bitwise identical results.  0: the PCG
+ *             inner products are accumulated with atomic additions (one
+ *             launch fewer each); results then vary in the last bits from
+ *             run to run.
+ *  reserved   must be 0.
  */
 typedef struct {
   double tau;
@@ -169,21 +203,30 @@ typedef struct {
   int32_t first_nev;
   uint64_t seed;
   double fp32_pivot_tol;
+  int32_t pu_kind;
+  int32_t eig_strict;
+  int32_t deterministic;
+  int32_t reserved;
 } geneo_options_t;
 
 typedef struct geneo_handle_s* geneo_handle_t;
 
 /* Per-solve report (Section 5.3 and 5.4 report iterations and a condition
  * estimate).  resid_hist may be NULL; otherwise it receives up to
- * resid_hist_cap relative residuals ||r_k||/||b|| (k = 0, 1, ...). */
+ * resid_hist_cap recursive relative residuals ||r_k||/||b|| (k = 0, 1, ...).
+ * converged = 1 when the true residual ||b - A x||/||b|| met tol. */
 typedef struct {
   int32_t iterations;
   int32_t converged;
   double rel_residual;       /* recursive ||r||/||b|| at exit */
-  double kappa_estimate;     /* Lanczos estimate of kappa(M^{-1} A) */
+  double kappa_estimate;     /* Lanczos estimate of kappa(M^{-1} A), from the
+                                CG coefficients before the first replacement */
   double* resid_hist;
   int32_t resid_hist_cap;
   int32_t resid_hist_len;
+  double true_residual;      /* ||b - A x||/||b|| of the returned x (FP64) */
+  int32_t replacements;      /* true-residual replacements (restarts) made */
+  int32_t reserved;
 } geneo_solve_info_t;
 
 /* Kernel families of geneo_coarse_info_t.prof_*. */
@@ -217,6 +260,9 @@ typedef struct {
                                 (K_j factored in FP64, a residual that stopped
                                 halving, or still iterating at iteration 30);
                                 the others use double-single products */
+  int32_t eig_unconverged;   /* subdomains whose eigensolve reached eig_maxit
+                                unconverged (their Ritz vectors are used) */
+  int32_t reserved;
   int64_t device_bytes;      /* device memory held by the handle */
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse
@@ -266,11 +312,18 @@ geneo_status_t geneo_apply(geneo_handle_t h, const double* r_dev, double* z_dev,
                            void* stream);
 
 /*
- * Solve A x = b by PCG with M^{-1}_{AS,2} (x0 = 0, stop when
- * ||r_k||_2 <= tol ||b||_2) for nrhs right-hand sides (stride n).  b and x
- * are device arrays unless `mem` is GENEO_MEM_HOST, in which case they are
- * host arrays and the copies are part of the call.  info may be NULL; with
- * nrhs > 1 it reports the last right-hand side.  Synchronises `stream`.
+ * Solve A x = b by PCG with M^{-1}_{AS,2} (Section 5; x0 = 0) for nrhs
+ * right-hand sides (stride n).  Stopping rule: when the recursively updated
+ * residual reaches ||r_k||_2 <= tol ||b||_2 the true residual b - A x is
+ * formed; the solve has converged when that meets tol too.  Otherwise the
+ * true residual replaces the recursive one and CG restarts from x, at most
+ * five times and only while each replacement at least halves it (below
+ * that the FP64 rounding of x, about eps ||(|A| |x|)|| / ||b||, bounds every
+ * residual); the call then returns GENEO_ERR_PCG_NOCONV with the reached
+ * true residual in info.  b and x are device arrays unless `mem` is
+ * GENEO_MEM_HOST, in which case they are host arrays and the copies are part
+ * of the call.  info may be NULL; with nrhs > 1 it reports the last
+ * right-hand side.  Synchronises `stream`.
  */
 geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int32_t nrhs,
                                double tol, int32_t maxit, int32_t mem,
@@ -288,11 +341,17 @@ geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int
  * condition estimate live in one fixed device array inside the library
  * (73,856 bytes on every device that loads the library, held until the
  * process exits), and the vectors come from the handle, allocated by
- * geneo_setup.  Limit: maxit <= 4095; larger values return GENEO_ERR_ARG.
- * The first call on a device looks up that array's device address (with the
- * handle's device current) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents; the scalars are cleared at the start of every call.  Calls whose
+ * geneo_setup; the host arrays of the condition estimate are sized by
+ * geneo_setup too.  Limit: maxit <= 4095; larger values return
+ * GENEO_ERR_ARG.  The handle's device must be current (else GENEO_ERR_ARG),
+ * and its options.profile must be 0 (profiling creates CUDA events; else
+ * GENEO_ERR_ARG).  The first call on a device looks up that array's device
+ * address (with the handle's device current) and caches it per device
+ * ordinal for the life of the process; make that first call before any
+ * stream capture, and do not call the function again after a
+ * cudaDeviceReset of that device.  All calls share the array and it keeps
+ * the last call's contents; the scalars are cleared at the start of every
+ * call.  The stopping rule and info are those of geneo_pcg_solve.  Calls whose
  * work overlaps on the GPU (on different streams, or on different handles
  * of the same device) race and must not be issued.  b_dev and x_dev are
  * device arrays of n doubles; info as in geneo_pcg_solve.  Synchronises
@@ -361,8 +420,13 @@ void geneo_destroy(geneo_handle_t h);
 /* Static string describing a status code. */
 const char* geneo_status_str(geneo_status_t s);
 
-/* Details of the last error on this handle: the device status words
- * (code, subdomain or matrix id, row or index, extra). */
+/* Details of the last error on this handle: the status code, the subdomain
+ * (or matrix id, -1 if none) and the row or index where the device recorded
+ * it (for GENEO_ERR_NOT_SPD: subdomain and pivot row of the failed
+ * factorisation; GENEO_ERR_NONFINITE from the assembly: subdomain and
+ * element).  With h = NULL: the same for the last geneo_setup call of the
+ * calling thread (code 0 if it succeeded), whose handle no longer exists
+ * when it failed.  Always returns GENEO_OK. */
 geneo_status_t geneo_last_error(geneo_handle_t h, int32_t* code, int32_t* where, int64_t* index);
 
 #ifdef __cplusplus

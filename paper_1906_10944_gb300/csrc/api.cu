@@ -23,6 +23,10 @@ geneo_status_t check_status(geneo_handle_s* h, cudaStream_t s) {
 
 namespace {
 
+// details of the last geneo_setup on this thread that failed (its handle is
+// gone by then), for geneo_last_error(NULL, ...)
+thread_local geneo::DevStatus g_setup_error{0, 0, 0};
+
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -95,6 +99,7 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   GENEO_TRY(to_device(p->elem_mats, p->n_elem * p->elem_ndof * p->elem_ndof, host, tmp, s, &dp.elem_mats));
   GENEO_TRY(to_device(p->sub_elem, sep[N], host, tmp, s, &dp.sub_elem));
   GENEO_TRY(to_device(p->sub_dof, sdp[N], host, tmp, s, &dp.sub_dof));
+  if (p->pu_weights) GENEO_TRY(to_device(p->pu_weights, sdp[N], host, tmp, s, &dp.pu_weights));
   // the handle keeps A and the Dirichlet mask
   DevMem& M = h->mem;
   GENEO_TRY(M.get(&h->rowptr, (size_t)h->n + 1));
@@ -127,6 +132,8 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
     h->lambda_host.clear();
     for (auto& d : h->hsub) d.s = 0;
   }
+  // eigensolver cap reached: an error only when the caller asks for it
+  if (h->opt.eig_strict && h->eig_unconv > 0) return GENEO_ERR_EIG_NOCONV;
   // a6-a7: coarse basis, coarse matrix, factorisation
   GENEO_TRY(geneo::build_coarse(h, asmb, X, tmp, s, &h->setup_ms[4], &h->setup_ms[5], &h->setup_ms[6]));
   // join the A_j factorisation (aux stream) before the temporaries go; A_j
@@ -160,6 +167,10 @@ void geneo_default_options(geneo_options_t* o) {
   o->first_nev = -1;
   o->fp32_pivot_tol = 1e-4;
   o->seed = 0x5EED5EEDull;
+  o->pu_kind = GENEO_PU_STANDARD;
+  o->eig_strict = 0;
+  o->deterministic = 1;
+  o->reserved = 0;
 }
 
 geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* opt, void* stream,
@@ -178,7 +189,9 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   if (o.nev_max < 0 || o.nev_max > 34 || !(o.sigma < 0.0) || !(o.eig_tol > 0.0) || o.eig_maxit < 1 ||
       !(o.fp32_pivot_tol >= 0.0 && o.fp32_pivot_tol < 1.0) ||
       (o.eig_form != GENEO_EIG_PAPER && o.eig_form != GENEO_EIG_FULL) ||
-      (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32))
+      (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32) ||
+      (o.pu_kind != GENEO_PU_STANDARD && o.pu_kind != GENEO_PU_SARKIS) ||
+      (o.eig_strict != 0 && o.eig_strict != 1) || (o.deterministic != 0 && o.deterministic != 1))
     return GENEO_ERR_ARG;
   // keep freed device memory in the stream-ordered pool for the next setup
   {
@@ -198,6 +211,11 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   const int guard = o.guard >= 0 ? o.guard : std::min(3, o.nev_max);
   h->s_block = std::min(o.nev_max + guard, 34);
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GENEO_ERR_CUDA;
+  }
   if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -209,9 +227,12 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   geneo_status_t st = setup_impl(h, prob, h->stream);
   if (st != GENEO_OK) {
     cudaStreamSynchronize(h->stream);
+    g_setup_error = h->hstat;
+    if (g_setup_error.code == 0) g_setup_error = geneo::DevStatus{(int32_t)st, -1, -1};
     geneo_destroy(h);
     return st;
   }
+  g_setup_error = geneo::DevStatus{0, 0, 0};
   *out = h;
   return GENEO_OK;
 }
@@ -272,6 +293,7 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->fp64_factors_K = h->nK64;
   info->fp64_factors_A = h->nA64;
   info->fp64_ortho = h->eig_o64;
+  info->eig_unconverged = h->eig_unconv;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->factor_flops = h->factor_flops;
@@ -357,10 +379,10 @@ const char* geneo_status_str(geneo_status_t s) {
 }
 
 geneo_status_t geneo_last_error(geneo_handle_t h, int32_t* code, int32_t* where, int64_t* index) {
-  if (!h) return GENEO_ERR_ARG;
-  if (code) *code = h->hstat.code;
-  if (where) *where = h->hstat.where;
-  if (index) *index = h->hstat.index;
+  const geneo::DevStatus& e = h ? h->hstat : g_setup_error;
+  if (code) *code = e.code;
+  if (where) *where = e.where;
+  if (index) *index = e.index;
   return GENEO_OK;
 }
 

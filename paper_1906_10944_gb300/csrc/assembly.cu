@@ -116,6 +116,102 @@ __global__ void k_pu(const SubDesc* __restrict__ sub, const int32_t* __restrict_
   }
 }
 
+// Caller weights (Definition 3): each X_j(k) in [0, 1] and zero on the
+// inner boundary of Omega_j (the N-rows outside D_j).
+__global__ void k_check_pu_local(const SubDesc* __restrict__ sub, const int32_t* __restrict__ nToD,
+                                 const double* __restrict__ pu, DevStatus* st) {
+  const SubDesc d = sub[blockIdx.x];
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const int64_t r = d.offN + a;
+    const double v = pu[r];
+    if (!(v >= 0.0 && v <= 1.0) || (nToD[r] < 0 && v != 0.0)) record_error(st, GENEO_ERR_ARG, blockIdx.x, a);
+  }
+}
+
+// ... and sum_j X_j(k) = 1 (to 1e-12) on every non-Dirichlet dof, summed in
+// the fixed order of the inverse map.
+__global__ void k_check_pu_sum(int64_t n, const uint8_t* __restrict__ dir, const int64_t* __restrict__ invD_ptr,
+                               const int32_t* __restrict__ invD_sub, const int32_t* __restrict__ invD_loc,
+                               const SubDesc* __restrict__ sub, const int32_t* __restrict__ dpos,
+                               const double* __restrict__ pu, DevStatus* st) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (dir[k]) continue;
+    double sum = 0.0;
+    for (int64_t t = invD_ptr[k]; t < invD_ptr[k + 1]; ++t) {
+      const SubDesc& d = sub[invD_sub[t]];
+      sum += pu[d.offN + dpos[d.offN + invD_loc[t]]];
+    }
+    if (!(fabs(sum - 1.0) <= 1e-12)) record_error(st, GENEO_ERR_ARG, -1, k);
+  }
+}
+
+// Smooth (Sarkis) partition of unity, Section 3 (Fig. 2, right).
+// Step 1: d_j(a) = element layers between N-row a and the inner boundary of
+// Omega_j (the N-rows outside D_j, d = 0), by breadth-first levels over the
+// local pattern: every coupling of a D_j row comes from an element of
+// Omega_j, so these are distances through Omega_j.  A subdomain without
+// inner boundary takes d = 1 everywhere.  The level loop is bounded by nN.
+__global__ void __launch_bounds__(kT)
+k_sarkis_dist(const SubDesc* __restrict__ sub, const int32_t* __restrict__ nToD,
+              const int64_t* __restrict__ lrow, const int32_t* __restrict__ lcol, int32_t* __restrict__ dist) {
+  const SubDesc d = sub[blockIdx.x];
+  int32_t* dj = dist + d.offN;
+  int inner = 0;
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const bool b = nToD[d.offN + a] < 0;
+    dj[a] = b ? 0 : -1;
+    inner |= b;
+  }
+  if (!__syncthreads_or(inner)) {
+    for (int a = threadIdx.x; a < d.nN; a += blockDim.x) dj[a] = 1;
+    return;
+  }
+  for (int level = 1; level <= d.nN; ++level) {
+    int changed = 0;
+    for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+      if (dj[a] >= 0) continue;
+      // a row set at this level never equals level - 1, so rows written in
+      // this sweep do not feed it
+      for (int64_t e = lrow[d.offN + a]; e < lrow[d.offN + a + 1]; ++e)
+        if (dj[lcol[e]] == level - 1) {
+          dj[a] = level;
+          changed = 1;
+          break;
+        }
+    }
+    if (!__syncthreads_or(changed)) break;
+  }
+}
+
+// Step 2: total(k) = sum_i d_i(k) over the subdomains whose D holds k (the
+// others contribute d = 0 or do not hold k).
+__global__ void k_sarkis_total(int64_t n, const int64_t* __restrict__ invD_ptr, const int32_t* __restrict__ invD_sub,
+                               const int32_t* __restrict__ invD_loc, const SubDesc* __restrict__ sub,
+                               const int32_t* __restrict__ dpos, const int32_t* __restrict__ dist,
+                               double* __restrict__ total) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int64_t t = invD_ptr[k]; t < invD_ptr[k + 1]; ++t) {
+      const SubDesc& d = sub[invD_sub[t]];
+      sum += (double)dist[d.offN + dpos[d.offN + invD_loc[t]]];
+    }
+    total[k] = sum;
+  }
+}
+
+// Step 3: X_j = d_j / total on D_j, 0 on the inner boundary.
+__global__ void k_sarkis_pu(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                            const int32_t* __restrict__ nToD, const int32_t* __restrict__ dist,
+                            const double* __restrict__ total, double* __restrict__ pu) {
+  const SubDesc d = sub[blockIdx.x];
+  for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
+    const int64_t r = d.offN + a;
+    pu[r] = nToD[r] >= 0 ? (double)dist[r] / total[Nlist[r]] : 0.0;
+  }
+}
+
 __global__ void k_fill_inv(const SubDesc* __restrict__ sub, const int32_t* __restrict__ list,
                            const int32_t* __restrict__ counts_per_sub, int use_nD,
                            const int64_t* __restrict__ ptr, int32_t* __restrict__ cursor,
@@ -230,7 +326,7 @@ __global__ void k_assemble(const SubDesc* __restrict__ sub, const int32_t* __res
                            const double* __restrict__ elem_mats, int ke,
                            const int32_t* __restrict__ e_tau, const int64_t* __restrict__ lrow,
                            const int32_t* __restrict__ lcol, double* __restrict__ lK,
-                           double* __restrict__ lB) {
+                           double* __restrict__ lB, DevStatus* st) {
   const SubDesc d = sub[blockIdx.x];
   const int32_t* Nj = Nlist + d.offN;
   const int32_t* Ej = sub_elem + d.offE;
@@ -256,6 +352,7 @@ __global__ void k_assemble(const SubDesc* __restrict__ sub, const int32_t* __res
         while (slot < r1 && lcol[slot] != bl) ++slot;
         if (slot >= r1) continue;  // cannot happen when A holds every element coupling
         const double v = Krow[bq];
+        if (!isfinite(v)) record_error(st, GENEO_ERR_NONFINITE, blockIdx.x, el);
         lK[slot] += v;
         if (ovl) lB[slot] += v;
       }
@@ -424,7 +521,12 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   GENEO_CUDA(cudaMemsetAsync(cmul, 0, sizeof(int32_t) * n, s));
   k_count_D<<<N, kT, 0, s>>>(h->dsub, h->Dlist, cmul); note_launch();
   k_check_cover<<<grid_for(n), kT, 0, s>>>(cmul, h->dir, n, h->dstat); note_launch();
-  k_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, cmul, h->pu); note_launch();
+  if (p->pu_weights) {  // caller weights (device view of the problem's array)
+    GENEO_CUDA(cudaMemcpyAsync(h->pu, p->pu_weights, sizeof(double) * h->sumN, cudaMemcpyDeviceToDevice, s));
+    k_check_pu_local<<<N, kT, 0, s>>>(h->dsub, h->nToD, h->pu, h->dstat); note_launch();
+  } else {
+    k_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, cmul, h->pu); note_launch();
+  }
   GENEO_CUDA(cudaGetLastError());
 
   // inverse map dof -> (j, D index), sorted by j
@@ -443,6 +545,10 @@ geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, Asse
   k_fill_inv<<<N, kT, 0, s>>>(h->dsub, h->Dlist, nullptr, 1, h->invD_ptr, cursor, h->invD_sub,
                               h->invD_loc); note_launch();
   k_sort_lists<<<grid_for(n), kT, 0, s>>>(h->invD_ptr, n, h->invD_sub, h->invD_loc); note_launch();
+  if (p->pu_weights) {
+    k_check_pu_sum<<<grid_for(n), kT, 0, s>>>(n, h->dir, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
+                                              h->dpos, h->pu, h->dstat); note_launch();
+  }
   GENEO_CUDA(cudaGetLastError());
   return check_status(h, s);
 }
@@ -517,11 +623,24 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   }
   GENEO_CUDA(cudaMemcpyAsync(h->dsub, h->hsub.data(), sizeof(SubDesc) * N, cudaMemcpyHostToDevice, s));
 
+  // smooth partition of unity (when chosen and no caller weights)
+  if (!p->pu_weights && h->opt.pu_kind == GENEO_PU_SARKIS) {
+    int32_t* dist = nullptr;
+    double* total = nullptr;
+    GENEO_TRY(tmp.get(&dist, (size_t)h->sumN));
+    GENEO_TRY(tmp.get(&total, (size_t)n));
+    k_sarkis_dist<<<N, kT, 0, s>>>(h->dsub, h->nToD, out.lrow, out.lcol, dist); note_launch();
+    k_sarkis_total<<<grid_for(n), kT, 0, s>>>(n, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub, h->dpos,
+                                              dist, total); note_launch();
+    k_sarkis_pu<<<N, kT, 0, s>>>(h->dsub, h->Nlist, h->nToD, dist, total, h->pu); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+  }
   // numeric assembly of Atilde_j, A_j^o, then B_j and K_j
   GENEO_TRY(tmp.get(&out.lK, (size_t)out.lnnz));
   GENEO_TRY(tmp.get(&out.lB, (size_t)out.lnnz));
   k_assemble<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, de_ptr, de, p->elem_dofs,
-                              p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB); note_launch();
+                              p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB,
+                              h->dstat); note_launch();
   k_pencil<<<N, kT, 0, s>>>(h->dsub, h->pu, out.lrow, out.lcol, out.lK, out.lB, h->opt.sigma,
                             h->opt.eig_form == GENEO_EIG_FULL); note_launch();
   GENEO_CUDA(cudaGetLastError());

@@ -90,7 +90,7 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
             if (!(dv > T(weak_tol))) weak[d.id] = 1;
             if (!finite_pos(dv)) dv = T(1);
           } else if (!finite_pos(dv)) {
-            record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)kb + t);
+            record_error(st, isfinite(dv) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id, (int64_t)kb + t);
             dv = T(1);
           }
           Dk[t * DS + t] = sqrt(dv);
@@ -228,7 +228,7 @@ k_band_panel(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb, D
       if (lane == t) {
         T dv = Dk[t * DS + t];
         if (!finite_pos(dv)) {
-          record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)kb + t);
+          record_error(st, isfinite(dv) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id, (int64_t)kb + t);
           dv = T(1);
         }
         Dk[t * DS + t] = sqrt(dv);
@@ -691,7 +691,7 @@ k_band_potrf_tc(float* __restrict__ base, const BandDesc* __restrict__ descs, De
             if (lane == 0 && !(p > weak_tol)) weak[d.id] = 1;
             if (!finite_pos(p)) p = 1.f;
           } else if (!finite_pos(p)) {
-            if (lane == 0) record_error(st, GENEO_ERR_NOT_SPD, d.id, (int64_t)j + t);
+            if (lane == 0) record_error(st, isfinite(p) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id, (int64_t)j + t);
             p = 1.f;
           }
           const float inv = rsqrtf(p);

@@ -61,6 +61,7 @@ struct geneo_handle_s {
   int eig_iters = 0;
   int eig_second_pass = 0;         // subdomains solved again with the full block
   int eig_o64 = 0;                 // FP32 mode: subdomains orthogonalised in FP64
+  int eig_unconv = 0;              // subdomains left unconverged at eig_maxit
 
   // apply / PCG work
   double* u = nullptr;             // [sumD] local solutions
@@ -77,6 +78,8 @@ struct geneo_handle_s {
   double local_solve_flops = 0, local_solve_bytes = 0, spmv_flops = 0, spmv_bytes = 0;
   double* hist = nullptr;          // PCG alpha/beta history (2 * hist_cap)
   int hist_cap = 0;
+  std::vector<double> pcg_host;    // host work of geneo_pcg_solve_noalloc (sized at setup)
+  int device = -1;                 // device the handle was set up on
 
   geneo::KernelProfiler prof;
 

@@ -1829,6 +1829,11 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   }
   GENEO_TRY(init_block(nullptr, o.seed));
   GENEO_TRY(iterate());
+  // subdomains the first pass left unconverged at eig_maxit
+  std::vector<int32_t> hdone1(N), unconv(N, 0);
+  GENEO_CUDA(cudaMemcpyAsync(hdone1.data(), done, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+  GENEO_CUDA(cudaStreamSynchronize(st));
+  for (int j = 0; j < N; ++j) unconv[j] = hdone1[j] ? 0 : 1;
   if (nev1 < nev) {
     std::vector<double> hnu1((size_t)N * s);
     GENEO_CUDA(cudaMemcpyAsync(hnu1.data(), nu, sizeof(double) * N * s, cudaMemcpyDeviceToHost, st));
@@ -1861,8 +1866,16 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       k_clear_p<<<ceil_div(N, 128), 128, 0, st>>>(spj, done, N); note_launch();
       GENEO_TRY(init_block(done, o.seed ^ 0x9E3779B97F4A7C15ull));
       GENEO_TRY(iterate());
+      // a redone subdomain counts by its second pass
+      std::vector<int32_t> hdone2(N);
+      GENEO_CUDA(cudaMemcpyAsync(hdone2.data(), done, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st));
+      GENEO_CUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j)
+        if (!redo[j]) unconv[j] = hdone2[j] ? 0 : 1;
     }
   }
+  h->eig_unconv = 0;
+  for (int j = 0; j < N; ++j) h->eig_unconv += unconv[j];
   const int it = total_it;
   h->eig_iters = it;
   h->eig_o64 = n64;

@@ -24,6 +24,9 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kRedBlocks = 1024;
+// allocation-free PCG: largest maxit accepted and scalar slots of its scratch
+constexpr int kNoAllocMaxIt = 4095;
+constexpr int kNoAllocScalars = 16;
 
 __global__ void __launch_bounds__(kT)
 k_restrict(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Dlist, const double* __restrict__ r,
@@ -141,7 +144,44 @@ __global__ void k_finish(const double* __restrict__ part, int nb, double* __rest
     hist_b[it] = scal[2];
   } else if (what == 4) {     // bb
     scal[5] = s;
+  } else if (what == 5) {     // ||b - A x||^2
+    scal[7] = s;
   }
+}
+
+// r = b - A x (the true residual, same row mapping and summation order as
+// k_spmv_dot); partial sums of r.r per block.
+__global__ void __launch_bounds__(kT)
+k_true_resid(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+             const double* __restrict__ val, const double* __restrict__ x, const double* __restrict__ b,
+             double* __restrict__ r, double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double rsum = 0.0;
+  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
+    const int64_t ra = r0 + g, rb = r0 + 4 + g;
+    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
+    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
+    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
+    double sa = 0.0, sb = 0.0;
+    while (ea < ea1 || eb < eb1) {
+      if (ea < ea1) { sa += val[ea] * x[col[ea]]; ea += 8; }
+      if (eb < eb1) { sb += val[eb] * x[col[eb]]; eb += 8; }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
+      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
+    }
+    if (sl == 0) {
+      if (ra < n) { const double v = b[ra] - sa; r[ra] = v; rsum += v * v; }
+      if (rb < n) { const double v = b[rb] - sb; r[rb] = v; rsum += v * v; }
+    }
+  }
+  rsum = block_sum(rsum, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = rsum;
 }
 
 __global__ void __launch_bounds__(kT)
@@ -170,43 +210,146 @@ __global__ void k_update_p(int64_t n, const double* __restrict__ scal, const dou
     p[i] = z[i] + beta * p[i];
 }
 
-// extreme eigenvalues of a symmetric tridiagonal matrix by bisection on the
-// Sturm sequence count
-double sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (q < 0) ++cnt;
-  for (size_t i = 1; i < d.size(); ++i) {
-    const double qq = (q == 0.0) ? 1e-300 : q;
-    q = d[i] - x - e[i - 1] * e[i - 1] / qq;
-    if (q < 0) ++cnt;
-  }
-  return cnt;
+// ---------------------------------------------------------------------------
+// PCG kernels of the non-deterministic mode (options.deterministic = 0): the
+// inner products are accumulated with atomic additions into the scalar
+// slots, and the scalar updates are folded into the kernels that use them,
+// so an iteration needs four launches besides the preconditioner instead of
+// seven.  Slots (parity p = iteration & 1): RZ[p] = 8 + p, PQ[p] = 10 + p,
+// RR[p] = 12 + p; flag 6 as in k_finish.
+// ---------------------------------------------------------------------------
+constexpr int kRZ = 8, kPQ = 10, kRR = 12;
+
+__device__ __forceinline__ void block_atomic_add(double v, double* dst, double* red) {
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) atomicAdd(dst, v);
 }
 
-double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, int k) {
-  double lo = 1e300, hi = -1e300;
-  for (size_t i = 0; i < d.size(); ++i) {
-    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < d.size() ? std::fabs(e[i]) : 0.0);
-    lo = std::min(lo, d[i] - r);
-    hi = std::max(hi, d[i] + r);
+// q = A p, PQ[par] += p.q; clears the other parity's slots for their next use
+__global__ void __launch_bounds__(kT)
+k_spmv_atomic(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+              const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
+              double* __restrict__ scal, int par) {
+  __shared__ double red[kT / 32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[kRZ + (par ^ 1)] = 0.0;
+    scal[kPQ + (par ^ 1)] = 0.0;
+    scal[kRR + (par ^ 1)] = 0.0;
   }
-  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_count(d, e, mid) > k) hi = mid; else lo = mid;
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double dsum = 0.0;
+  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
+    const int64_t ra = r0 + g, rb = r0 + 4 + g;
+    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
+    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
+    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
+    double sa = 0.0, sb = 0.0;
+    while (ea < ea1 || eb < eb1) {
+      if (ea < ea1) { sa += val[ea] * p[col[ea]]; ea += 8; }
+      if (eb < eb1) { sb += val[eb] * p[col[eb]]; eb += 8; }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
+      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
+    }
+    if (sl == 0) {
+      if (ra < n) { q[ra] = sa; dsum += sa * p[ra]; }
+      if (rb < n) { q[rb] = sb; dsum += sb * p[rb]; }
+    }
   }
-  return 0.5 * (lo + hi);
+  block_atomic_add(dsum, &scal[kPQ + par], red);
 }
 
-double condition_estimate(const std::vector<double>& a, const std::vector<double>& b, int m) {
+// alpha = RZ[par] / PQ[par]; x += alpha p, r -= alpha q, RR[par] += r.r
+__global__ void __launch_bounds__(kT)
+k_update_xr_atomic(int64_t n, double* __restrict__ scal, const double* __restrict__ p,
+                   const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                   double* __restrict__ hist_a, int it, int par) {
+  __shared__ double red[kT / 32];
+  const double pq = scal[kPQ + par];
+  const bool bad = !(pq > 0.0);
+  const double alpha = bad ? 0.0 : scal[kRZ + par] / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hist_a[it] = alpha;
+    if (bad) scal[6] = 1.0;
+  }
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  block_atomic_add(s, &scal[kRR + par], red);
+}
+
+// scal[slot] += a.b
+__global__ void __launch_bounds__(kT)
+k_dot_atomic(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ scal,
+             int slot) {
+  __shared__ double red[kT / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  block_atomic_add(s, &scal[slot], red);
+}
+
+// beta = RZ[par ^ 1] / RZ[par] (new over old); p = z + beta p
+__global__ void k_update_p_atomic(int64_t n, double* __restrict__ scal, const double* __restrict__ z,
+                                  double* __restrict__ p, double* __restrict__ hist_b, int it, int par) {
+  const double rz_new = scal[kRZ + (par ^ 1)], rz_old = scal[kRZ + par];
+  const double beta = rz_old > 0.0 ? rz_new / rz_old : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hist_b[it] = beta;
+    if (!(rz_new > 0.0)) scal[6] = 1.0;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// Condition estimate lambda_max / lambda_min of the Lanczos tridiagonal
+// matrix of the CG coefficients (alpha a[0..m), beta b[0..m-1)): both
+// extreme eigenvalues by bisection on the Sturm sequence count, in caller
+// storage d, e of m entries.
+double condition_estimate_fixed(const double* a, const double* b, int m, double* d, double* e) {
   if (m <= 0) return 1.0;
-  std::vector<double> d(m), e(std::max(m - 1, 0));
   for (int i = 0; i < m; ++i) {
     d[i] = 1.0 / a[i] + (i > 0 ? b[i - 1] / a[i - 1] : 0.0);
     if (i < m - 1) e[i] = std::sqrt(std::max(b[i], 0.0)) / a[i];
   }
-  const double lmin = tridiag_eig(d, e, 0), lmax = tridiag_eig(d, e, m - 1);
-  return lmax / lmin;
+  auto count = [&](double x) {
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      q = d[i] - x - e[i - 1] * e[i - 1] / (q == 0.0 ? 1e-300 : q);
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  double ext[2];
+  for (int which = 0; which < 2; ++which) {
+    const int k = which == 0 ? 0 : m - 1;
+    double l = lo, u = hi;
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (count(mid) > k) u = mid; else l = mid;
+    }
+    ext[which] = 0.5 * (l + u);
+  }
+  return ext[1] / ext[0];
 }
 
 }  // namespace
@@ -229,6 +372,9 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   GENEO_TRY(M.get(&h->xoffH, 1));
   GENEO_CUDA(cudaMemset(h->xoffH, 0, sizeof(int64_t)));
   if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
+  // host arrays of the allocation-free solve (Lanczos coefficients and the
+  // bisection work), sized once here so that solve never touches the heap
+  h->pcg_host.assign(4 * (size_t)(kNoAllocMaxIt + 1), 0.0);
   h->red_blocks = kRedBlocks;
   // algorithmic work of one apply
   // bytes per factor entry: 4 with FP32 factors, 8 for those factored in FP64
@@ -292,29 +438,37 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
   return GENEO_OK;
 }
 
-geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
-                   geneo_solve_info_t* info, cudaStream_t s) {
+// Buffers of one PCG solve: device reduction partials, scalars and the
+// alpha/beta history (cap entries each), and host arrays of cap entries for
+// the condition estimate.
+struct PcgBufs {
+  double *red, *scal, *da, *db;
+  int cap;
+  double *ha, *hb, *hd, *he;
+};
+
+// Preconditioned CG (Section 5), x0 = 0.  The recursive residual is tested
+// first; when it reaches tol the true residual b - A x is formed, and while
+// that is still above tol it replaces the recursive one and CG restarts from
+// x (p = M^{-1} r), at most kMaxReplace times and only while each
+// replacement at least halves the true residual (below that the rounding of
+// x in FP64 bounds what any iteration can reach).  The Lanczos estimate of
+// kappa(M^{-1} A) uses the coefficients before the first replacement.
+constexpr int kMaxReplace = 5;
+
+geneo_status_t pcg_core(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
+                        geneo_solve_info_t* info, cudaStream_t s, const PcgBufs& B) {
   const int64_t n = h->n;
-  const int nb = h->red_blocks;
-  const int gridv = nb;
-  std::vector<double> ha(std::max(maxit, 1) + 1), hb(std::max(maxit, 1) + 1);
-  if (h->hist_cap < (int)ha.size()) {
-    h->mem.stream = s;  // the handle's last stream (see geneo_destroy)
-    if (h->hist) h->mem.release(h->hist);
-    h->hist = nullptr;
-    GENEO_TRY(h->mem.get(&h->hist, 2 * ha.size()));
-    h->hist_cap = (int)ha.size();
-  }
-  double* da = h->hist;
-  double* db = h->hist + h->hist_cap;
-  // x = 0, r = b, ||b||
+  const int nb = kRedBlocks;
+  double* scal = B.scal;
+  double* red = B.red;
   GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   GENEO_CUDA(cudaMemcpyAsync(h->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  GENEO_CUDA(cudaMemsetAsync(h->scal, 0, sizeof(double) * 16, s));
-  k_dot<<<gridv, kT, 0, s>>>(n, b, b, h->red); note_launch();
-  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 4, da, db, 0); note_launch();
+  GENEO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 16, s));
+  k_dot<<<nb, kT, 0, s>>>(n, b, b, red); note_launch();
+  k_finish<<<1, kT, 0, s>>>(red, nb, scal, 4, B.da, B.db, 0); note_launch();
   GENEO_CUDA(cudaGetLastError());
-  GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
   GENEO_CUDA(cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(h->hpin[5]);
   int hist_len = 0;
@@ -322,67 +476,155 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
     if (info && info->resid_hist && hist_len < info->resid_hist_cap) info->resid_hist[hist_len] = v;
     ++hist_len;
   };
+  if (info) {
+    info->iterations = 0;
+    info->converged = 0;
+    info->rel_residual = NAN;
+    info->true_residual = NAN;
+    info->kappa_estimate = NAN;
+    info->replacements = 0;
+    info->resid_hist_len = 0;
+  }
+  if (!std::isfinite(bnorm)) return GENEO_ERR_NONFINITE;
   if (bnorm == 0.0) {
     if (info) {
-      info->iterations = 0;
       info->converged = 1;
       info->rel_residual = 0.0;
+      info->true_residual = 0.0;
       info->kappa_estimate = 1.0;
-      info->resid_hist_len = 0;
     }
     return GENEO_OK;
   }
   push_hist(1.0);
-  GENEO_TRY(apply_prec(h, h->r, h->zv, s));
-  GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red); note_launch();
-  k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 0, da, db, 0); note_launch();
-  GENEO_CUDA(cudaGetLastError());
+  const bool det = h->opt.deterministic != 0;
   int it = 0;
-  double rel = 1.0;
-  bool breakdown = false;
-  while (rel > tol && it < maxit) {
+  auto restart = [&]() -> geneo_status_t {  // p = z = M^{-1} r, rz = r.z
+    GENEO_TRY(apply_prec(h, h->r, h->zv, s));
+    GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (det) {
+      k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
+      k_finish<<<1, kT, 0, s>>>(red, nb, scal, 0, B.da, B.db, 0); note_launch();
+    } else {
+      GENEO_CUDA(cudaMemsetAsync(scal + kRZ, 0, sizeof(double) * 6, s));
+      k_dot_atomic<<<nb, kT, 0, s>>>(n, h->r, h->zv, scal, kRZ + (it & 1)); note_launch();
+    }
+    GENEO_CUDA(cudaGetLastError());
+    return GENEO_OK;
+  };
+  // true residual into zv (free between the update and the next apply)
+  auto true_residual = [&](double* out) -> geneo_status_t {
+    k_true_resid<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, x, b, h->zv, red); note_launch();
+    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 5, B.da, B.db, 0); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    *out = std::sqrt(h->hpin[7]) / bnorm;
+    return GENEO_OK;
+  };
+  GENEO_TRY(restart());
+  int replaced = 0, n_lanczos = -1;
+  double rel = 1.0, rel_true = NAN, last_true = INFINITY;
+  bool breakdown = false, converged = false, have_true = false, nonfinite = false;
+  while (it < maxit && it < B.cap - 1) {
+    const int par = it & 1;
     {
       const int pv = h->prof.begin(GENEO_PROF_SPMV, h->spmv_flops, h->spmv_bytes, s);
-      k_spmv_dot<<<gridv, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, h->red); note_launch();
+      if (det) {
+        k_spmv_dot<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, red); note_launch();
+      } else {
+        k_spmv_atomic<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, scal, par); note_launch();
+      }
       h->prof.end(pv, s);
     }
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 1, da, db, it); note_launch();
-    k_update_xr<<<gridv, kT, 0, s>>>(n, h->scal, h->p, h->q, x, h->r, h->red); note_launch();
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 2, da, db, it); note_launch();
+    if (det) {
+      k_finish<<<1, kT, 0, s>>>(red, nb, scal, 1, B.da, B.db, it); note_launch();
+      k_update_xr<<<nb, kT, 0, s>>>(n, scal, h->p, h->q, x, h->r, red); note_launch();
+      k_finish<<<1, kT, 0, s>>>(red, nb, scal, 2, B.da, B.db, it); note_launch();
+    } else {
+      k_update_xr_atomic<<<nb, kT, 0, s>>>(n, scal, h->p, h->q, x, h->r, B.da, it, par); note_launch();
+    }
     GENEO_CUDA(cudaGetLastError());
-    GENEO_CUDA(cudaMemcpyAsync(h->hpin, h->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
     GENEO_CUDA(cudaStreamSynchronize(s));
+    if (!det) h->hpin[3] = h->hpin[kRR + par];
     ++it;
+    have_true = false;
     if (h->hpin[6] != 0.0) {
       breakdown = true;
       break;
     }
     rel = std::sqrt(h->hpin[3]) / bnorm;
     push_hist(rel);
-    if (rel <= tol) break;
+    if (!std::isfinite(rel)) {
+      nonfinite = true;
+      break;
+    }
+    if (rel <= tol) {
+      GENEO_TRY(true_residual(&rel_true));
+      have_true = true;
+      if (rel_true <= tol) {
+        converged = true;
+        break;
+      }
+      if (replaced >= kMaxReplace || !(rel_true <= 0.5 * last_true)) break;
+      last_true = rel_true;
+      ++replaced;
+      if (n_lanczos < 0) n_lanczos = it;
+      GENEO_CUDA(cudaMemcpyAsync(h->r, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      GENEO_TRY(restart());
+      continue;
+    }
     GENEO_TRY(apply_prec(h, h->r, h->zv, s));
-    k_dot<<<gridv, kT, 0, s>>>(n, h->r, h->zv, h->red); note_launch();
-    k_finish<<<1, kT, 0, s>>>(h->red, nb, h->scal, 3, da, db, it - 1); note_launch();
-    k_update_p<<<gridv, kT, 0, s>>>(n, h->scal, h->zv, h->p); note_launch();
+    if (det) {
+      k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
+      k_finish<<<1, kT, 0, s>>>(red, nb, scal, 3, B.da, B.db, it - 1); note_launch();
+      k_update_p<<<nb, kT, 0, s>>>(n, scal, h->zv, h->p); note_launch();
+    } else {
+      k_dot_atomic<<<nb, kT, 0, s>>>(n, h->r, h->zv, scal, kRZ + (par ^ 1)); note_launch();
+      k_update_p_atomic<<<nb, kT, 0, s>>>(n, scal, h->zv, h->p, B.db, it - 1, par); note_launch();
+    }
     GENEO_CUDA(cudaGetLastError());
   }
-  GENEO_CUDA(cudaMemcpyAsync(ha.data(), da, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));
-  GENEO_CUDA(cudaMemcpyAsync(hb.data(), db, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
+  if (!have_true && !breakdown && !nonfinite) GENEO_TRY(true_residual(&rel_true));
+  int nalpha = n_lanczos >= 0 ? n_lanczos : (breakdown ? std::max(it - 1, 0) : it);
+  nalpha = std::min(nalpha, B.cap);
+  if (nalpha > 0) {
+    GENEO_CUDA(cudaMemcpyAsync(B.ha, B.da, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaMemcpyAsync(B.hb, B.db, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
+  }
   GENEO_CUDA(cudaStreamSynchronize(s));
-  const int nalpha = breakdown ? std::max(it - 1, 0) : it;
   if (info) {
     info->iterations = it;
-    info->converged = rel <= tol;
+    info->converged = converged;
     info->rel_residual = rel;
-    info->kappa_estimate = condition_estimate(ha, hb, nalpha);
+    info->true_residual = rel_true;
+    info->replacements = replaced;
+    info->kappa_estimate = condition_estimate_fixed(B.ha, B.hb, nalpha, B.hd, B.he);
     info->resid_hist_len = std::min(hist_len, info->resid_hist ? info->resid_hist_cap : 0);
   }
   GENEO_TRY(check_status(h, s));
-  h->prof.collect();
+  if (nonfinite || !std::isfinite(rel_true) && !breakdown) return GENEO_ERR_NONFINITE;
   if (breakdown) return GENEO_ERR_BREAKDOWN;
-  if (rel > tol) return GENEO_ERR_PCG_NOCONV;
+  if (!converged) return GENEO_ERR_PCG_NOCONV;
   return GENEO_OK;
+}
+
+geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
+                   geneo_solve_info_t* info, cudaStream_t s) {
+  const int cap = std::max(maxit, 1) + 1;
+  if (h->hist_cap < cap) {
+    h->mem.stream = s;  // the handle's last stream (see geneo_destroy)
+    if (h->hist) h->mem.release(h->hist);
+    h->hist = nullptr;
+    GENEO_TRY(h->mem.get(&h->hist, 2 * (size_t)cap));
+    h->hist_cap = cap;
+  }
+  std::vector<double> host(4 * (size_t)cap);
+  const PcgBufs B{h->red, h->scal, h->hist, h->hist + h->hist_cap, cap,
+                  host.data(), host.data() + cap, host.data() + 2 * cap, host.data() + 3 * cap};
+  geneo_status_t st = pcg_core(h, b, x, tol, maxit, info, s, B);
+  h->prof.collect();
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -398,8 +640,6 @@ geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, in
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kNoAllocMaxIt = 4095;                      // largest maxit accepted
-constexpr int kNoAllocScalars = 16;
 constexpr int kNoAllocDoubles = kRedBlocks + kNoAllocScalars + 2 * (kNoAllocMaxIt + 1);
 constexpr int kMaxDevices = 64;
 
@@ -422,131 +662,24 @@ geneo_status_t pcg_scratch(double** out) {
   return GENEO_OK;
 }
 
-// Extreme eigenvalues of the Lanczos tridiagonal matrix with caller storage.
-double condition_estimate_fixed(const double* a, const double* b, int m, double* d, double* e) {
-  if (m <= 0) return 1.0;
-  for (int i = 0; i < m; ++i) {
-    d[i] = 1.0 / a[i] + (i > 0 ? b[i - 1] / a[i - 1] : 0.0);
-    if (i < m - 1) e[i] = std::sqrt(std::max(b[i], 0.0)) / a[i];
-  }
-  auto count = [&](double x) {
-    int c = 0;
-    double q = d[0] - x;
-    if (q < 0) ++c;
-    for (int i = 1; i < m; ++i) {
-      q = d[i] - x - e[i - 1] * e[i - 1] / (q == 0.0 ? 1e-300 : q);
-      if (q < 0) ++c;
-    }
-    return c;
-  };
-  double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
-    lo = std::min(lo, d[i] - r);
-    hi = std::max(hi, d[i] + r);
-  }
-  double ext[2];
-  for (int which = 0; which < 2; ++which) {
-    const int k = which == 0 ? 0 : m - 1;
-    double l = lo, u = hi;
-    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
-      const double mid = 0.5 * (l + u);
-      if (count(mid) > k) u = mid; else l = mid;
-    }
-    ext[which] = 0.5 * (l + u);
-  }
-  return ext[1] / ext[0];
-}
-
-thread_local double t_hist[2][kNoAllocMaxIt + 1];
-thread_local double t_tri[2][kNoAllocMaxIt + 1];
 
 }  // namespace
 
 geneo_status_t pcg_noalloc(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
                            geneo_solve_info_t* info, cudaStream_t s) {
-  if (maxit > kNoAllocMaxIt) return GENEO_ERR_ARG;
+  if (maxit > kNoAllocMaxIt || h->prof.on) return GENEO_ERR_ARG;
+  int dev = -1;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) return GENEO_ERR_ARG;
+  if ((int)h->pcg_host.size() < 4 * (kNoAllocMaxIt + 1)) return GENEO_ERR_ARG;
   h->mem.stream = s;  // the handle's last stream (see geneo_destroy); no allocation
   double* scr = nullptr;
   GENEO_TRY(pcg_scratch(&scr));
-  const int64_t n = h->n;
-  const int nb = kRedBlocks;
-  double* red = scr;
-  double* scal = scr + kRedBlocks;
-  double* da = scal + kNoAllocScalars;
-  double* db = da + (kNoAllocMaxIt + 1);
-  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  GENEO_CUDA(cudaMemcpyAsync(h->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  GENEO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kNoAllocScalars, s));
-  k_dot<<<nb, kT, 0, s>>>(n, b, b, red); note_launch();
-  k_finish<<<1, kT, 0, s>>>(red, nb, scal, 4, da, db, 0); note_launch();
-  GENEO_CUDA(cudaGetLastError());
-  GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
-  GENEO_CUDA(cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(h->hpin[5]);
-  int hist_len = 0;
-  auto push_hist = [&](double v) {
-    if (info && info->resid_hist && hist_len < info->resid_hist_cap) info->resid_hist[hist_len] = v;
-    ++hist_len;
-  };
-  if (bnorm == 0.0) {
-    if (info) {
-      info->iterations = 0;
-      info->converged = 1;
-      info->rel_residual = 0.0;
-      info->kappa_estimate = 1.0;
-      info->resid_hist_len = 0;
-    }
-    return GENEO_OK;
-  }
-  push_hist(1.0);
-  GENEO_TRY(apply_prec(h, h->r, h->zv, s));
-  GENEO_CUDA(cudaMemcpyAsync(h->p, h->zv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
-  k_finish<<<1, kT, 0, s>>>(red, nb, scal, 0, da, db, 0); note_launch();
-  GENEO_CUDA(cudaGetLastError());
-  int it = 0;
-  double rel = 1.0;
-  bool breakdown = false;
-  while (rel > tol && it < maxit) {
-    k_spmv_dot<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, red); note_launch();
-    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 1, da, db, it); note_launch();
-    k_update_xr<<<nb, kT, 0, s>>>(n, scal, h->p, h->q, x, h->r, red); note_launch();
-    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 2, da, db, it); note_launch();
-    GENEO_CUDA(cudaGetLastError());
-    GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
-    GENEO_CUDA(cudaStreamSynchronize(s));
-    ++it;
-    if (h->hpin[6] != 0.0) {
-      breakdown = true;
-      break;
-    }
-    rel = std::sqrt(h->hpin[3]) / bnorm;
-    push_hist(rel);
-    if (rel <= tol) break;
-    GENEO_TRY(apply_prec(h, h->r, h->zv, s));
-    k_dot<<<nb, kT, 0, s>>>(n, h->r, h->zv, red); note_launch();
-    k_finish<<<1, kT, 0, s>>>(red, nb, scal, 3, da, db, it - 1); note_launch();
-    k_update_p<<<nb, kT, 0, s>>>(n, scal, h->zv, h->p); note_launch();
-    GENEO_CUDA(cudaGetLastError());
-  }
-  const int nalpha = breakdown ? std::max(it - 1, 0) : it;
-  if (nalpha > 0) {
-    GENEO_CUDA(cudaMemcpyAsync(t_hist[0], da, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
-    GENEO_CUDA(cudaMemcpyAsync(t_hist[1], db, sizeof(double) * nalpha, cudaMemcpyDeviceToHost, s));
-  }
-  GENEO_CUDA(cudaStreamSynchronize(s));
-  if (info) {
-    info->iterations = it;
-    info->converged = rel <= tol;
-    info->rel_residual = rel;
-    info->kappa_estimate = condition_estimate_fixed(t_hist[0], t_hist[1], nalpha, t_tri[0], t_tri[1]);
-    info->resid_hist_len = std::min(hist_len, info->resid_hist ? info->resid_hist_cap : 0);
-  }
-  GENEO_TRY(check_status(h, s));
-  if (breakdown) return GENEO_ERR_BREAKDOWN;
-  if (rel > tol) return GENEO_ERR_PCG_NOCONV;
-  return GENEO_OK;
+  constexpr int cap = kNoAllocMaxIt + 1;
+  double* hh = h->pcg_host.data();
+  const PcgBufs B{scr, scr + kRedBlocks, scr + kRedBlocks + kNoAllocScalars,
+                  scr + kRedBlocks + kNoAllocScalars + cap, cap, hh, hh + cap, hh + 2 * cap, hh + 3 * cap};
+  return pcg_core(h, b, x, tol, maxit, info, s, B);
 }
 
 }  // namespace geneo

@@ -22,6 +22,8 @@ GENEO_EIG_PAPER = 0
 GENEO_EIG_FULL = 1
 GENEO_PREC_FP64 = 0
 GENEO_PREC_FP32 = 1
+GENEO_PU_STANDARD = 0
+GENEO_PU_SARKIS = 1
 
 PROF_FAMILIES = ["factor", "eig_solve", "gram", "spmm", "gemm", "small_eig", "local_solve",
                  "coarse_solve", "spmv", "other", "ortho32"]
@@ -48,6 +50,7 @@ class geneo_problem_t(C.Structure):
         ("n_elem", C.c_int64), ("elem_ndof", C.c_int32), ("n_sub", C.c_int32),
         ("elem_dofs", C.c_void_p), ("elem_mats", C.c_void_p), ("sub_elem_ptr", C.c_void_p),
         ("sub_elem", C.c_void_p), ("sub_dof_ptr", C.c_void_p), ("sub_dof", C.c_void_p),
+        ("pu_weights", C.c_void_p),
     ]
 
 
@@ -57,7 +60,8 @@ class geneo_options_t(C.Structure):
         ("nev_max", C.c_int32), ("fixed_nev", C.c_int32), ("eig_form", C.c_int32),
         ("eig_maxit", C.c_int32), ("guard", C.c_int32), ("precision", C.c_int32),
         ("profile", C.c_int32), ("first_nev", C.c_int32), ("seed", C.c_uint64),
-        ("fp32_pivot_tol", C.c_double),
+        ("fp32_pivot_tol", C.c_double), ("pu_kind", C.c_int32), ("eig_strict", C.c_int32),
+        ("deterministic", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -66,6 +70,7 @@ class geneo_solve_info_t(C.Structure):
         ("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
         ("kappa_estimate", C.c_double), ("resid_hist", C.POINTER(C.c_double)),
         ("resid_hist_cap", C.c_int32), ("resid_hist_len", C.c_int32),
+        ("true_residual", C.c_double), ("replacements", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -74,7 +79,7 @@ class geneo_coarse_info_t(C.Structure):
         ("n_sub", C.c_int32), ("dim_coarse", C.c_int32), ("coarse_bandwidth", C.c_int32),
         ("eig_iterations", C.c_int32), ("block_size", C.c_int32),
         ("fp64_factors_K", C.c_int32), ("fp64_factors_A", C.c_int32), ("fp64_ortho", C.c_int32),
-        ("device_bytes", C.c_int64),
+        ("eig_unconverged", C.c_int32), ("reserved", C.c_int32), ("device_bytes", C.c_int64),
         ("setup_ms", C.c_double * 8), ("factor_flops", C.c_double), ("factor_event_ms", C.c_double),
         ("eigsolve_flops", C.c_double), ("eigsolve_event_ms", C.c_double),
         ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
@@ -195,8 +200,7 @@ def geneo_pcg_solve(h, b, x, nrhs=1, tol=1e-8, maxit=1000, mem=GENEO_MEM_DEVICE,
                                C.c_void_p(_stream(stream)))
     if raise_on_error:
         _check(code, "geneo_pcg_solve")
-    out = {"status": code, "iterations": info.iterations, "converged": bool(info.converged),
-           "rel_residual": info.rel_residual, "kappa_estimate": info.kappa_estimate}
+    out = _info_dict(code, info)
     if hist is not None:
         out["resid_hist"] = np.array(hist[:min(info.resid_hist_len, hist_cap)])
     return out
@@ -210,8 +214,13 @@ def geneo_pcg_solve_noalloc(h, b, x, tol=1e-8, maxit=1000, stream=None, raise_on
                                        C.c_void_p(_stream(stream)))
     if raise_on_error:
         _check(code, "geneo_pcg_solve_noalloc")
+    return _info_dict(code, info)
+
+
+def _info_dict(code, info):
     return {"status": code, "iterations": info.iterations, "converged": bool(info.converged),
-            "rel_residual": info.rel_residual, "kappa_estimate": info.kappa_estimate}
+            "rel_residual": info.rel_residual, "true_residual": info.true_residual,
+            "replacements": info.replacements, "kappa_estimate": info.kappa_estimate}
 
 
 def geneo_query(h):
@@ -221,7 +230,7 @@ def geneo_query(h):
     return {"n_sub": q.n_sub, "dim_coarse": q.dim_coarse, "coarse_bandwidth": q.coarse_bandwidth,
             "eig_iterations": q.eig_iterations, "block_size": q.block_size,
             "fp64_factors_K": q.fp64_factors_K, "fp64_factors_A": q.fp64_factors_A,
-            "fp64_ortho": q.fp64_ortho,
+            "fp64_ortho": q.fp64_ortho, "eig_unconverged": q.eig_unconverged,
             "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms),
             "factor_flops": q.factor_flops, "factor_event_ms": q.factor_event_ms,
             "eigsolve_flops": q.eigsolve_flops, "eigsolve_event_ms": q.eigsolve_event_ms,
@@ -318,16 +327,19 @@ def make_problem(arrays, n, n_sub, elem_ndof, ndof_node=1, mem=GENEO_MEM_DEVICE)
     for k in ("row_ptr", "col", "val", "dirichlet", "elem_dofs", "elem_mats", "sub_elem_ptr",
               "sub_elem", "sub_dof_ptr", "sub_dof"):
         setattr(p, k, _ptr(arrays[k]))
+    p.pu_weights = _ptr(arrays.get("pu_weights"))
     return p
 
 
 class GenEO:
     """Owns a handle; keeps the device copies of the inputs alive until close()."""
 
-    def __init__(self, prob, device_arrays=None, stream=None, **opts):
+    def __init__(self, prob, device_arrays=None, stream=None, pu_weights=None, **opts):
         import torch
         load_library()
         host = problem_arrays(prob)
+        if pu_weights is not None:
+            host["pu_weights"] = np.ascontiguousarray(pu_weights, dtype=np.float64)
         if device_arrays is None:
             device_arrays = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
         self.arrays = device_arrays

@@ -5,11 +5,11 @@ import scipy.sparse.linalg as spla
 import oracle
 
 
-def run_gpu(prob, **opts):
+def run_gpu(prob, pu_weights=None, **opts):
     """Set up the GPU preconditioner for prob and return (wrapper, torch)."""
     import torch
     from paper_1906_10944_gb300 import geneo as G
-    return G.GenEO(prob, **opts), torch
+    return G.GenEO(prob, pu_weights=pu_weights, **opts), torch
 
 
 def gpu_solve(sol, prob, tol=1e-8, maxit=2000):
@@ -34,9 +34,31 @@ def check_selection(lg_all, lo_all, m_gpu, m_or, tau, nev):
     return bool(np.any(np.abs(lo - tau) <= 1e-6 * tau))
 
 
-def compare_setup(prob, sol, orc, tau, nev, fixed=False):
-    """Per-subdomain parity of D_j, X_j, selected eigenvalues and coarse vectors."""
+def principal_angle(Zg, Zo, lam, m):
+    """Largest principal angle (radians) between the spans of the first m'
+    columns of Zg and Zo, m' <= m the largest count whose next eigenvalue is
+    separated by a relative gap above 1e-2 (a cluster split at m' leaves its
+    subspace undetermined); 0 when there is no such m'."""
+    mm = 0
+    for k in range(m, 0, -1):
+        nxt = lam[k] if k < lam.size else np.inf
+        if (nxt - lam[k - 1]) > 1e-2 * max(abs(nxt), 1e-3):
+            mm = k
+            break
+    if mm == 0:
+        return 0.0
+    qg, _ = np.linalg.qr(Zg[:, :mm])
+    qo, _ = np.linalg.qr(Zo[:, :mm])
+    s = np.linalg.svd(qo.T @ qg, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+def compare_setup(prob, sol, orc, tau, nev, fixed=False, stats=None):
+    """Per-subdomain parity of D_j, X_j, selected eigenvalues and coarse
+    vectors; stats (a dict) receives the largest relative eigenvalue error
+    and the largest principal angle between the coarse spaces."""
     worst_lam = 0.0
+    worst_angle = 0.0
     for j in range(prob.n_sub):
         g = sol.subdomain(j)
         s = orc.sets[j]
@@ -53,6 +75,9 @@ def compare_setup(prob, sol, orc, tau, nev, fixed=False):
                                                      np.maximum(np.abs(lo[:m]), 1e-3 * tau))))
             # coarse vectors: compare where the eigenvalue is well separated
             Zo = orc.Zloc[j][s["dpos"], :]
+            ang = principal_angle(g["Z"], Zo, lo, m)
+            assert ang <= 1e-4, (j, ang)
+            worst_angle = max(worst_angle, ang)
             for k in range(m):
                 gap = np.min(np.abs(np.delete(lo[:nev + 5], k) - lo[k])) / max(abs(lo[k]), 1e-3)
                 zg = g["Z"][:, k]
@@ -64,6 +89,9 @@ def compare_setup(prob, sol, orc, tau, nev, fixed=False):
                     # rule may pick either
                     err = min(np.linalg.norm(zg - Zo[:, k]), np.linalg.norm(zg + Zo[:, k]))
                     assert err < 1e-4, (j, k, err, gap)
+    if stats is not None:
+        stats["eig_rel_err"] = worst_lam
+        stats["coarse_angle"] = worst_angle
     return worst_lam
 
 

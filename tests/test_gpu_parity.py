@@ -6,12 +6,16 @@ the oracle; relative error <= 1e-7 against a direct solve, or the oracle's own
 error at the same tolerance times 10 when that is larger (the error a residual
 of 1e-8 implies depends on kappa(A)).
 
-Residuals: PCG stops when the recursive residual ||r_k|| / ||b|| (the one the
-iteration updates) reaches tol, so that is asserted <= tol.  The true residual
-||b - A x|| / ||b|| drifts from it by rounding in the recurrences; at contrast
-1e6 the oracle's own FP64 PCG on the 2D channel problem stops with a true /
-recursive ratio of 1.41, so the true residual is bounded by TRUE_RES_FACTOR *
-tol.
+Residuals: PCG (library and oracle alike) stops when the true residual
+||b - A x|| / ||b|| reaches tol (the recursive residual is tested first and
+replaced by the true one while that is above tol), so the library's reported
+true residual is asserted <= tol and the one recomputed here with scipy <=
+1.01 tol (the two FP64 evaluations differ in rounding).
+
+Every full check prints the worst relative eigenvalue error, the largest
+principal angle between the library's and the oracle's coarse spaces (per
+subdomain, over the selected vectors up to a separated eigenvalue), the
+solution error against a direct solve and the iteration counts.
 """
 import numpy as np
 import pytest
@@ -22,7 +26,20 @@ from gpu_helpers import compare_setup, gpu_solve, oracle_reference_solution, run
 
 pytestmark = pytest.mark.gpu
 
-TRUE_RES_FACTOR = 1.5
+
+
+def check_residual(prob, x, info, tol):
+    """True residual <= tol as the library evaluates it, and the scipy
+    recomputation within the rounding of an FP64 residual evaluation,
+    eps ||(|A| |x|)|| / ||b|| per evaluation (at contrast 1e6 that is a few
+    1e-9, the same order as the residual itself)."""
+    bn = np.linalg.norm(prob.b)
+    res = np.linalg.norm(prob.b - prob.A @ x) / bn
+    ev = np.finfo(np.float64).eps * np.linalg.norm(abs(prob.A) @ np.abs(x)) / bn
+    assert info["converged"] and info["true_residual"] <= tol, (info["rel_residual"], info["true_residual"])
+    assert res <= tol + 2 * ev and abs(info["true_residual"] - res) <= 2 * ev + 1e-3 * tol, \
+        (info["true_residual"], res, ev)
+    return res
 
 
 def _c1(contrast=1e6, seed=0):
@@ -30,26 +47,32 @@ def _c1(contrast=1e6, seed=0):
     return gen.darcy_problem((64, 64), k, (4, 4), 1)
 
 
-def _full_check(prob, tau=0.3, nev=10, fixed=False, form="paper", tol=1e-8):
+def _full_check(prob, tau=0.3, nev=10, fixed=False, form="paper", tol=1e-8, name="", precision=0,
+                pu=None, gpu_pu=None, iter_slack=0.0):
     orc = oracle.GenEOOracle(prob, oracle.OracleOptions(tau=tau, nev_max=nev, fixed_nev=fixed,
-                                                        eig_form=form))
+                                                        eig_form=form), pu=pu)
+    kw = {} if gpu_pu is None else gpu_pu
     sol, torch = run_gpu(prob, tau=tau, nev_max=nev, fixed_nev=int(fixed),
-                         eig_form=0 if form == "paper" else 1)
+                         eig_form=0 if form == "paper" else 1, precision=precision, **kw)
     try:
         q = sol.query()
-        compare_setup(prob, sol, orc, tau, nev, fixed)
+        stats = {}
+        compare_setup(prob, sol, orc, tau, nev, fixed, stats=stats)
         assert q["dim_coarse"] == orc.dim_H or not fixed
         x, info = gpu_solve(sol, prob, tol=tol)
         xo, ito, _, kapo = orc.solve(tol=tol)
         xs = oracle_reference_solution(prob)
-        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and info["rel_residual"] <= tol and res <= TRUE_RES_FACTOR * tol, \
-            (info["rel_residual"], res)
-        assert abs(info["iterations"] - ito) <= 2, (info["iterations"], ito)
+        res = check_residual(prob, x, info, tol)
+        assert abs(info["iterations"] - ito) <= 2 + iter_slack * ito, (info["iterations"], ito)
         err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
         err_o = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
         assert err <= max(1e-7, 10 * err_o), (err, err_o)
-        assert abs(info["kappa_estimate"] - kapo) <= 0.05 * kapo
+        # FP32 local solves change M^{-1} slightly
+        assert abs(info["kappa_estimate"] - kapo) <= (0.05 if precision == 0 else 0.15) * kapo
+        print("PARITY %s prec=%d: eig rel err %.2e, coarse angle %.2e rad, solution err %.2e "
+              "(oracle %.2e), true residual %.2e, iterations %d (oracle %d), kappa %.3f (oracle %.3f)"
+              % (name, precision, stats["eig_rel_err"], stats["coarse_angle"], err, err_o, res,
+                 info["iterations"], ito, info["kappa_estimate"], kapo))
         return sol, orc, info
     finally:
         sol.close()
@@ -57,15 +80,15 @@ def _full_check(prob, tau=0.3, nev=10, fixed=False, form="paper", tol=1e-8):
 
 def test_c1_darcy_2d_high_contrast():
     """2D Darcy 64x64, 4x4 subdomains, overlap 1, channels at contrast 1e6."""
-    _full_check(_c1())
+    _full_check(_c1(), name="c1")
 
 
 def test_c1_full_eigen_form():
-    _full_check(_c1(), form="full")
+    _full_check(_c1(), form="full", name="c1-full-form")
 
 
 def test_fixed_nev_mode():
-    _full_check(_c1(contrast=1e4, seed=3), nev=4, fixed=True)
+    _full_check(_c1(contrast=1e4, seed=3), nev=4, fixed=True, name="c1-fixed-nev")
 
 
 def test_one_level_apply_exact():
@@ -113,14 +136,110 @@ def test_darcy_3d_ragged():
     kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
                                   slab_z=(30, 80), slab_thickness=1)
     prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
-    _full_check(prob, nev=8)
+    _full_check(prob, nev=8, name="darcy3d-ragged")
 
 
 def test_elasticity_3d_small():
     """3D laminate elasticity (3 dofs per node), floating subdomains carry six
     rigid-body modes."""
     prob = gen.elasticity_problem((12, 6, 6), (3, 1, 1), 1, layer_thickness=1)
-    _full_check(prob, nev=10)
+    _full_check(prob, nev=10, name="elasticity")
+
+
+def test_elasticity_3d_mixed_precision():
+    """The laminate elasticity case with FP32 factors (the precision its full
+    size configuration runs in): FP64 eigenvalue bar, the same coarse space
+    (principal angles), the true residual at tol, iterations within 10 % + 2."""
+    prob = gen.elasticity_problem((12, 6, 6), (3, 1, 1), 1, layer_thickness=1)
+    _full_check(prob, nev=10, name="elasticity", precision=1, iter_slack=0.1)
+
+
+def test_darcy_3d_ragged_mixed_precision():
+    nel = (18, 14, 12)
+    kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
+                                  slab_z=(30, 80), slab_thickness=1)
+    prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
+    _full_check(prob, nev=8, name="darcy3d-ragged", precision=1, iter_slack=0.1)
+
+
+def test_c1_mixed_precision():
+    """FP32 factors (local solves and the eigensolver's shift-invert operator)
+    with FP64 residuals, Rayleigh-Ritz, coarse problem and PCG."""
+    _full_check(_c1(), name="c1", precision=1, iter_slack=0.1)
+
+
+def _random_pu(prob, seed):
+    """Caller weights of Definition 3 that are not the standard ones: random
+    positive weights on each D_j, normalised to sum to one per dof, zero on
+    the inner boundary (a test input)."""
+    sets = oracle.subdomain_sets(prob)
+    rng = np.random.default_rng(seed)
+    raw = [np.zeros(s["N"].size) for s in sets]
+    tot = np.zeros(prob.n)
+    for s, w in zip(sets, raw):
+        w[s["dpos"]] = rng.uniform(0.2, 1.0, s["dpos"].size)
+        tot[s["D"]] += w[s["dpos"]]
+    for s, w in zip(sets, raw):
+        w[s["dpos"]] /= tot[s["D"]]
+    return raw
+
+
+def test_caller_standard_weights_bitwise():
+    """Passing the standard partition of unity as caller weights gives
+    bitwise the same eigenvalues, coarse space and solution as passing none."""
+    prob = _c1()
+    orc_sets = oracle.subdomain_sets(prob)
+    _, xs = oracle.partition_of_unity(prob, orc_sets)
+    outs = []
+    for w in (None, np.concatenate(xs)):
+        sol, _ = run_gpu(prob, nev_max=10, pu_weights=w)
+        try:
+            x, info = gpu_solve(sol, prob)
+            subs = [sol.subdomain(j) for j in range(prob.n_sub)]
+            outs.append((x, np.concatenate([g["lambda"] for g in subs]),
+                         np.concatenate([g["Z"].ravel() for g in subs]), info["iterations"]))
+        finally:
+            sol.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_caller_random_weights_match_oracle():
+    """Non-standard caller weights: the library matches the oracle run with
+    the same weights (eigenvalues, coarse space, PCG)."""
+    prob = _c1(contrast=1e4, seed=2)
+    w = _random_pu(prob, 7)
+    _full_check(prob, name="c1-random-pu", pu=w, gpu_pu={"pu_weights": np.concatenate(w)})
+
+
+def test_caller_weights_rejected():
+    """Weights that do not sum to one, or that are non-zero on the inner
+    boundary, are rejected with GENEO_ERR_ARG."""
+    from paper_1906_10944_gb300 import geneo as G
+    prob = _c1()
+    sets = oracle.subdomain_sets(prob)
+    _, xs = oracle.partition_of_unity(prob, sets)
+    bad1 = np.concatenate(xs) * 1.001
+    bad2 = [x.copy() for x in xs]
+    inner = np.setdiff1d(np.arange(sets[5]["N"].size), sets[5]["dpos"])
+    bad2[5][inner[0]] = 0.5
+    for w in (bad1, np.concatenate(bad2)):
+        with pytest.raises(G.GenEOError) as e:
+            G.GenEO(prob, pu_weights=w, nev_max=10)
+        assert e.value.code == 1
+
+
+def test_sarkis_partition_of_unity_matches_oracle():
+    """The smooth (Sarkis) partition of unity computed on the device equals
+    the oracle's bit for bit (integer layer distances, one division), and the
+    GenEO setup and solve built on it match the oracle's."""
+    prob = gen.darcy_problem((64, 64), gen.kappa_channels_2d((64, 64), seed=0), (4, 4), 2)
+    _full_check(prob, name="c1-overlap2-sarkis", pu="sarkis", gpu_pu={"pu_kind": 1})
+
+
+def test_sarkis_3d_elasticity():
+    prob = gen.elasticity_problem((12, 6, 6), (3, 1, 1), 2, layer_thickness=1)
+    _full_check(prob, nev=10, name="elasticity-sarkis", pu="sarkis", gpu_pu={"pu_kind": 1})
 
 
 def test_single_subdomain_is_direct_solve():
@@ -131,7 +250,7 @@ def test_single_subdomain_is_direct_solve():
     try:
         assert sol.query()["dim_coarse"] == 0
         x, info = gpu_solve(sol, prob)
-        assert info["iterations"] <= 1
+        assert info["iterations"] <= 1 and info["converged"]
         xs = oracle_reference_solution(prob)
         assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
     finally:
@@ -165,45 +284,9 @@ def test_host_memory_path():
     try:
         x = np.zeros(prob.n)
         info = G.geneo_pcg_solve(h, np.ascontiguousarray(prob.b), x, tol=1e-8, mem=G.GENEO_MEM_HOST)
-        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
-            (info["rel_residual"], res, info["iterations"])
+        check_residual(prob, x, info, 1e-8)
     finally:
         G.geneo_destroy(h)
-
-
-@pytest.mark.parametrize("case", ["c1", "3d"])
-def test_mixed_precision_matches_oracle(case):
-    """FP32 factors (local solves and the eigensolver's shift-invert operator)
-    with FP64 residuals, Rayleigh-Ritz, coarse problem and PCG: eigenvalues
-    still meet the FP64 tolerance (the eigensolver's residuals are FP64), the
-    solve reaches relative residual 1e-8, and the PCG iteration count stays
-    within 10 % (+2) of the oracle's."""
-    if case == "c1":
-        prob = _c1()
-        nev = 10
-    else:
-        nel = (18, 14, 12)
-        kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
-                                      slab_z=(30, 80), slab_thickness=1)
-        prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
-        nev = 8
-    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=nev))
-    sol, _ = run_gpu(prob, nev_max=nev, precision=1)
-    try:
-        for j in range(prob.n_sub):
-            g = sol.subdomain(j)
-            m = min(g["m"], orc.ms[j])
-            lo = orc.lams[j][:m]
-            assert np.all(np.abs(g["lambda"][:m] - lo) <= 1e-6 * np.maximum(np.abs(lo), 3e-4)), j
-        x, info = gpu_solve(sol, prob)
-        _, ito, _, _ = orc.solve(tol=1e-8)
-        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
-            (info["rel_residual"], res, info["iterations"])
-        assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
-    finally:
-        sol.close()
 
 
 def test_uneven_batch_darcy_3d():
@@ -245,9 +328,7 @@ def test_mixed_precision_fp64_refactor(pivot_tol):
             assert np.all(np.abs(g["lambda"][:m] - lo) <= 1e-6 * np.maximum(np.abs(lo), 3e-4)), j
         x, info = gpu_solve(sol, prob)
         _, ito, _, _ = orc.solve(tol=1e-8)
-        res = np.linalg.norm(prob.b - prob.A @ x) / np.linalg.norm(prob.b)
-        assert info["converged"] and info["rel_residual"] <= 1e-8 and res <= TRUE_RES_FACTOR * 1e-8, \
-            (info["rel_residual"], res, info["iterations"])
+        check_residual(prob, x, info, 1e-8)
         assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
     finally:
         sol.close()
