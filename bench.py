@@ -474,6 +474,8 @@ def main():
                     help="PCG iterations the reference arm extrapolates to (default: the "
                          "oracle's own count from tests/golden, else a fixed estimate)")
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--eig-solve-tf32", type=int, default=0,
+                    help="mixed path: eigensolver block solves in one TF32 pass (1) or three (0)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--serve-requests", type=int, default=150)
     args = ap.parse_args()
@@ -525,7 +527,8 @@ def main():
 
     def options(precision, profile=0):
         prec = G.GENEO_PREC_FP32 if precision == "mixed" else G.GENEO_PREC_FP64
-        return G.geneo_default_options(nev_max=w["nev"], tau=w["tau"], precision=prec, profile=profile)
+        return G.geneo_default_options(nev_max=w["nev"], tau=w["tau"], precision=prec, profile=profile,
+                                       eig_solve_tf32=int(args.eig_solve_tf32 and precision == "mixed"))
 
     def step(opts):
         h = G.geneo_setup(problem, opts, stream)

@@ -170,6 +170,8 @@ void geneo_default_options(geneo_options_t* o) {
   o->pu_kind = GENEO_PU_STANDARD;
   o->eig_strict = 0;
   o->deterministic = 1;
+  o->eig_solve_tf32 = 0;
+  o->factor_kernel = 0;
   o->reserved = 0;
 }
 
@@ -191,7 +193,9 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
       (o.eig_form != GENEO_EIG_PAPER && o.eig_form != GENEO_EIG_FULL) ||
       (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32) ||
       (o.pu_kind != GENEO_PU_STANDARD && o.pu_kind != GENEO_PU_SARKIS) ||
-      (o.eig_strict != 0 && o.eig_strict != 1) || (o.deterministic != 0 && o.deterministic != 1))
+      (o.eig_strict != 0 && o.eig_strict != 1) || (o.deterministic != 0 && o.deterministic != 1) ||
+      (o.eig_solve_tf32 != 0 && o.eig_solve_tf32 != 1) || (o.factor_kernel != 0 && o.factor_kernel != 1) ||
+      o.reserved != 0)
     return GENEO_ERR_ARG;
   // keep freed device memory in the stream-ordered pool for the next setup
   {

@@ -715,6 +715,13 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   auto t1 = std::chrono::steady_clock::now();
   EventTimer ev;
   ev.start(s);
+  // FP32 factors: tiled-band planes for the fifth-generation tensor-core
+  // factorisation, allocated on the main stream before the fork
+  Tc5Plan planK, planA;
+  if (h->fp32 && h->opt.factor_kernel != 1) {
+    GENEO_TRY(tc5_prepare(bkf.data(), N, out.maxwK, tmp, s, &planK));
+    GENEO_TRY(tc5_prepare(baf.data(), N, h->maxwA, tmp, s, &planA));
+  }
   // K_j on the main stream, A_j concurrently on the auxiliary stream
   GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
   GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
@@ -732,9 +739,9 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     // failing the setup
     const float wt = (float)h->opt.fp32_pivot_tol;
     GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s, equil,
-                                out.weak, wt));
+                                out.weak, wt, &planK));
     GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux, equil,
-                                out.weak + N, wt));
+                                out.weak + N, wt, &planA));
   } else {
     GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
     GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));

@@ -22,6 +22,7 @@
 // updated in the shared ring); diagonal blocks are solved by warp shuffles.
 // The factor is read once per sweep; b and x once each.
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace geneo {
 
@@ -410,51 +411,6 @@ k_band_dinv(T* __restrict__ base, const BandDesc* __restrict__ descs) {
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-copy pipeline helpers (cp.async.bulk + mbarrier, sm_90 and later).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~2^22 polls (seconds), reports
-// GENEO_ERR_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, DevStatus* st, int id,
-                                                  int64_t where) {
-  for (int it = 0; it < (1 << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  record_error(st, GENEO_ERR_TIMEOUT, id, where);
-  return false;
-}
-
-// ---------------------------------------------------------------------------
 // Left-looking FP32 band Cholesky on the tensor cores.
 //
 // Panel j (columns j .. j+b-1, b <= 32) of the rows r in [j, j + R),
@@ -491,9 +447,6 @@ __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint
       "{%0,%1,%2,%3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 constexpr int kPB = 32;   // panel width of the tensor-core factorisation
@@ -1344,7 +1297,7 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
 template <int NT>
 struct MtcKP { static constexpr int v = NT == 1 ? 8 : (NT == 4 ? 40 : 24); };
 
-template <int NT, int kStages>
+template <int NT, int kStages, int PASSES>
 __global__ void __launch_bounds__(kThreads, 1)
 k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ descs,
                  double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
@@ -1485,8 +1438,10 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
             uint32_t bh[2], bl[2];
             split_tf32(r1[8 * nt], bh[0], bl[0]);
             split_tf32(r2[8 * nt], bh[1], bl[1]);
-            mma_tf32(acc[nt][0], al, bh);
-            mma_tf32(acc[nt][1], ah, bl);
+            if (PASSES == 3) {
+              mma_tf32(acc[nt][0], al, bh);
+              mma_tf32(acc[nt][1], ah, bl);
+            }
             mma_tf32(acc[nt][2], ah, bh);
           }
         }
@@ -1585,8 +1540,10 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
             for (int q = 0; q < 4; ++q) split_tf32(x[q], ah[q], al[q]);
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-              mma_tf32(cacc[nt], al, bh[h][nt]);
-              mma_tf32(cacc[nt], ah, bl[h][nt]);
+              if (PASSES == 3) {
+                mma_tf32(cacc[nt], al, bh[h][nt]);
+                mma_tf32(cacc[nt], ah, bl[h][nt]);
+              }
               mma_tf32(cacc[nt], ah, bh[h][nt]);
             }
           }
@@ -1625,12 +1582,25 @@ inline int next_pow2(int v) {
 
 template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
-                          DevStatus* st, cudaStream_t s, bool equil, int32_t* weak, float weak_tol) {
+                          DevStatus* st, cudaStream_t s, bool equil, int32_t* weak, float weak_tol,
+                          const Tc5Plan* tc5) {
   if (count <= 0) return GENEO_OK;
   if (equil && max_n > 0) {
     k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
     k_band_equil_a<T><<<dim3((max_n + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
     GENEO_CUDA(cudaGetLastError());
+  }
+  // FP32: fifth-generation tensor cores (tcgen05, TMA) when the batch fits
+  if constexpr (sizeof(T) == 4) {
+    if (tc5 && tc5->ok) {
+      GENEO_TRY(tc5_factor(*tc5, base, d_desc, st, s, weak, weak_tol));
+      if (max_n > 0) {
+        const int nb = (max_n + 15) / 16;
+        k_band_dinv<T><<<dim3((nb + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
+        GENEO_CUDA(cudaGetLastError());
+      }
+      return GENEO_OK;
+    }
   }
   // FP32: left-looking tensor-core kernel when a panel's rows and two chunk
   // buffers fit in shared memory
@@ -1740,11 +1710,11 @@ inline size_t mtc_smem(int max_w, int ring, int NT, int stages) {
                                 (size_t)(kThreads / 32 + 1) * 16 * KP);
 }
 
-template <int NT, int kStages>
+template <int NT, int kStages, int PASSES>
 geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float* base, const BandDesc* d_desc,
                             double* xbase, const int64_t* xoff, int c0, int kc,
                             const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
-  auto kern = k_band_solve_mtc<NT, kStages>;
+  auto kern = k_band_solve_mtc<NT, kStages, PASSES>;
   GENEO_CUDA(allow_smem(kern));
   kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
@@ -1752,13 +1722,16 @@ geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float*
   return GENEO_OK;
 }
 
-geneo_status_t launch_mtc(int NT, int stages, int count, size_t smem, cudaStream_t s, const float* base,
-                          const BandDesc* d_desc, double* xbase, const int64_t* xoff, int c0, int kc,
-                          const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
-#define GENEO_MTC(nt, sg)                                                                          \
-  if (NT == nt && stages == sg)                                                                    \
-    return launch_mtc_t<nt, sg>(count, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, \
-                                ring, st);
+geneo_status_t launch_mtc(int NT, int stages, int passes, int count, size_t smem, cudaStream_t s,
+                          const float* base, const BandDesc* d_desc, double* xbase, const int64_t* xoff,
+                          int c0, int kc, const int32_t* nrhs_dev, const int32_t* skip_dev, int ring,
+                          DevStatus* st) {
+#define GENEO_MTC(nt, sg)                                                                              \
+  if (NT == nt && stages == sg)                                                                        \
+    return passes == 1 ? launch_mtc_t<nt, sg, 1>(count, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
+                                                 nrhs_dev, skip_dev, ring, st)                         \
+                       : launch_mtc_t<nt, sg, 3>(count, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
+                                                 nrhs_dev, skip_dev, ring, st);
   GENEO_MTC(1, 2) GENEO_MTC(1, 3) GENEO_MTC(1, 4) GENEO_MTC(2, 2) GENEO_MTC(2, 3) GENEO_MTC(2, 4)
   GENEO_MTC(3, 2) GENEO_MTC(3, 3) GENEO_MTC(3, 4) GENEO_MTC(4, 2) GENEO_MTC(4, 3) GENEO_MTC(4, 4)
 #undef GENEO_MTC
@@ -1830,7 +1803,7 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n) {
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
   // One right-hand side (the preconditioner's local solves): two stages and
   // one register slot per warp keep the block small enough for several
@@ -1866,8 +1839,8 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
         const int kk = std::min(kc, 8 * NT);
         int stages = 4;
         while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > 227 * 1024) --stages;
-        GENEO_TRY(launch_mtc(NT, stages, count, mtc_smem(max_w, ring, NT, stages), s, base, d_desc, xbase,
-                             xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
+        GENEO_TRY(launch_mtc(NT, stages, tc_passes, count, mtc_smem(max_w, ring, NT, stages), s, base,
+                             d_desc, xbase, xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
         if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch
       }
       return GENEO_OK;
@@ -1890,14 +1863,14 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
 }
 
 template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, int, DevStatus*,
-                                           cudaStream_t, bool, int32_t*, float);
+                                           cudaStream_t, bool, int32_t*, float, const Tc5Plan*);
 template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, int, DevStatus*,
-                                          cudaStream_t, bool, int32_t*, float);
+                                          cudaStream_t, bool, int32_t*, float, const Tc5Plan*);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
-                                           DevStatus*, cudaStream_t, int);
+                                           DevStatus*, cudaStream_t, int, int);
 template geneo_status_t band_solve<float>(const float*, const BandDesc*, int, int, double*,
                                           const int64_t*, int, const int32_t*, const int32_t*,
-                                          DevStatus*, cudaStream_t, int);
+                                          DevStatus*, cudaStream_t, int, int);
 
 }  // namespace geneo

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libgeneo.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -281,16 +282,39 @@ inline cudaError_t allow_smem(K kern) {
 geneo_status_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
                                   DevMem& tmp, cudaStream_t st);
 
+// band_tc5.cu: FP32 band Cholesky on the fifth-generation tensor cores.
+// tc5_prepare allocates the tiled-band planes of a batch (host descriptors in
+// batch order) and their tensor maps on stream s; p->ok stays false when the
+// batch does not fit the kernel (the older kernels then factor it).
+// tc5_factor (after equilibration) packs the bands, factors them and unpacks
+// the factors back into the bands.
+struct Tc5Plan {
+  CUtensorMap mhi, mlo;
+  bool ok = false;
+  int W = 0, count = 0, max_n = 0;
+  uint32_t cols = 0;
+  size_t smem = 0;
+  float* phi = nullptr;
+  float* plo = nullptr;
+  int64_t* dz = nullptr;
+};
+geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
+                           Tc5Plan* p);
+geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc, DevStatus* st, cudaStream_t s,
+                          int32_t* weak, float weak_tol);
+
 // band.cu
 // Batched Cholesky.  equil: factor S A S (s = diag^{-1/2}) and keep s.
 // weak (may be NULL): instead of reporting GENEO_ERR_NOT_SPD, matrix d sets
 // weak[d.id] = 1 when one of its pivots is not above weak_tol (relative to
 // the unit diagonal of an equilibrated band); the caller factors those
 // matrices again in FP64.
+// tc5 (FP32, may be NULL): a prepared plan sends the factorisation to the
+// fifth-generation tensor-core kernel.
 template <typename T>
 geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w, int max_n,
                           DevStatus* st, cudaStream_t s, bool equil = false,
-                          int32_t* weak = nullptr, float weak_tol = 0.f);
+                          int32_t* weak = nullptr, float weak_tol = 0.f, const Tc5Plan* tc5 = nullptr);
 // Solve L L^T X = X in place for `nrhs` columns per matrix (column-major,
 // leading dimension = matrix n, column stride = n); X for matrix i (i = the
 // descriptor's id when >= 0, else its batch position) starts at
@@ -298,10 +322,13 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
 // capped by nrhs; skip_dev (may be NULL) skips matrices with a non-zero flag;
 // a descriptor with n = 0 is skipped.
 // max_n (largest matrix order, 0 if unknown) enables the one-right-hand-side
-// solve with the vector resident in shared memory.
+// solve with the vector resident in shared memory.  tc_passes (FP32 factors,
+// several right-hand sides): 3 = each tensor-core product as three TF32
+// passes (about FP32 accuracy), 1 = one TF32 pass.
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0);
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0,
+                          int tc_passes = 3);
 
 }  // namespace geneo

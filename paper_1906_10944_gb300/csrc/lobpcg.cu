@@ -1431,7 +1431,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
                         int kmax) -> geneo_status_t {
     if (f32) {
       GENEO_TRY(band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
-                                  ncols, skip, h->dstat, st, maxn));
+                                  ncols, skip, h->dstat, st, maxn, o.eig_solve_tf32 ? 1 : 3));
       if (asmb.nK64)  // the K_j factored in FP64 (their FP32 descriptors have n = 0)
         GENEO_TRY(band_solve<double>(asmb.bandK64, asmb.dbandK64, asmb.nK64, asmb.maxwK64, S, xoff, kmax,
                                      ncols, skip, h->dstat, st, asmb.maxnK64));

@@ -61,7 +61,8 @@ class geneo_options_t(C.Structure):
         ("eig_maxit", C.c_int32), ("guard", C.c_int32), ("precision", C.c_int32),
         ("profile", C.c_int32), ("first_nev", C.c_int32), ("seed", C.c_uint64),
         ("fp32_pivot_tol", C.c_double), ("pu_kind", C.c_int32), ("eig_strict", C.c_int32),
-        ("deterministic", C.c_int32), ("reserved", C.c_int32),
+        ("deterministic", C.c_int32), ("eig_solve_tf32", C.c_int32),
+        ("factor_kernel", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
