@@ -402,57 +402,79 @@ def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
             "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
 
 
-# serving trace: seeded Darcy problems of mixed size (16^3-element subdomains,
-# overlap 2, nev <= 20, FP32 factors), 1..4 right-hand sides per request
-SERVE_SIZES = [(32, 32, 32), (48, 48, 48), (64, 64, 64)]
-SERVE_SEEDS = (11, 12)
-SERVE_WORKERS = 3
-SERVE_LOAD = 0.6
+# Serving trace: Poisson arrivals (mean 20 requests/s) over a set of seeded
+# problems, half 3D Darcy (n^3 elements, n in SERVE_DARCY, 16^3-element boxes,
+# overlap 2, nev <= 20) and half laminate elasticity (n^3, n in SERVE_ELAST,
+# boxes of about 12^3 elements, overlap 2, nev <= 30), SERVE_SAMPLES
+# coefficient samples of each size; FP32 factors.  Handles stay resident
+# between requests (admission by device-memory footprint, budget 180 GB);
+# each request solves 1-8 right-hand sides in one library call.
+SERVE_DARCY = (32, 48, 64, 96, 128)
+SERVE_ELAST = (24, 32, 48, 64)
+SERVE_SAMPLES = 2
+SERVE_RATE = 20.0
+SERVE_WORKERS = 4
+SERVE_BUDGET = 180e9
+
+
+def serve_problems():
+    """(name, problem) of the serving trace: host arrays, seeded."""
+    import gen
+    out = []
+    for smp in range(SERVE_SAMPLES):
+        for n in SERVE_DARCY:
+            kap = gen.kappa_grf_layers_3d((n, n, n), seed=100 + 10 * smp + n)
+            out.append(("darcy%d-s%d" % (n, smp), gen.darcy_problem((n, n, n), kap, (n // 16,) * 3, 2), 20))
+        for n in SERVE_ELAST:
+            parts = (max(1, round(n / 12)),) * 3
+            out.append(("elast%d-s%d" % (n, smp),
+                        gen.elasticity_problem((n, n, n), parts, 2, layer_thickness=2, seed=200 + 10 * smp + n),
+                        30))
+    return out
 
 
 def serve_measure(n_requests, warmup, tol):
-    """p50/p99 latency of a Poisson request trace at SERVE_LOAD of the
-    estimated capacity of SERVE_WORKERS concurrent streams."""
+    """p50/p99 latency and solves/s of the serving trace (see above)."""
     import numpy as np
     import torch
-    import gen
     from paper_1906_10944_gb300 import geneo as G
     from paper_1906_10944_gb300 import serve as S
-    problems, rhs, keep, sizes = [], [], [], []
-    for nel in SERVE_SIZES:
-        for seed in SERVE_SEEDS:
-            kap = gen.kappa_grf_layers_3d(nel, seed=seed)
-            prob = gen.darcy_problem(nel, kap, tuple(e // 16 for e in nel), 2)
-            dev = {k: torch.from_numpy(v).cuda() for k, v in G.problem_arrays(prob).items()}
-            keep.append(dev)
-            opts = G.geneo_default_options(nev_max=20, tau=0.3, precision=G.GENEO_PREC_FP32)
-            problems.append((G.make_problem(dev, prob.n, prob.n_sub, 8, 1, G.GENEO_MEM_DEVICE), opts, prob.n))
-            rng = np.random.default_rng(1000 + len(rhs))
-            b = rng.uniform(-1.0, 1.0, (4, prob.n))
-            b[:, prob.dirichlet != 0] = 0.0
-            rhs.append(torch.from_numpy(b.reshape(-1)).cuda())
-            sizes.append(prob.n)
+    t_gen = time.perf_counter()
+    probs = serve_problems()
+    t_gen = time.perf_counter() - t_gen
+    problems, rhs, keep, names = [], [], [], []
+    for i, (name, prob, nev) in enumerate(probs):
+        dev = {k: torch.from_numpy(v).cuda() for k, v in G.problem_arrays(prob).items()}
+        keep.append(dev)
+        opts = G.geneo_default_options(nev_max=nev, tau=0.3, precision=G.GENEO_PREC_FP32)
+        problems.append((G.make_problem(dev, prob.n, prob.n_sub, prob.elem_dofs.shape[1], prob.ndn,
+                                        G.GENEO_MEM_DEVICE), opts, prob.n))
+        rng = np.random.default_rng(1000 + i)
+        b = rng.uniform(-1.0, 1.0, (8, prob.n))
+        b[:, prob.dirichlet != 0] = 0.0
+        rhs.append(torch.from_numpy(b.reshape(-1)).cuda())
+        names.append((name, prob.n))
     torch.cuda.synchronize()
-    solve = S.library_solve_fn(problems, rhs, tol=tol)
-    make_stream = torch.cuda.Stream
-    # calibration: every problem once, alone (also the warm-up of each size)
-    cal = [S.Request(i, i, nrhs=1, arrival=0.0) for i in range(len(problems))]
-    S.Server(solve, workers=1, make_stream=make_stream).run(cal)
-    mean_service = sum(r.service for r in cal) / len(cal)
-    rate = SERVE_LOAD * SERVE_WORKERS / mean_service
-    trace = S.poisson_trace(n_requests + warmup, rate, seed=5, choices=len(problems))
+    pool = S.library_pool(problems, SERVE_BUDGET)
+    solve = S.resident_solve_fn(problems, rhs, pool, tol=tol)
+    trace = S.poisson_trace(n_requests + warmup, SERVE_RATE, seed=5, choices=len(problems), max_nrhs=8)
     reqs = [S.Request(i, k, nrhs=m, arrival=t) for i, (t, k, m) in enumerate(trace)]
-    S.Server(solve, workers=SERVE_WORKERS, make_stream=make_stream).run(reqs)
+    S.Server(solve, workers=SERVE_WORKERS, make_stream=torch.cuda.Stream).run(reqs)
     out = S.summarize(reqs, warmup=warmup)
+    out.update(pool.stats())
+    pool.close()
     bad = sum(1 for r in reqs if r.result and not all(i["converged"] for i in r.result))
-    out.update({"workers": SERVE_WORKERS, "offered_rps": rate, "load": SERVE_LOAD,
-                "calibrated_service_ms": 1e3 * mean_service, "unconverged": bad,
-                "trace": "%d requests after %d warm-up, Poisson arrivals (seed 5); 3D Darcy %s elements "
-                         "(dofs %s), two kappa seeds each, 16^3-element subdomains, overlap 2, nev<=20, "
-                         "FP32 factors; 1-4 right-hand sides per request; latency = arrival to last "
-                         "solution (setup + PCG rel-res %g + release)"
-                         % (n_requests, warmup, "/".join("%d^3" % e[0] for e in SERVE_SIZES),
-                            "/".join(str(n) for n in sizes[::2]), tol)})
+    out.update({"workers": SERVE_WORKERS, "offered_rps": SERVE_RATE, "unconverged": bad,
+                "host_generation_s": t_gen,
+                "trace": "%d requests after %d warm-up, Poisson arrivals at %g/s (seed 5); %d problems: 3D "
+                         "Darcy %s elements (16^3-element boxes, overlap 2, nev<=20) and laminate "
+                         "elasticity %s elements (about 12^3-element boxes, overlap 2, nev<=30), %d seeded "
+                         "coefficient samples each, FP32 factors; 1-8 right-hand sides per request in one "
+                         "geneo_pcg_solve call; handles resident, admitted by device footprint (budget "
+                         "%g GB); latency = arrival to last solution, rel-res %g"
+                         % (n_requests, warmup, SERVE_RATE, len(problems),
+                            "/".join("%d^3" % n for n in SERVE_DARCY), "/".join("%d^3" % n for n in SERVE_ELAST),
+                            SERVE_SAMPLES, SERVE_BUDGET / 1e9, tol)})
     return out
 
 
@@ -477,7 +499,8 @@ def main():
     ap.add_argument("--eig-solve-tf32", type=int, default=0,
                     help="mixed path: eigensolver block solves in one TF32 pass (1) or three (0)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
-    ap.add_argument("--serve-requests", type=int, default=150)
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-warmup", type=int, default=50)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -634,7 +657,7 @@ def main():
 
     serve = None
     if rank == 0 and not args.no_serve:
-        serve = serve_measure(args.serve_requests, 15, args.tol)
+        serve = serve_measure(args.serve_requests, args.serve_warmup, args.tol)
 
     if rank == 0:
         line = {

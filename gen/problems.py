@@ -389,7 +389,7 @@ def uneven_darcy_problem(nel, n_parts, min_side, max_side, seed=3, contrast_rang
 
 
 def elasticity_problem(nel, parts, overlap, layer_thickness=2, body_force=(0.0, 0.0, -1.0),
-                       name="laminate"):
+                       name="laminate", seed=None):
     """Q1 hexahedral linear elasticity of a fibre/resin laminate (Section 2, eq. 3).
 
     Domain [0, nx*h] x [0, ny*h] x [0, nz*h] with h = 1/nz.  Layers of
@@ -397,6 +397,9 @@ def elasticity_problem(nel, parts, overlap, layer_thickness=2, body_force=(0.0, 
     E2 = E3 = 10, nu12 = nu13 = 0.3, nu23 = 0.4, G12 = G13 = 5,
     G23 = E2/(2(1+nu23)), units GPa) and resin (isotropic E = 3, nu = 0.35);
     successive fibre layers turn by 90 degrees about z.  Clamped at x = 0.
+    With a seed the laminate is a random sample: each fibre layer's
+    orientation (0 or 90 degrees) is drawn, and each resin layer's modulus is
+    scaled by a log-uniform factor in [1/2, 2] (SplitMix64 stream).
     """
     nel = tuple(int(v) for v in nel)
     assert len(nel) == 3
@@ -411,7 +414,15 @@ def elasticity_problem(nel, parts, overlap, layer_thickness=2, body_force=(0.0, 
     layer = ez // layer_thickness
     kind = np.where(layer % 2 == 1, 0, np.where((layer // 2) % 2 == 0, 1, 2))  # 0 resin, 1/2 fibre
     table = np.stack([k_res, k_fib0, k_fib90])
-    elem_mats = table[kind]
+    if seed is None:
+        elem_mats = table[kind]
+    else:
+        nl = int(layer.max()) + 1
+        u = splitmix64(np.arange(2 * nl, dtype=np.uint64) + np.uint64(seed << 20)).astype(np.float64) / 2.0 ** 64
+        orient = np.where(u[:nl] < 0.5, 1, 2)
+        scale = 2.0 ** (2.0 * u[nl:] - 1.0)
+        kind = np.where(layer % 2 == 1, 0, orient[layer])
+        elem_mats = table[kind] * np.where(kind == 0, scale[layer], 1.0)[:, None, None]
     load = np.zeros(24)
     load[2::3] = body_force[2] * h ** 3 / 8
     load[0::3] = body_force[0] * h ** 3 / 8

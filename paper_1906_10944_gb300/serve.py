@@ -1,12 +1,16 @@
 """Concurrent solve service over the C ABI.
 
-A request is one linear system family A x_i = b_i (i < nrhs): the GenEO
-setup of A (Sections 3 and 4), PCG for each right-hand side (Section 5) and
-the release of the handle.  Worker threads take requests first come, first
-served, each on its own CUDA stream, so the setups and solves of different
-requests overlap on the GPU (the library allocates from the stream-ordered
-pool, so no call synchronises the device).  Latency is measured from a
-request's arrival to its last solution.
+A request is one linear system family A x_i = b_i (i < nrhs): PCG for each
+right-hand side (Section 5) with the GenEO preconditioner of A (Sections 3
+and 4).  Worker threads take requests first come, first served, each on its
+own CUDA stream, so the setups and solves of different requests overlap on
+the GPU (the library allocates from the stream-ordered pool, so no call
+synchronises the device).  With a ResidentPool the set-up handle of each
+problem stays on the device between requests (admitted by device-memory
+footprint, released least recently used first), so a request for a
+resident problem only solves; `library_solve_fn` instead sets up and
+releases per request.  Latency is measured from a request's arrival to its
+last solution.
 
 The arithmetic lives in the library; this module only queues, dispatches and
 records times.  `solve_fn` may be replaced (tests use a host stand-in).
@@ -41,7 +45,7 @@ class Request:
         return self.finish - self.start
 
 
-def poisson_trace(n: int, rate: float, seed: int, choices: int, max_nrhs: int = 4):
+def poisson_trace(n: int, rate: float, seed: int, choices: int, max_nrhs: int = 8):
     """Seeded arrival offsets (exponential gaps of mean 1 / rate), the index of
     the problem each request uses and its number of right-hand sides."""
     rng = random.Random(seed)
@@ -79,6 +83,158 @@ def library_solve_fn(problems, rhs, tol=1e-8, maxit=2000):
         return infos
 
     return solve
+
+
+class ResidentPool:
+    """Set-up handles kept on the device between requests, one per problem
+    key, so a request for a problem already set up only solves.
+
+    Admission by device-memory footprint: a new setup is admitted when the
+    bytes of the resident handles plus its estimate (`estimate(key)`) fit in
+    `budget`; idle handles are released least recently used first to make
+    room; while busy handles hold the memory the setup waits; a setup larger
+    than the whole budget is admitted once nothing else is resident.  After a
+    setup the estimate is replaced by the handle's measured bytes
+    (`bytes_of(handle)`).  Solves on one handle are serialised (a handle owns
+    one set of work vectors); different handles run concurrently.
+    `setup(key, stream)` and `destroy(handle)` do the library calls."""
+
+    class Entry:
+        def __init__(self, key):
+            self.key = key
+            self.handle = None
+            self.bytes = 0.0
+            self.ready = False
+            self.busy = 0
+            self.last = 0.0
+            self.lock = threading.Lock()
+
+    def __init__(self, setup: Callable, destroy: Callable, bytes_of: Callable, estimate: Callable,
+                 budget: float):
+        self.setup, self.destroy, self.bytes_of, self.estimate = setup, destroy, bytes_of, estimate
+        self.budget = float(budget)
+        self.entries = {}
+        self.used = 0.0
+        self.peak = 0.0
+        self.hits = self.misses = self.evictions = 0
+        self.cond = threading.Condition()
+
+    def _evict_one(self):
+        idle = [e for e in self.entries.values() if e.ready and e.busy == 0]
+        if not idle:
+            return False
+        e = min(idle, key=lambda x: x.last)
+        del self.entries[e.key]
+        self.used -= e.bytes
+        self.evictions += 1
+        self.cond.release()
+        try:
+            self.destroy(e.handle)
+        finally:
+            self.cond.acquire()
+        return True
+
+    def acquire(self, key, stream=None):
+        """The entry of `key`, set up if needed, marked busy; call release()."""
+        with self.cond:
+            while True:
+                e = self.entries.get(key)
+                if e is not None:
+                    if e.ready:
+                        e.busy += 1
+                        self.hits += 1
+                        return e
+                    self.cond.wait()
+                    continue
+                need = float(self.estimate(key))
+                while self.used + need > self.budget and self._evict_one():
+                    pass
+                if self.used + need > self.budget and self.entries:
+                    self.cond.wait()
+                    continue
+                e = self.Entry(key)
+                e.bytes = need
+                e.busy = 1
+                self.entries[key] = e
+                self.used += need
+                self.peak = max(self.peak, self.used)
+                self.misses += 1
+                break
+        try:
+            h = self.setup(key, stream)
+        except Exception:
+            with self.cond:
+                del self.entries[key]
+                self.used -= e.bytes
+                self.cond.notify_all()
+            raise
+        with self.cond:
+            e.handle = h
+            b = float(self.bytes_of(h))
+            self.used += b - e.bytes
+            self.peak = max(self.peak, self.used)
+            e.bytes = b
+            e.ready = True
+            self.cond.notify_all()
+        return e
+
+    def release(self, e):
+        with self.cond:
+            e.busy -= 1
+            e.last = time.perf_counter()
+            self.cond.notify_all()
+
+    def close(self):
+        with self.cond:
+            for e in list(self.entries.values()):
+                if e.handle is not None:
+                    self.destroy(e.handle)
+            self.entries.clear()
+            self.used = 0.0
+
+    def stats(self):
+        n = self.hits + self.misses
+        return {"resident_hits": self.hits, "setups": self.misses, "evictions": self.evictions,
+                "hit_rate": self.hits / n if n else float("nan"), "peak_resident_gb": self.peak / 1e9,
+                "budget_gb": self.budget / 1e9}
+
+
+def resident_solve_fn(problems, rhs, pool: ResidentPool, tol=1e-8, maxit=2000):
+    """Solve function over resident handles: the payload of a request is a
+    problem key; rhs[key] = device tensor (n * max_nrhs) of right-hand sides.
+    The request's right-hand sides go to the library in one geneo_pcg_solve
+    call (nrhs columns).  One output buffer per worker thread."""
+    import torch
+    from . import geneo as G
+    local = threading.local()
+
+    def solve(req: Request, stream):
+        k = req.payload
+        n = problems[k][2]
+        x = getattr(local, "x", None)
+        if x is None or x.numel() < n * req.nrhs:
+            with torch.cuda.stream(stream):
+                x = torch.empty(max(n * req.nrhs, 1), dtype=torch.float64, device="cuda")
+            local.x = x
+        e = pool.acquire(k, stream)
+        try:
+            with e.lock:
+                info = G.geneo_pcg_solve(e.handle, rhs[k], x, req.nrhs, tol, maxit, G.GENEO_MEM_DEVICE,
+                                         stream=stream)
+        finally:
+            pool.release(e)
+        return [info]
+
+    return solve
+
+
+def library_pool(problems, budget, bytes_per_dof=2.8e3):
+    """A ResidentPool over problems[k] = (geneo_problem_t, geneo_options_t, n)."""
+    from . import geneo as G
+    return ResidentPool(setup=lambda k, stream: G.geneo_setup(problems[k][0], problems[k][1], stream),
+                        destroy=G.geneo_destroy,
+                        bytes_of=lambda h: G.geneo_query(h)["device_bytes"],
+                        estimate=lambda k: bytes_per_dof * problems[k][2], budget=budget)
 
 
 def footprint_by_dofs(problems, bytes_per_dof: float, bytes_per_rhs_dof: float = 16.0):

@@ -1,6 +1,7 @@
 """Service logic of paper_1906_10944_gb300.serve on the host (no GPU): a
 stand-in solve function that sleeps, so queueing, dispatch and the latency
 bookkeeping can be checked exactly."""
+import threading
 import time
 
 from paper_1906_10944_gb300 import serve as S
@@ -12,7 +13,7 @@ def test_poisson_trace_is_seeded_and_ordered():
     assert a == b
     t = [x[0] for x in a]
     assert all(t2 > t1 for t1, t2 in zip(t, t[1:]))
-    assert {x[1] for x in a} <= set(range(4)) and {x[2] for x in a} <= {1, 2, 3, 4}
+    assert {x[1] for x in a} <= set(range(4)) and {x[2] for x in a} <= set(range(1, 9))
     # mean gap of an exponential with rate 50 is 20 ms (loose bound for 200 draws)
     assert 0.014 < t[-1] / len(t) < 0.028
 
@@ -102,3 +103,76 @@ def test_footprint_by_dofs():
     fp = S.footprint_by_dofs(problems, 2800.0)
     assert fp(S.Request(0, 1, nrhs=2)) == 2800.0 * 8000 + 16.0 * 8000 * 2
     assert fp(S.Request(1, 0, nrhs=1)) == 2800.0 * 1000 + 16.0 * 1000
+
+
+class _FakeLib:
+    """Host stand-in for the library calls of a ResidentPool."""
+
+    def __init__(self, sizes):
+        self.sizes = sizes
+        self.live = {}
+        self.setups = 0
+        self.lock = threading.Lock()
+
+    def setup(self, key, stream):
+        with self.lock:
+            self.setups += 1
+            h = object()
+            self.live[id(h)] = (h, key)
+        time.sleep(0.002)
+        return h
+
+    def destroy(self, h):
+        with self.lock:
+            del self.live[id(h)]
+
+    def bytes_of(self, h):
+        return self.sizes[self.live[id(h)][1]]
+
+
+def test_resident_pool_reuses_and_evicts_lru():
+    lib = _FakeLib({0: 40.0, 1: 40.0, 2: 40.0})
+    pool = S.ResidentPool(lib.setup, lib.destroy, lib.bytes_of, estimate=lambda k: 40.0, budget=100.0)
+    for k in (0, 1, 0, 0, 1):
+        pool.release(pool.acquire(k))
+    assert lib.setups == 2 and pool.hits == 3
+    e0 = pool.acquire(0)
+    pool.release(e0)            # 0 used last: 1 is the least recently used
+    pool.release(pool.acquire(2))
+    assert pool.evictions == 1 and set(k for _, k in lib.live.values()) == {0, 2}
+    assert pool.peak <= 100.0
+    pool.close()
+    assert not lib.live
+
+
+def test_resident_pool_waits_for_busy_memory():
+    """A setup that does not fit next to busy handles waits until they are
+    released (nothing is evicted from under a solve)."""
+    lib = _FakeLib({0: 60.0, 1: 60.0})
+    pool = S.ResidentPool(lib.setup, lib.destroy, lib.bytes_of, estimate=lambda k: 60.0, budget=100.0)
+    e0 = pool.acquire(0)
+    got = []
+
+    def other():
+        e = pool.acquire(1)
+        got.append(time.perf_counter())
+        pool.release(e)
+
+    th = threading.Thread(target=other)
+    th.start()
+    time.sleep(0.05)
+    assert not got                     # waiting: 0 is busy
+    t_rel = time.perf_counter()
+    pool.release(e0)
+    th.join(5)
+    assert got and got[0] >= t_rel and pool.evictions == 1
+    pool.close()
+
+
+def test_resident_pool_oversized_request_alone():
+    lib = _FakeLib({0: 30.0, 1: 500.0})
+    pool = S.ResidentPool(lib.setup, lib.destroy, lib.bytes_of, estimate=lambda k: lib.sizes[k], budget=100.0)
+    pool.release(pool.acquire(0))
+    pool.release(pool.acquire(1))   # evicts 0, then runs alone
+    assert pool.evictions == 1 and [k for _, k in lib.live.values()] == [1]
+    pool.close()
