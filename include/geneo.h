@@ -274,7 +274,10 @@ typedef struct {
                                 the others use double-single products */
   int32_t eig_unconverged;   /* subdomains whose eigensolve reached eig_maxit
                                 unconverged (their Ritz vectors are used) */
-  int32_t reserved;
+  int32_t factor_classes;    /* GENEO_PREC_FP32: batches the K_j and A_j
+                                factorisations ran in (size classes of the
+                                half bandwidth, each launched as one
+                                persistent kernel) */
   int64_t device_bytes;      /* device memory held by the handle */
   double setup_ms[8];        /* per phase: structure, assembly, factor,
                                 eigensolve, basis, coarse matrix, coarse
@@ -334,8 +337,13 @@ geneo_status_t geneo_apply(geneo_handle_t h, const double* r_dev, double* z_dev,
  * residual); the call then returns GENEO_ERR_PCG_NOCONV with the reached
  * true residual in info.  b and x are device arrays unless `mem` is
  * GENEO_MEM_HOST, in which case they are host arrays and the copies are part
- * of the call.  info may be NULL; with nrhs > 1 it reports the last
- * right-hand side.  Synchronises `stream`.
+ * of the call.  Several right-hand sides (nrhs >= 2) are solved together,
+ * up to 8 at a time: their CG recurrences advance in lockstep so each
+ * iteration reads A and the subdomain factors once for all of them, and each
+ * stops on its own test (the same stopping rule); the result equals
+ * separate solves up to rounding.  info may be NULL; with nrhs > 1 it
+ * reports the last right-hand side (no residual history).  Synchronises
+ * `stream`.
  */
 geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int32_t nrhs,
                                double tol, int32_t maxit, int32_t mem,

@@ -262,6 +262,37 @@ geneo_status_t geneo_pcg_solve(geneo_handle_t h, const double* b, double* x, int
   double *db = nullptr, *dx = nullptr;
   DevMem tmp;
   tmp.stream = s;
+  // several right-hand sides: solved together, up to kBlk at a time (the
+  // dense coarse inverse is needed, which every coarse space up to 16384
+  // vectors has)
+  if (nrhs >= 2 && (h->dimH == 0 || h->Hinv)) {
+    const int kb = std::min(nrhs, geneo::kBlk);
+    if (mem == GENEO_MEM_HOST) {
+      GENEO_TRY(tmp.get(&db, (size_t)n * kb));
+      GENEO_TRY(tmp.get(&dx, (size_t)n * kb));
+    }
+    for (int i0 = 0; i0 < nrhs; i0 += kb) {
+      const int k = std::min(kb, nrhs - i0);
+      const double* bi = b + (int64_t)i0 * n;
+      double* xi = x + (int64_t)i0 * n;
+      if (mem == GENEO_MEM_HOST) {
+        cudaError_t e = cudaMemcpyAsync(db, bi, sizeof(double) * n * k, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { tmp.free_all(); return GENEO_ERR_CUDA; }
+        bi = db;
+        xi = dx;
+      }
+      geneo_status_t st = geneo::pcg_block(h, bi, xi, k, tol, maxit, info, s);
+      if (mem == GENEO_MEM_HOST) {
+        cudaError_t e = cudaMemcpyAsync(x + (int64_t)i0 * n, dx, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { tmp.free_all(); return GENEO_ERR_CUDA; }
+      }
+      if (st != GENEO_OK && worst == GENEO_OK) worst = st;
+      if (st == GENEO_ERR_CUDA || st == GENEO_ERR_OOM || st == GENEO_ERR_ARG) break;
+    }
+    tmp.free_all();
+    return worst;
+  }
   if (mem == GENEO_MEM_HOST) {
     GENEO_TRY(tmp.get(&db, (size_t)n));
     GENEO_TRY(tmp.get(&dx, (size_t)n));
@@ -298,6 +329,7 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->fp64_factors_A = h->nA64;
   info->fp64_ortho = h->eig_o64;
   info->eig_unconverged = h->eig_unconv;
+  info->factor_classes = h->factor_classes;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->factor_flops = h->factor_flops;

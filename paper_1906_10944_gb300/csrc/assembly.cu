@@ -470,6 +470,67 @@ geneo_status_t refactor_fp64(geneo_handle_s* h, const AssemblyOut& a, const int3
   return GENEO_OK;
 }
 
+// A factorisation batch: descriptors (host and device copies) of one size
+// class, largest factorisations first, and its tensor-core plan.
+struct FactorBatch {
+  std::vector<BandDesc> h;
+  BandDesc* d = nullptr;
+  int maxw = 0, maxn = 0;
+  Tc5Plan plan;
+};
+
+// Size classes of a cost-sorted batch for the fifth-generation tensor-core
+// kernel: the widths that kernel takes are grouped so that no class pads a
+// band to more than 1/0.6 of its own width (rounded up to 32), each class
+// with its own tiled-band planes; the widths it does not take form one
+// batch for the older kernels.  Without the kernel: one batch.
+geneo_status_t factor_batches(const std::vector<BandDesc>& sorted, bool tc5_on, DevMem& tmp, cudaStream_t s,
+                              std::vector<FactorBatch>& out) {
+  out.clear();
+  std::vector<std::vector<BandDesc>> groups;
+  std::vector<BandDesc> rest;
+  if (!tc5_on) {
+    rest = sorted;
+  } else {
+    std::vector<int> widths;
+    for (const BandDesc& b : sorted)
+      if (tc5_fits(b.w)) widths.push_back((b.w + 31) & ~31);
+    std::sort(widths.begin(), widths.end(), std::greater<int>());
+    widths.erase(std::unique(widths.begin(), widths.end()), widths.end());
+    std::vector<int> tops;  // the W of each class, descending
+    for (int W : widths)
+      if (tops.empty() || W < 0.6 * tops.back()) tops.push_back(W);
+    groups.resize(tops.size());
+    for (const BandDesc& b : sorted) {
+      if (!tc5_fits(b.w)) {
+        rest.push_back(b);
+        continue;
+      }
+      const int W = (b.w + 31) & ~31;
+      size_t g = 0;  // the smallest class top that still covers W
+      for (size_t i = 0; i < tops.size(); ++i)
+        if (tops[i] >= W) g = i;
+      groups[g].push_back(b);
+    }
+  }
+  if (!rest.empty()) groups.push_back(rest);
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    if (groups[gi].empty()) continue;
+    FactorBatch fb;
+    fb.h = groups[gi];
+    for (const BandDesc& b : fb.h) {
+      fb.maxw = std::max(fb.maxw, b.w);
+      fb.maxn = std::max(fb.maxn, b.n);
+    }
+    GENEO_TRY(tmp.get(&fb.d, fb.h.size()));
+    GENEO_CUDA(cudaMemcpyAsync(fb.d, fb.h.data(), sizeof(BandDesc) * fb.h.size(), cudaMemcpyHostToDevice, s));
+    const bool is_rest = tc5_on && gi + 1 == groups.size() && !rest.empty();
+    if (tc5_on && !is_rest) GENEO_TRY(tc5_prepare(fb.h.data(), (int)fb.h.size(), fb.maxw, tmp, s, &fb.plan));
+    out.push_back(std::move(fb));
+  }
+  return GENEO_OK;
+}
+
 }  // namespace
 
 geneo_status_t build_structure(geneo_handle_s* h, const geneo_problem_t* p, AssemblyOut& a_out,
@@ -715,13 +776,13 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   auto t1 = std::chrono::steady_clock::now();
   EventTimer ev;
   ev.start(s);
-  // FP32 factors: tiled-band planes for the fifth-generation tensor-core
-  // factorisation, allocated on the main stream before the fork
-  Tc5Plan planK, planA;
-  if (h->fp32 && h->opt.factor_kernel != 1) {
-    GENEO_TRY(tc5_prepare(bkf.data(), N, out.maxwK, tmp, s, &planK));
-    GENEO_TRY(tc5_prepare(baf.data(), N, h->maxwA, tmp, s, &planA));
-  }
+  // FP32 factors: size classes of the half bandwidth for the
+  // fifth-generation tensor-core factorisation (each class padded to its own
+  // W), their tiled-band planes allocated on the main stream before the fork
+  std::vector<FactorBatch> batK, batA;
+  const bool tc5_on = h->fp32 && h->opt.factor_kernel != 1;
+  GENEO_TRY(factor_batches(bkf, tc5_on, tmp, s, batK));
+  GENEO_TRY(factor_batches(baf, tc5_on, tmp, s, batA));
   // K_j on the main stream, A_j concurrently on the auxiliary stream
   GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
   GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
@@ -738,10 +799,13 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
     // a weak pivot flags the matrix for an FP64 factorisation instead of
     // failing the setup
     const float wt = (float)h->opt.fp32_pivot_tol;
-    GENEO_TRY(band_potrf<float>((float*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s, equil,
-                                out.weak, wt, &planK));
-    GENEO_TRY(band_potrf<float>((float*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux, equil,
-                                out.weak + N, wt, &planA));
+    for (const FactorBatch& fb : batK)
+      GENEO_TRY(band_potrf<float>((float*)out.bandK, fb.d, (int)fb.h.size(), fb.maxw, fb.maxn, h->dstat, s, equil,
+                                  out.weak, wt, fb.plan.ok ? &fb.plan : nullptr));
+    for (const FactorBatch& fb : batA)
+      GENEO_TRY(band_potrf<float>((float*)h->bandA, fb.d, (int)fb.h.size(), fb.maxw, fb.maxn, h->dstat, h->aux,
+                                  equil, out.weak + N, wt, fb.plan.ok ? &fb.plan : nullptr));
+    h->factor_classes = (int)(batK.size() + batA.size());
   } else {
     GENEO_TRY(band_potrf<double>((double*)out.bandK, fdK, N, out.maxwK, maxnK, h->dstat, s));
     GENEO_TRY(band_potrf<double>((double*)h->bandA, fdA, N, h->maxwA, h->maxnD, h->dstat, h->aux));

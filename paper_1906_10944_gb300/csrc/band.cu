@@ -1585,14 +1585,14 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
                           DevStatus* st, cudaStream_t s, bool equil, int32_t* weak, float weak_tol,
                           const Tc5Plan* tc5) {
   if (count <= 0) return GENEO_OK;
-  if (equil && max_n > 0) {
-    k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
-    k_band_equil_a<T><<<dim3((max_n + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
-    GENEO_CUDA(cudaGetLastError());
-  }
-  // FP32: fifth-generation tensor cores (tcgen05, TMA) when the batch fits
+  // FP32: fifth-generation tensor cores (tcgen05, TMA) when the batch fits;
+  // the packing into the tiled band applies the equilibration
   if constexpr (sizeof(T) == 4) {
     if (tc5 && tc5->ok) {
+      if (equil && max_n > 0) {
+        k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
+        GENEO_CUDA(cudaGetLastError());
+      }
       GENEO_TRY(tc5_factor(*tc5, base, d_desc, st, s, weak, weak_tol));
       if (max_n > 0) {
         const int nb = (max_n + 15) / 16;
@@ -1601,6 +1601,11 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
       }
       return GENEO_OK;
     }
+  }
+  if (equil && max_n > 0) {
+    k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
+    k_band_equil_a<T><<<dim3((max_n + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
+    GENEO_CUDA(cudaGetLastError());
   }
   // FP32: left-looking tensor-core kernel when a panel's rows and two chunk
   // buffers fit in shared memory

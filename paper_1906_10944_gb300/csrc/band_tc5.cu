@@ -52,19 +52,24 @@
 namespace geneo {
 namespace {
 
-constexpr int kT5 = 256;                       // threads (8 warps)
+constexpr int kEpi5 = 256;                     // epilogue / panel threads (warps 0-7)
+constexpr int kT5 = kEpi5 + 64;                // + copy warp 8 + MMA warp 9
 constexpr int kPB5 = 32;                       // panel width = row block height
-constexpr int kSt5 = 3;                        // pipeline stages
+constexpr int kStA5 = 4;                       // A-tile stages
+constexpr int kStB5 = 2;                       // B-tile stages
 constexpr int kUS5 = kPB5 + 1;                 // row stride of the panel block in shared memory
 constexpr uint32_t kBox5 = 32u * 32u * 4u;     // one 32 x 32 FP32 box (4 KB)
 constexpr uint32_t kTileA5 = 4 * kBox5;        // 128 rows x 32 columns
 constexpr uint32_t kTileB5 = kBox5;            // 32 rows x 32 columns
-constexpr uint32_t kStage5 = 2 * kTileA5 + 2 * kTileB5;  // hi and lo of A and B: 40 KB
+constexpr uint32_t kStageA5 = 2 * kTileA5;     // hi and lo of an A tile: 32 KB
+constexpr uint32_t kStageB5 = 2 * kTileB5;     // hi and lo of a B tile: 8 KB
 constexpr uint32_t kIdesc5 = umma_idesc_tf32(128, 32);
+// afull, aempty, bfull, bempty, acc_full[2], acc_empty[2], pdone, fin
+constexpr int kBars5 = 2 * kStA5 + 2 * kStB5 + 2 + 2 + 2;
 
 size_t tc5_smem(int W) {
-  return 1024 + (size_t)kSt5 * kStage5 + (size_t)(kPB5 + W) * kUS5 * sizeof(float) + kPB5 * sizeof(float) +
-         (2 * kSt5 + 2) * sizeof(uint64_t) + 16;
+  return 1024 + (size_t)kStA5 * kStageA5 + (size_t)kStB5 * kStageB5 + (size_t)(kPB5 + W) * kUS5 * sizeof(float) +
+         2 * kPB5 * sizeof(float) + kBars5 * sizeof(uint64_t) + 16;
 }
 
 // Bounded wait that also gives up early once another role has aborted.
@@ -79,252 +84,359 @@ __device__ __forceinline__ bool wait5(uint64_t* bar, uint32_t parity, volatile i
   return false;
 }
 
+__device__ __forceinline__ void arrive5(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the 256 panel threads only (the copy and MMA warps run on)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 __device__ __forceinline__ bool finite_pos5(float v) { return v > 0.f && isfinite(v); }
 
+// Warp-specialised: warp 8 (one lane) streams the tiles of panel after
+// panel, warp 9 (one lane) issues the MMAs into one of two TMEM
+// accumulators (panel J uses buffer J % 2), and warps 0-7 run the panel
+// steps.  A tiles go through a ring of kStA5 stages, the B tile of each
+// k-chunk (shared by the chunk's row tiles) through a ring of kStB5.  The
+// tiles of panel J + 1 that do not read panel J's columns (all k-chunks but
+// the last) are loaded and multiplied while panel J is being factored; the
+// last k-chunk waits for panel J's write-back (pdone).  Barriers: afull /
+// aempty and bfull / bempty (stage rings), acc_full[b] (MMA -> panel
+// threads), acc_empty[b] (panel threads -> MMA: buffer b read), pdone
+// (panel written).
 __global__ void __launch_bounds__(kT5, 1)
 k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  float* __restrict__ phi, float* __restrict__ plo, const BandDesc* __restrict__ descs,
-                 const int64_t* __restrict__ zoff, int W, uint32_t tmem_cols, DevStatus* st,
-                 int32_t* __restrict__ weak, float weak_tol) {
-  const BandDesc d = descs[blockIdx.x];
-  const int n = d.n, w = d.w;
-  const int64_t z0 = zoff[blockIdx.x];
+                 const int64_t* __restrict__ zoff, int count, int32_t* __restrict__ queue, int W,
+                 uint32_t tmem_cols, DevStatus* st, int32_t* __restrict__ weak, float weak_tol) {
   const int Wt = W + kPB5;
-  const int QW = W / kPB5;  // k-chunks in a full window
+  const int QW = W / kPB5;                 // k-chunks in a full window
+  const uint32_t bufcols = tmem_cols / 2;  // columns of one accumulator buffer
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  unsigned char* stages = base;
-  float* Us = reinterpret_cast<float*>(base + kSt5 * kStage5);
+  unsigned char* stA = base;
+  unsigned char* stB = base + kStA5 * kStageA5;
+  float* Us = reinterpret_cast<float*>(stB + kStB5 * kStageB5);
   float* Dinv = Us + (size_t)(kPB5 + W) * kUS5;
-  uint64_t* full = reinterpret_cast<uint64_t*>(Dinv + kPB5);
-  uint64_t* empty = full + kSt5;
-  uint64_t* accum = empty + kSt5;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* afull = reinterpret_cast<uint64_t*>(Dinv + 2 * kPB5);
+  uint64_t* aempty = afull + kStA5;
+  uint64_t* bfull = aempty + kStA5;
+  uint64_t* bempty = bfull + kStB5;
+  uint64_t* acc_full = bempty + kStB5;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* pdone = acc_empty + 2;
+  uint64_t* fin = pdone + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  volatile uint32_t* inited_s = reinterpret_cast<volatile uint32_t*>(tslot + 2);
+  volatile int* item_s = reinterpret_cast<volatile int*>(tslot + 2);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
   if (tid == 0) {
-    for (int i = 0; i < kSt5; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+    for (int i = 0; i < kStA5; ++i) {
+      mbar_init(&afull[i], 1);
+      mbar_init(&aempty[i], 1);
     }
-    mbar_init(accum, 1);
+    for (int i = 0; i < kStB5; ++i) {
+      mbar_init(&bfull[i], 1);
+      mbar_init(&bempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], kEpi5);
+    }
+    mbar_init(pdone, kEpi5);
+    mbar_init(fin, 1);
     *abort = 0;
-    *inited_s = 0;
     fence_barrier_init();
   }
-  if (wid == 0) tmem_alloc(tslot, tmem_cols);
+  if (wid == 9) tmem_alloc(tslot, tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  uint32_t issued[kSt5] = {0, 0, 0};  // thread 0: copies issued into each stage
-  uint32_t t_issue = 0;               // thread 0: tiles issued (all panels)
-  uint32_t t_mma = 0;                 // thread 32: tiles consumed
-  uint32_t n_commit = 0;              // thread 32: commits to `accum`
-  uint32_t n_acc = 0;                 // all threads: accumulator phases waited
-
-  for (int J = 0; J * kPB5 < n; ++J) {
-    const int c0 = J * kPB5;
-    const int b = min(kPB5, n - c0);
-    const int R = min(n, c0 + kPB5 + w) - c0;
-    const int nh = ((R + 31) / 32 + 3) / 4;   // 128-row chunks
-    const int q0 = max(0, QW - J);            // first k-chunk with columns >= 0
-    const bool any = q0 < QW;
-    if (tid == 0 && any) {
-      // ---- producer: tiles (q, h) for q in [q0, QW), h < min(nh, q / 4 + 1)
-      for (int q = q0; q < QW; ++q) {
-        const int hmax = min(nh, q / 4 + 1);
-        for (int hh = 0; hh < hmax; ++hh) {
-          const uint32_t s = t_issue % kSt5;
-          bool go = !*abort;
-          if (go && t_issue >= (uint32_t)kSt5)
-            go = wait5(&empty[s], ((t_issue / kSt5) - 1) & 1, abort, st, d.id, c0);
-          if (go) {
-            unsigned char* sb = stages + s * kStage5;
-            mbar_arrive_expect_tx(&full[s], kStage5);
-            for (int i = 0; i < 4; ++i) {
-              const int I = J + 4 * hh + i;
-              const int x = 32 * (J + q - I);
-              tma_load_3d(sb + i * kBox5, &tm_hi, x, 0, (int)(z0 + I), &full[s]);
-              tma_load_3d(sb + kTileA5 + i * kBox5, &tm_lo, x, 0, (int)(z0 + I), &full[s]);
+  // role state carried over the matrices this CTA takes from the queue
+  uint32_t issA[kStA5] = {0, 0, 0, 0}, issB[kStB5] = {0, 0};  // copy lane: arms per stage
+  uint32_t ta = 0, tb = 0;  // copy and MMA lanes: A tiles and B tiles so far
+  int pb = 0;               // panels of the earlier matrices (barrier phases run on)
+  for (;;) {
+    // work queue: the next matrix in batch order (largest first)
+    if (tid == 0) *item_s = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = *item_s;
+    __syncthreads();
+    if (item >= count) break;
+    const BandDesc d = descs[item];
+    const int n = d.n, w = d.w;
+    const int64_t z0 = zoff[item];
+    const int np = (n + kPB5 - 1) / kPB5;  // panels
+    if (wid == 8) {
+      // ------------------------------------------------------------ copies
+      if (lane == 0) {
+        for (int J = 0; J < np; ++J) {
+          const int c0 = J * kPB5;
+          const int R = min(n, c0 + kPB5 + w) - c0;
+          const int nh = ((R + 31) / 32 + 3) / 4;
+          const int q0 = max(0, QW - J);
+          for (int q = q0; q < QW; ++q, ++tb) {
+            // the last k-chunk holds panel J - 1's columns
+            if (q == QW - 1 && J >= 1 && !*abort) wait5(pdone, (pb + J - 1) & 1, abort, st, d.id, c0);
+            {
+              const uint32_t sb = tb % kStB5;
+              if (!*abort && (tb < (uint32_t)kStB5 || wait5(&bempty[sb], ((tb / kStB5) - 1) & 1, abort, st, d.id, c0))) {
+                unsigned char* dst = stB + sb * kStageB5;
+                mbar_arrive_expect_tx(&bfull[sb], kStageB5);
+                tma_load_3d(dst, &tm_hi, 32 * q, 0, (int)(z0 + J), &bfull[sb]);
+                tma_load_3d(dst + kTileB5, &tm_lo, 32 * q, 0, (int)(z0 + J), &bfull[sb]);
+                ++issB[sb];
+              }
             }
-            tma_load_3d(sb + 2 * kTileA5, &tm_hi, 32 * q, 0, (int)(z0 + J), &full[s]);
-            tma_load_3d(sb + 2 * kTileA5 + kTileB5, &tm_lo, 32 * q, 0, (int)(z0 + J), &full[s]);
-            ++issued[s];
-          }
-          ++t_issue;
-        }
-      }
-    }
-    if (tid == 32 && any) {
-      // ---- MMA issuer
-      uint32_t inited = 0;  // bit h: D_h written in this panel
-      for (int q = q0; q < QW; ++q) {
-        const int hmax = min(nh, q / 4 + 1);
-        for (int hh = 0; hh < hmax; ++hh) {
-          const uint32_t s = t_mma % kSt5;
-          bool go = !*abort;
-          if (go) go = wait5(&full[s], (t_mma / kSt5) & 1, abort, st, d.id, c0);
-          if (go) {
-            tc_fence_after();
-            const uint32_t sa = smem_u32(stages + s * kStage5);
-            const uint32_t dt = tmem + 32u * hh;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ah = umma_desc_sw128(sa + 32 * kk);
-              const uint64_t al = umma_desc_sw128(sa + kTileA5 + 32 * kk);
-              const uint64_t bh = umma_desc_sw128(sa + 2 * kTileA5 + 32 * kk);
-              const uint64_t bl = umma_desc_sw128(sa + 2 * kTileA5 + kTileB5 + 32 * kk);
-              const uint32_t acc = ((inited >> hh) & 1u) | (kk > 0 ? 1u : 0u);
-              umma_tf32(dt, al, bh, kIdesc5, acc);
-              umma_tf32(dt, ah, bl, kIdesc5, 1u);
-              umma_tf32(dt, ah, bh, kIdesc5, 1u);
+            const int hmax = min(nh, q / 4 + 1);
+            for (int hh = 0; hh < hmax; ++hh, ++ta) {
+              const uint32_t sa = ta % kStA5;
+              if (*abort) continue;
+              if (ta >= (uint32_t)kStA5 && !wait5(&aempty[sa], ((ta / kStA5) - 1) & 1, abort, st, d.id, c0)) continue;
+              unsigned char* dst = stA + sa * kStageA5;
+              mbar_arrive_expect_tx(&afull[sa], kStageA5);
+              for (int i = 0; i < 4; ++i) {
+                const int I = J + 4 * hh + i;
+                const int x = 32 * (J + q - I);
+                tma_load_3d(dst + i * kBox5, &tm_hi, x, 0, (int)(z0 + I), &afull[sa]);
+                tma_load_3d(dst + kTileA5 + i * kBox5, &tm_lo, x, 0, (int)(z0 + I), &afull[sa]);
+              }
+              ++issA[sa];
             }
-            inited |= 1u << hh;
-            umma_commit(&empty[s]);
-          }
-          ++t_mma;
-        }
-      }
-      *inited_s = inited;
-      umma_commit(accum);  // arrives once every MMA issued so far has finished
-      ++n_commit;
-    }
-    __syncthreads();
-    uint32_t inited = 0;
-    if (any) {
-      wait5(accum, n_acc & 1, abort, st, d.id, c0);
-      ++n_acc;
-      tc_fence_after();
-      inited = *inited_s;
-    }
-    // ---- U = A - D for the panel rows.  Warp w reads TMEM lanes
-    // 32 (w % 4) .. + 31 of the chunks h = w / 4, w / 4 + 2, ...
-    __syncwarp();
-    for (int hh = wid >> 2; hh < nh; hh += 2) {
-      const int row = 128 * hh + 32 * (wid & 3) + lane;
-      float dv[32];
-      if ((inited >> hh) & 1u) {
-        tmem_ld32(tmem + ((uint32_t)(32 * (wid & 3)) << 16) + 32u * hh, dv);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) dv[i] = 0.f;
-      }
-      if (row < R) {
-        const int I = J + row / 32;
-        const int64_t o = ((z0 + I) * 32 + (row & 31)) * (int64_t)Wt + (W - 32 * (I - J));
-#pragma unroll
-        for (int col = 0; col < 32; ++col) {
-          float u = 0.f;
-          if (col < b && col <= row && row - col <= w) u = (phi[o + col] + plo[o + col]) - dv[col];
-          Us[(size_t)row * kUS5 + col] = u;
-        }
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    // ---- the 32 x 32 diagonal block in warp 0: lane r holds row r; step t
-    // takes pivot t from lane t (a pivot that is not positive is reported
-    // and replaced by 1), scales column t and updates the trailing part
-    if (wid == 0) {
-      float a[kPB5];
-#pragma unroll
-      for (int u = 0; u < kPB5; ++u) a[u] = (lane < b && u <= lane) ? Us[lane * kUS5 + u] : 0.f;
-#pragma unroll
-      for (int t = 0; t < kPB5; ++t) {
-        if (t < b) {
-          float p = __shfl_sync(0xffffffffu, a[t], t);
-          if (weak) {
-            if (lane == 0 && !(p > weak_tol)) weak[d.id] = 1;
-            if (!finite_pos5(p)) p = 1.f;
-          } else if (!finite_pos5(p)) {
-            if (lane == 0) record_error(st, isfinite(p) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id,
-                                        (int64_t)c0 + t);
-            p = 1.f;
-          }
-          const float inv = rsqrtf(p);
-          if (lane == t) {
-            a[t] = p * inv;
-            Dinv[t] = inv;
-          } else if (lane > t) {
-            a[t] *= inv;
-          }
-#pragma unroll
-          for (int u = t + 1; u < kPB5; ++u) {
-            const float lut = __shfl_sync(0xffffffffu, a[t], u);
-            if (lane >= u) a[u] -= a[t] * lut;
           }
         }
       }
-      if (lane < b) {
-#pragma unroll
-        for (int u = 0; u < kPB5; ++u)
-          if (u <= lane) Us[lane * kUS5 + u] = a[u];
-      } else {
-        Dinv[lane] = 0.f;
-      }
-    }
-    __syncthreads();
-    // ---- rows below: x L_JJ^T = u, one row per thread
-    for (int i = b + tid; i < R; i += kT5) {
-      float* ur = Us + (size_t)i * kUS5;
-      float x[kPB5];
-#pragma unroll
-      for (int t = 0; t < kPB5; ++t) x[t] = ur[t];
-#pragma unroll
-      for (int t = 0; t < kPB5; ++t) {
-        if (t < b) {
-          float v = x[t];
-#pragma unroll
-          for (int u = 0; u < t; ++u) v -= x[u] * Us[t * kUS5 + u];
-          x[t] = v * Dinv[t];
+    } else if (wid == 9) {
+      // ------------------------------------------------------------ MMAs
+      if (lane == 0) {
+        for (int J = 0; J < np; ++J) {
+          const int c0 = J * kPB5;
+          const int R = min(n, c0 + kPB5 + w) - c0;
+          const int nh = ((R + 31) / 32 + 3) / 4;
+          const int q0 = max(0, QW - J);
+          const int G = pb + J;  // panel index over this CTA's matrices
+          const int b = G & 1;
+          if (G >= 2 && !*abort) wait5(&acc_empty[b], ((G >> 1) - 1) & 1, abort, st, d.id, c0);
+          tc_fence_after();
+          const uint32_t dbuf = tmem + (uint32_t)b * bufcols;
+          uint32_t inited = 0;
+          for (int q = q0; q < QW; ++q, ++tb) {
+            const uint32_t sb = tb % kStB5;
+            const bool bok = !*abort && wait5(&bfull[sb], (tb / kStB5) & 1, abort, st, d.id, c0);
+            const uint32_t bsa = smem_u32(stB + sb * kStageB5);
+            const int hmax = min(nh, q / 4 + 1);
+            for (int hh = 0; hh < hmax; ++hh, ++ta) {
+              const uint32_t sa = ta % kStA5;
+              if (!bok || *abort || !wait5(&afull[sa], (ta / kStA5) & 1, abort, st, d.id, c0)) continue;
+              tc_fence_after();
+              const uint32_t asa = smem_u32(stA + sa * kStageA5);
+              const uint32_t dt = dbuf + 32u * hh;
+  #pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ah = umma_desc_sw128(asa + 32 * kk);
+                const uint64_t al = umma_desc_sw128(asa + kTileA5 + 32 * kk);
+                const uint64_t bh = umma_desc_sw128(bsa + 32 * kk);
+                const uint64_t bl = umma_desc_sw128(bsa + kTileB5 + 32 * kk);
+                const uint32_t acc = ((inited >> hh) & 1u) | (kk > 0 ? 1u : 0u);
+                umma_tf32(dt, al, bh, kIdesc5, acc);
+                umma_tf32(dt, ah, bl, kIdesc5, 1u);
+                umma_tf32(dt, ah, bh, kIdesc5, 1u);
+              }
+              inited |= 1u << hh;
+              umma_commit(&aempty[sa]);
+            }
+            if (bok) umma_commit(&bempty[sb]);  // the k-chunk's row tiles are all issued
+          }
+          umma_commit(&acc_full[b]);  // every MMA of this panel has finished
         }
       }
-#pragma unroll
-      for (int t = 0; t < kPB5; ++t) ur[t] = x[t];
-    }
-    __syncthreads();
-    // ---- the panel's columns back to both planes (warp per row, coalesced)
-    for (int i = wid; i < R; i += kT5 / 32) {
-      const int r = c0 + i, c = c0 + lane;
-      if (lane < b && c <= r && r - c <= w) {
-        const int I = J + i / 32;
-        const int64_t o = ((z0 + I) * 32 + (i & 31)) * (int64_t)Wt + (W - 32 * (I - J)) + lane;
-        const float x = Us[(size_t)i * kUS5 + lane];
-        const float xh = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-        phi[o] = xh;
-        plo[o] = x - xh;
+    } else {
+      // ------------------------------------------------------------ panels
+      for (int J = 0; J < np; ++J) {
+        const int c0 = J * kPB5;
+        const int b = min(kPB5, n - c0);
+        const int R = min(n, c0 + kPB5 + w) - c0;
+        const int nh = ((R + 31) / 32 + 3) / 4;
+        const int q0 = max(0, QW - J);
+        const int G = pb + J;
+        const int buf = G & 1;
+        // the panel's entries of A (both planes) into Us: eight lanes per row,
+        // four columns each (16-byte loads), four row groups of 32 rows per
+        // batch in flight; entries outside the band are zero in the planes
+        {
+          const int rsub = lane >> 3, cg = 4 * (lane & 7);
+          for (int i0 = 4 * wid + rsub; i0 < R; i0 += 4 * kEpi5 / 8) {
+            float4 vh[4], vl[4];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + u * (kEpi5 / 8);
+              vh[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+              vl[u] = vh[u];
+              if (i < R) {
+                const int I = J + i / 32;
+                const int64_t o = ((z0 + I) * 32 + (i & 31)) * (int64_t)Wt + (W - 32 * (I - J)) + cg;
+                vh[u] = *reinterpret_cast<const float4*>(phi + o);
+                vl[u] = *reinterpret_cast<const float4*>(plo + o);
+              }
+            }
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + u * (kEpi5 / 8);
+              if (i < R) {
+                float* ur = Us + (size_t)i * kUS5 + cg;
+                ur[0] = vh[u].x + vl[u].x;
+                ur[1] = vh[u].y + vl[u].y;
+                ur[2] = vh[u].z + vl[u].z;
+                ur[3] = vh[u].w + vl[u].w;
+              }
+            }
+          }
+        }
+        if (!*abort) wait5(&acc_full[buf], (G >> 1) & 1, abort, st, d.id, c0);
+        tc_fence_after();
+        epi_sync();
+        // U = A - D.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 of the
+        // chunks h = w / 4, w / 4 + 2, ...; chunk h holds data when one of its
+        // tiles was multiplied (some k-chunk q >= 4 h exists)
+        __syncwarp();
+        for (int hh = wid >> 2; hh < nh; hh += 2) {
+          if (!(q0 < QW && 4 * hh <= QW - 1)) continue;
+          float dv[32];
+          tmem_ld32(tmem + (uint32_t)buf * bufcols + ((uint32_t)(32 * (wid & 3)) << 16) + 32u * hh, dv);
+          const int row = 128 * hh + 32 * (wid & 3) + lane;
+          if (row < R) {
+            float* ur = Us + (size_t)row * kUS5;
+  #pragma unroll
+            for (int col = 0; col < 32; ++col)
+              if (col < b && col <= row && row - col <= w) ur[col] -= dv[col];
+          }
+        }
+        tc_fence_before();
+        arrive5(&acc_empty[buf]);  // the MMAs may refill this buffer
+        epi_sync();
+        // ---- the 32 x 32 diagonal block in warp 0: lane r holds row r; step t
+        // takes pivot t from lane t (a pivot that is not positive is reported
+        // and replaced by 1), scales column t and updates the trailing part
+        if (wid == 0) {
+          // lane r holds row r; step t publishes the scaled column t in Dcol
+          // (shared memory) and every lane updates its row from it
+          float* Dcol = Dinv + kPB5;  // kPB5 scratch values after Dinv
+          float a[kPB5];
+  #pragma unroll
+          for (int u = 0; u < kPB5; ++u) a[u] = (lane < b && u <= lane) ? Us[lane * kUS5 + u] : 0.f;
+  #pragma unroll
+          for (int t = 0; t < kPB5; ++t) {
+            if (t < b) {
+              float p = __shfl_sync(0xffffffffu, a[t], t);
+              if (weak) {
+                if (lane == 0 && !(p > weak_tol)) weak[d.id] = 1;
+                if (!finite_pos5(p)) p = 1.f;
+              } else if (!finite_pos5(p)) {
+                if (lane == 0) record_error(st, isfinite(p) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id,
+                                            (int64_t)c0 + t);
+                p = 1.f;
+              }
+              const float inv = rsqrtf(p);
+              if (lane == t) {
+                a[t] = p * inv;
+                Dinv[t] = inv;
+              } else if (lane > t) {
+                a[t] *= inv;
+              }
+              Dcol[lane] = a[t];
+              __syncwarp();
+  #pragma unroll
+              for (int u = t + 1; u < kPB5; ++u)
+                if (lane >= u) a[u] -= a[t] * Dcol[u];
+              __syncwarp();
+            }
+          }
+          if (lane < b) {
+  #pragma unroll
+            for (int u = 0; u < kPB5; ++u)
+              if (u <= lane) Us[lane * kUS5 + u] = a[u];
+          } else {
+            Dinv[lane] = 0.f;
+          }
+        }
+        epi_sync();
+        // ---- rows below: x L_JJ^T = u, one row per thread
+        for (int i = b + tid; i < R; i += kEpi5) {
+          float* ur = Us + (size_t)i * kUS5;
+          float x[kPB5];
+  #pragma unroll
+          for (int t = 0; t < kPB5; ++t) x[t] = ur[t];
+  #pragma unroll
+          for (int t = 0; t < kPB5; ++t) {
+            if (t < b) {
+              float v = x[t];
+  #pragma unroll
+              for (int u = 0; u < t; ++u) v -= x[u] * Us[t * kUS5 + u];
+              x[t] = v * Dinv[t];
+            }
+          }
+  #pragma unroll
+          for (int t = 0; t < kPB5; ++t) ur[t] = x[t];
+        }
+        epi_sync();
+        // ---- the panel's columns back to both planes: eight lanes per row,
+        // 16-byte stores.  Us holds exact zeros outside the band (A is zero
+        // there and every update of such an entry is 0 - 0), which is also
+        // what the planes hold there.
+        {
+          const int rsub = lane >> 3, cg = 4 * (lane & 7);
+          for (int i = 4 * wid + rsub; i < R; i += kEpi5 / 8) {
+            const int I = J + i / 32;
+            const int64_t o = ((z0 + I) * 32 + (i & 31)) * (int64_t)Wt + (W - 32 * (I - J)) + cg;
+            const float* ur = Us + (size_t)i * kUS5 + cg;
+            float4 xh, xl;
+            xh.x = __uint_as_float(__float_as_uint(ur[0]) & 0xffffe000u); xl.x = ur[0] - xh.x;
+            xh.y = __uint_as_float(__float_as_uint(ur[1]) & 0xffffe000u); xl.y = ur[1] - xh.y;
+            xh.z = __uint_as_float(__float_as_uint(ur[2]) & 0xffffe000u); xl.z = ur[2] - xh.z;
+            xh.w = __uint_as_float(__float_as_uint(ur[3]) & 0xffffe000u); xl.w = ur[3] - xh.w;
+            *reinterpret_cast<float4*>(phi + o) = xh;
+            *reinterpret_cast<float4*>(plo + o) = xl;
+          }
+        }
+        fence_proxy_async_global();  // the next panel's copies read these columns
+        arrive5(pdone);
+        epi_sync();                  // Us is refilled by the next panel
       }
     }
-    fence_proxy_async_global();  // the next panel's copies read these columns
-    __syncthreads();
+    pb += np;
   }
-  // ---- drain: the last phase of every stage's copies, and every MMA issued
-  if (tid == 0)
-    for (int s = 0; s < kSt5; ++s)
-      if (issued[s] > 0)
-        for (int it = 0; it < (1 << 22) && !mbar_try_wait(&full[s], (issued[s] - 1) & 1); ++it) {
+  // drain: the last phase of every stage's copies, and every MMA issued
+  if (tid == 8 * 32) {
+    for (int i = 0; i < kStA5; ++i)
+      if (issA[i] > 0)
+        for (int it = 0; it < (1 << 22) && !mbar_try_wait(&afull[i], (issA[i] - 1) & 1); ++it) {
         }
-  if (tid == 32) {
-    umma_commit(accum);
-    const uint32_t ph = n_commit & 1;  // phase index n_commit completes with this commit
-    for (int it = 0; it < (1 << 22) && !mbar_try_wait(accum, ph); ++it) {
+    for (int i = 0; i < kStB5; ++i)
+      if (issB[i] > 0)
+        for (int it = 0; it < (1 << 22) && !mbar_try_wait(&bfull[i], (issB[i] - 1) & 1); ++it) {
+        }
+  }
+  if (tid == 9 * 32) {
+    umma_commit(fin);
+    for (int it = 0; it < (1 << 22) && !mbar_try_wait(fin, 0); ++it) {
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (wid == 0) {
+  if (wid == 9) {
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, tmem_cols);
   }
 }
 
-// band (skewed rows, BandDesc) -> tiled-band planes; one warp per row
+// band (skewed rows, BandDesc) -> tiled-band planes, every entry of every
+// row block (zeros outside the band and beyond n), one warp per row.  With
+// a row scaling (d.scl >= 0) the planes receive s_r s_c a_rc, the
+// equilibrated matrix S A S.
 __global__ void __launch_bounds__(256)
 k_tb_pack(const float* __restrict__ band, const BandDesc* __restrict__ descs, const int64_t* __restrict__ zoff,
           int W, float* __restrict__ phi, float* __restrict__ plo) {
@@ -332,17 +444,23 @@ k_tb_pack(const float* __restrict__ band, const BandDesc* __restrict__ descs, co
   const int Wt = W + kPB5;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < d.n; r += nw) {
+  const float* S = d.scl >= 0 ? band + d.scl : nullptr;
+  const int rows = (d.n + 31) & ~31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
     const int I = r / 32;
     const float* src = band + d.off + (int64_t)r * d.ld;
-    float* dh = phi + ((zoff[blockIdx.y] + I) * 32 + (r & 31)) * (int64_t)Wt;
-    float* dl = plo + ((zoff[blockIdx.y] + I) * 32 + (r & 31)) * (int64_t)Wt;
-    for (int c = max(0, r - d.w) + lane; c <= r; c += 32) {
-      const float x = src[c - r + d.w];
+    const int64_t o = ((zoff[blockIdx.y] + I) * 32 + (r & 31)) * (int64_t)Wt;
+    const float sr = (S && r < d.n) ? S[r] : 1.f;
+    for (int xx = lane; xx < Wt; xx += 32) {
+      const int c = xx + 32 * I - W;
+      float x = 0.f;
+      if (r < d.n && c >= 0 && c <= r && r - c <= d.w) {
+        x = src[c - r + d.w];
+        if (S) x *= sr * S[c];
+      }
       const float xh = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-      const int xx = c - 32 * I + W;
-      dh[xx] = xh;
-      dl[xx] = x - xh;
+      phi[o + xx] = xh;
+      plo[o + xx] = x - xh;
     }
   }
 }
@@ -398,6 +516,12 @@ bool encode_tb_map(CUtensorMap* m, float* base, int W, int64_t Z) {
 
 }  // namespace
 
+bool tc5_fits(int w) {
+  const int W = (w + 31) & ~31;
+  const int nh = (kPB5 + W + 127) / 128;
+  return W >= kPB5 && tc5_smem(W) <= 227 * 1024 && 2 * 32 * nh <= 512;
+}
+
 geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
                            Tc5Plan* p) {
   p->ok = false;
@@ -407,7 +531,7 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   if (W < kPB5 || smem > 227 * 1024) return GENEO_OK;  // the older kernels take it
   const int nh = (kPB5 + W + 127) / 128;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(32 * nh)) cols <<= 1;
+  while (cols < (uint32_t)(2 * 32 * nh)) cols <<= 1;  // two accumulator buffers
   if (cols > 512) return GENEO_OK;
   std::vector<int64_t> zo(count);
   int64_t Z = 0;
@@ -422,10 +546,9 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   GENEO_TRY(tmp.get(&p->phi, plane));
   GENEO_TRY(tmp.get(&p->plo, plane));
   GENEO_TRY(tmp.get(&p->dz, (size_t)count));
+  GENEO_TRY(tmp.get(&p->queue, 1));
   if (!encode_tb_map(&p->mhi, p->phi, W, Z) || !encode_tb_map(&p->mlo, p->plo, W, Z)) return GENEO_OK;
   GENEO_CUDA(cudaMemcpyAsync(p->dz, zo.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, s));
-  GENEO_CUDA(cudaMemsetAsync(p->phi, 0, sizeof(float) * plane, s));
-  GENEO_CUDA(cudaMemsetAsync(p->plo, 0, sizeof(float) * plane, s));
   p->W = W;
   p->cols = cols;
   p->smem = smem;
@@ -441,8 +564,14 @@ geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc,
   k_tb_pack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_CUDA(allow_smem(k_band_potrf_tc5));
-  k_band_potrf_tc5<<<p.count, kT5, p.smem, s>>>(p.mhi, p.mlo, p.phi, p.plo, d_desc, p.dz, p.W, p.cols, st,
-                                                 weak, weak_tol);
+  // persistent CTAs, one per SM (the shared memory allows no more), taking
+  // matrices from the queue in batch order
+  int dev = 0, sms = 0;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  GENEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GENEO_CUDA(cudaMemsetAsync(p.queue, 0, sizeof(int32_t), s));
+  k_band_potrf_tc5<<<std::min(p.count, sms), kT5, p.smem, s>>>(p.mhi, p.mlo, p.phi, p.plo, d_desc, p.dz, p.count,
+                                                                p.queue, p.W, p.cols, st, weak, weak_tol);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
   k_tb_unpack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo); note_launch();

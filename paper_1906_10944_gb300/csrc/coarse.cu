@@ -174,7 +174,15 @@ inline double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// X = I (dim x dim, column-major)
+__global__ void k_identity(double* __restrict__ X, int dim) {
+  const int64_t tot = (int64_t)dim * dim;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = (i % dim == i / dim) ? 1.0 : 0.0;
+}
+
 }  // namespace
+
 
 geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const double* X, DevMem& tmp,
                             cudaStream_t s, double* ms_basis, double* ms_matrix, double* ms_factor) {
@@ -264,6 +272,38 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
   GENEO_TRY(band_potrf<double>(h->bandH, h->dbandH, 1, wH, h->dimH, h->dstat, s));
   h->prof.end(pf, s);
   GENEO_TRY(check_status(h, s));
+  // The preconditioner's coarse solve A_H y = c runs on one small band, a
+  // chain of dependent steps on one SM; instead A_H^{-1} is formed once here
+  // (A_H X = I solved with the factor, 16 columns per block, all column
+  // blocks in one launch) and each apply is a dense FP64 matrix-vector
+  // product spread over the GPU.  Kept up to 16384 coarse dofs (2 GB).
+  if (h->dimH <= 16384) {
+    const int dim = h->dimH, nc = (dim + 15) / 16;
+    std::vector<BandDesc> rep(nc, bh);
+    std::vector<int64_t> xo(nc);
+    std::vector<int32_t> cnt(nc);
+    for (int i = 0; i < nc; ++i) {
+      rep[i].id = -1;  // vectors indexed by the position in the batch
+      xo[i] = (int64_t)i * 16 * dim;
+      cnt[i] = std::min(16, dim - 16 * i);
+    }
+    BandDesc* drep = nullptr;
+    int64_t* dxo = nullptr;
+    int32_t* dcnt = nullptr;
+    GENEO_TRY(tmp.get(&drep, (size_t)nc));
+    GENEO_TRY(tmp.get(&dxo, (size_t)nc));
+    GENEO_TRY(tmp.get(&dcnt, (size_t)nc));
+    GENEO_TRY(h->mem.get(&h->Hinv, (size_t)dim * dim));
+    GENEO_TRY(h->mem.get(&h->yH, (size_t)dim));
+    GENEO_CUDA(cudaMemcpyAsync(drep, rep.data(), sizeof(BandDesc) * nc, cudaMemcpyHostToDevice, s));
+    GENEO_CUDA(cudaMemcpyAsync(dxo, xo.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, s));
+    GENEO_CUDA(cudaMemcpyAsync(dcnt, cnt.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+    k_identity<<<(unsigned)std::min<int64_t>(((int64_t)dim * dim + kT - 1) / kT, 152 * 16), kT, 0, s>>>(
+        h->Hinv, dim); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_TRY(band_solve<double>(h->bandH, drep, nc, wH, h->Hinv, dxo, 16, dcnt, nullptr, h->dstat, s, 0));
+    GENEO_TRY(check_status(h, s));
+  }
   *ms_factor = ms_since(t2);
   tmp.release(Y);
   return GENEO_OK;

@@ -297,9 +297,12 @@ struct Tc5Plan {
   float* phi = nullptr;
   float* plo = nullptr;
   int64_t* dz = nullptr;
+  int32_t* queue = nullptr;  // work counter of the persistent launch
 };
 geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
                            Tc5Plan* p);
+// whether a band of half bandwidth w fits the kernel (shared memory, TMEM)
+bool tc5_fits(int w);
 geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc, DevStatus* st, cudaStream_t s,
                           int32_t* weak, float weak_tol);
 

@@ -48,6 +48,7 @@ struct geneo_handle_s {
   int nA64 = 0, maxwA64 = 0, maxnA64 = 0;
   std::vector<uint8_t> a64;        // [N] 1: A_j factored in FP64
   int nK64 = 0;                    // the same count for K_j (setup only)
+  int factor_classes = 0;          // FP32: factorisation batches (size classes) of K_j and A_j
 
   // coarse space
   int dimH = 0, wH = 0;
@@ -56,6 +57,16 @@ struct geneo_handle_s {
   double* bandH = nullptr;         // band factor of A_H
   geneo::BandDesc* dbandH = nullptr;
   int64_t* xoffH = nullptr;        // {0}
+  double* Hinv = nullptr;          // A_H^{-1} (dimH x dimH), or NULL: band solves
+  double* yH = nullptr;            // [dimH] coarse solution
+  // SELL-32 copy of A for the PCG products: slice s holds rows 32 s .. 32 s
+  // + 31, entry t of row 32 s + l at sell_off[s] + 32 t + l (padding: value
+  // 0, column of the row itself)
+  int64_t* sell_off = nullptr;     // [n/32 + 1]
+  int32_t* sell_col = nullptr;
+  double* sell_val = nullptr;
+  int64_t sell_nnz = 0;
+  int spmv_blocks = 1024;          // grid of the SELL product (resident blocks)
   std::vector<double> lambda_host; // [N * s] ascending lambda per subdomain
   int s_block = 0;
   int eig_iters = 0;
@@ -79,6 +90,12 @@ struct geneo_handle_s {
   double* hist = nullptr;          // PCG alpha/beta history (2 * hist_cap)
   int hist_cap = 0;
   std::vector<double> pcg_host;    // host work of geneo_pcg_solve_noalloc (sized at setup)
+  // several right-hand sides at once (solve_block.cu): n x kBlk blocks and
+  // the subdomain vectors of kBlk columns, allocated on first use
+  double *blk_r = nullptr, *blk_z = nullptr, *blk_p = nullptr, *blk_q = nullptr, *blk_t = nullptr;
+  double *blk_u = nullptr, *blk_c = nullptr, *blk_y = nullptr, *blk_part = nullptr, *blk_scal = nullptr;
+  int32_t* blk_mask = nullptr;
+  int64_t* blk_uoff = nullptr;
   int device = -1;                 // device the handle was set up on
 
   geneo::KernelProfiler prof;
@@ -131,8 +148,15 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& a, const doubl
                             double* ms_factor);
 
 // solve.cu
+// Condition estimate lambda_max / lambda_min of the Lanczos tridiagonal
+// matrix of CG coefficients a[0..m), b[0..m-1) (bisection; work d, e of m).
+double condition_estimate_fixed(const double* a, const double* b, int m, double* d, double* e);
 geneo_status_t alloc_solver(geneo_handle_s* h);
 geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStream_t s);
 geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
                    geneo_solve_info_t* info, cudaStream_t s);
+// solve_block.cu: k <= kBlk right-hand sides at once (stride n, device)
+constexpr int kBlk = 8;
+geneo_status_t pcg_block(geneo_handle_s* h, const double* b, double* x, int k, double tol, int maxit,
+                         geneo_solve_info_t* info, cudaStream_t s);
 }  // namespace geneo

@@ -71,43 +71,6 @@ k_prolong(int64_t n, const uint8_t* __restrict__ dir, const double* __restrict__
   }
 }
 
-// q = A p; partial sums of p.q per block.  Eight lanes per row and two rows
-// per lane group in flight (rows r0 + g and r0 + 4 + g of an eight-row group
-// per warp), so each warp keeps several independent load chains going; the
-// in-row and per-block summation orders are fixed.
-__global__ void __launch_bounds__(kT)
-k_spmv_dot(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-           const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
-           double* __restrict__ part) {
-  __shared__ double red[kT / 32];
-  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double dsum = 0.0;
-  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
-    const int64_t ra = r0 + g, rb = r0 + 4 + g;
-    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
-    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
-    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
-    double sa = 0.0, sb = 0.0;
-    while (ea < ea1 || eb < eb1) {
-      if (ea < ea1) { sa += val[ea] * p[col[ea]]; ea += 8; }
-      if (eb < eb1) { sb += val[eb] * p[col[eb]]; eb += 8; }
-    }
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) {
-      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
-      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
-    }
-    if (sl == 0) {
-      if (ra < n) { q[ra] = sa; dsum += sa * p[ra]; }
-      if (rb < n) { q[rb] = sb; dsum += sb * p[rb]; }
-    }
-  }
-  dsum = block_sum(dsum, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = dsum;
-}
-
 __global__ void __launch_bounds__(kT)
 k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ part) {
   __shared__ double red[kT / 32];
@@ -117,6 +80,160 @@ k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b, dou
     s += a[i] * b[i];
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// SELL-32 copy of A for the PCG products (one thread per row, the 32 rows of
+// a slice in one warp, so every value and column load is one coalesced
+// 128- or 256-byte access; the p gathers hit L2).  Built once per handle.
+// ---------------------------------------------------------------------------
+// slice length: 32 x the longest row of the slice
+__global__ void k_sell_len(int64_t n, const int64_t* __restrict__ rowptr, int64_t* __restrict__ len) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsl = (n + 31) / 32;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nsl;
+       sl += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t r = sl * 32 + lane;
+    int l = r < n ? (int)(rowptr[r + 1] - rowptr[r]) : 0;
+    for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(0xffffffffu, l, o));
+    if (lane == 0) len[sl] = 32 * (int64_t)l;
+  }
+}
+
+__global__ void k_sell_fill(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const int64_t* __restrict__ off,
+                            int32_t* __restrict__ scol, double* __restrict__ sval) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ((n + 31) & ~(int64_t)31);
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = r >> 5, l = r & 31;
+    const int64_t o = off[sl], w = (off[sl + 1] - o) >> 5;
+    const int64_t b = r < n ? rowptr[r] : 0, len = r < n ? rowptr[r + 1] - b : 0;
+    for (int64_t t = 0; t < w; ++t) {
+      const bool in = t < len;
+      scol[o + 32 * t + l] = in ? col[b + t] : (int32_t)(r < n ? r : 0);
+      sval[o + 32 * t + l] = in ? val[b + t] : 0.0;
+    }
+  }
+}
+
+// y = A x for the rows of two slices at once (lane l: rows 32 sl + l and
+// 32 sl2 + l; sl2 < 0: none), four products of each in flight
+__device__ __forceinline__ void sell_row2(const int64_t* __restrict__ off, const int32_t* __restrict__ scol,
+                                          const double* __restrict__ sval, const double* __restrict__ x,
+                                          int64_t sl, int64_t sl2, int l, double* y) {
+  const int64_t oa = off[sl] + l;
+  const int wa = (int)((off[sl + 1] - off[sl]) >> 5);
+  const int64_t ob = sl2 >= 0 ? off[sl2] + l : 0;
+  const int wb = sl2 >= 0 ? (int)((off[sl2 + 1] - off[sl2]) >> 5) : 0;
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+  const int wm = min(wa, wb);
+  int t = 0;
+  for (; t + 1 < wm; t += 2) {
+    const int64_t ea = oa + 32 * (int64_t)t, eb = ob + 32 * (int64_t)t;
+    const double v0 = sval[ea], v1 = sval[ea + 32], u0 = sval[eb], u1 = sval[eb + 32];
+    const int32_t c0 = scol[ea], c1 = scol[ea + 32], d0 = scol[eb], d1 = scol[eb + 32];
+    a0 += v0 * x[c0];
+    a1 += v1 * x[c1];
+    b0 += u0 * x[d0];
+    b1 += u1 * x[d1];
+  }
+  for (int ta = t; ta < wa; ++ta) {
+    const int64_t e = oa + 32 * (int64_t)ta;
+    a0 += sval[e] * x[scol[e]];
+  }
+  for (int tb = t; tb < wb; ++tb) {
+    const int64_t e = ob + 32 * (int64_t)tb;
+    b0 += sval[e] * x[scol[e]];
+  }
+  y[0] = a0 + a1;
+  y[1] = b0 + b1;
+}
+
+// y = A x for the rows of one slice (lane l: row 32 sl + l), four products in flight
+__device__ __forceinline__ double sell_row(const int64_t* __restrict__ off, const int32_t* __restrict__ scol,
+                                           const double* __restrict__ sval, const double* __restrict__ x,
+                                           int64_t sl, int l) {
+  const int64_t o = off[sl] + l;
+  const int w = (int)((off[sl + 1] - off[sl]) >> 5);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int t = 0;
+  for (; t + 3 < w; t += 4) {
+    const int64_t e = o + 32 * (int64_t)t;
+    a0 += sval[e] * x[scol[e]];
+    a1 += sval[e + 32] * x[scol[e + 32]];
+    a2 += sval[e + 64] * x[scol[e + 64]];
+    a3 += sval[e + 96] * x[scol[e + 96]];
+  }
+  for (; t < w; ++t) {
+    const int64_t e = o + 32 * (int64_t)t;
+    a0 += sval[e] * x[scol[e]];
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// q = A p; partial sums of p.q per block
+__global__ void __launch_bounds__(kT)
+k_spmv_sell_dot(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ scol,
+                const double* __restrict__ sval, const double* __restrict__ p, double* __restrict__ q,
+                double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  const int l = threadIdx.x & 31;
+  const int64_t nsl = (n + 31) / 32;
+  double dsum = 0.0;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += 2 * nw) {
+    const int64_t sl2 = sl + nw < nsl ? sl + nw : -1;
+    double v[2];
+    sell_row2(off, scol, sval, p, sl, sl2, l, v);
+    const int64_t r = sl * 32 + l, r2 = (sl + nw) * 32 + l;
+    if (r < n) {
+      q[r] = v[0];
+      dsum += v[0] * p[r];
+    }
+    if (sl2 >= 0 && r2 < n) {
+      q[r2] = v[1];
+      dsum += v[1] * p[r2];
+    }
+  }
+  dsum = block_sum(dsum, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = dsum;
+}
+
+// r = b - A x; partial sums of r.r per block
+__global__ void __launch_bounds__(kT)
+k_true_resid_sell(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ scol,
+                  const double* __restrict__ sval, const double* __restrict__ x, const double* __restrict__ b,
+                  double* __restrict__ r, double* __restrict__ part) {
+  __shared__ double red[kT / 32];
+  const int l = threadIdx.x & 31;
+  const int64_t nsl = (n + 31) / 32;
+  double rsum = 0.0;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nsl;
+       sl += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double v = sell_row(off, scol, sval, x, sl, l);
+    const int64_t i = sl * 32 + l;
+    if (i < n) {
+      const double ri = b[i] - v;
+      r[i] = ri;
+      rsum += ri * ri;
+    }
+  }
+  rsum = block_sum(rsum, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = rsum;
+}
+
+// y = X c with X = A_H^{-1} (symmetric; row i read as column i, contiguous):
+// one warp per row
+__global__ void __launch_bounds__(kT)
+k_coarse_gemv(const double* __restrict__ X, int dim, const double* __restrict__ c, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < dim; i += (gridDim.x * blockDim.x) >> 5) {
+    const double* xi = X + (int64_t)i * dim;
+    double a = 0.0;
+    for (int j = lane; j < dim; j += 32) a += xi[j] * c[j];
+    a = warp_sum(a);
+    if (lane == 0) y[i] = a;
+  }
 }
 
 // scalars: 0 rz, 1 alpha, 2 beta, 3 rr, 4 pq, 5 bb, 6 flag
@@ -147,41 +264,6 @@ __global__ void k_finish(const double* __restrict__ part, int nb, double* __rest
   } else if (what == 5) {     // ||b - A x||^2
     scal[7] = s;
   }
-}
-
-// r = b - A x (the true residual, same row mapping and summation order as
-// k_spmv_dot); partial sums of r.r per block.
-__global__ void __launch_bounds__(kT)
-k_true_resid(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-             const double* __restrict__ val, const double* __restrict__ x, const double* __restrict__ b,
-             double* __restrict__ r, double* __restrict__ part) {
-  __shared__ double red[kT / 32];
-  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double rsum = 0.0;
-  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
-    const int64_t ra = r0 + g, rb = r0 + 4 + g;
-    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
-    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
-    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
-    double sa = 0.0, sb = 0.0;
-    while (ea < ea1 || eb < eb1) {
-      if (ea < ea1) { sa += val[ea] * x[col[ea]]; ea += 8; }
-      if (eb < eb1) { sb += val[eb] * x[col[eb]]; eb += 8; }
-    }
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) {
-      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
-      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
-    }
-    if (sl == 0) {
-      if (ra < n) { const double v = b[ra] - sa; r[ra] = v; rsum += v * v; }
-      if (rb < n) { const double v = b[rb] - sb; r[rb] = v; rsum += v * v; }
-    }
-  }
-  rsum = block_sum(rsum, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = rsum;
 }
 
 __global__ void __launch_bounds__(kT)
@@ -227,8 +309,8 @@ __device__ __forceinline__ void block_atomic_add(double v, double* dst, double* 
 
 // q = A p, PQ[par] += p.q; clears the other parity's slots for their next use
 __global__ void __launch_bounds__(kT)
-k_spmv_atomic(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-              const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
+k_spmv_atomic(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ scol,
+              const double* __restrict__ sval, const double* __restrict__ p, double* __restrict__ q,
               double* __restrict__ scal, int par) {
   __shared__ double red[kT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -236,28 +318,16 @@ k_spmv_atomic(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __re
     scal[kPQ + (par ^ 1)] = 0.0;
     scal[kRR + (par ^ 1)] = 0.0;
   }
-  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int l = threadIdx.x & 31;
+  const int64_t nsl = (n + 31) / 32;
   double dsum = 0.0;
-  for (int64_t r0 = warp * 8; r0 < n; r0 += nwarps * 8) {
-    const int64_t ra = r0 + g, rb = r0 + 4 + g;
-    int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
-    if (ra < n) { ea = rowptr[ra] + sl; ea1 = rowptr[ra + 1]; }
-    if (rb < n) { eb = rowptr[rb] + sl; eb1 = rowptr[rb + 1]; }
-    double sa = 0.0, sb = 0.0;
-    while (ea < ea1 || eb < eb1) {
-      if (ea < ea1) { sa += val[ea] * p[col[ea]]; ea += 8; }
-      if (eb < eb1) { sb += val[eb] * p[col[eb]]; eb += 8; }
-    }
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) {
-      sa += __shfl_xor_sync(0xffffffffu, sa, off, 8);
-      sb += __shfl_xor_sync(0xffffffffu, sb, off, 8);
-    }
-    if (sl == 0) {
-      if (ra < n) { q[ra] = sa; dsum += sa * p[ra]; }
-      if (rb < n) { q[rb] = sb; dsum += sb * p[rb]; }
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nsl;
+       sl += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double v = sell_row(off, scol, sval, p, sl, l);
+    const int64_t r = sl * 32 + l;
+    if (r < n) {
+      q[r] = v;
+      dsum += v * p[r];
     }
   }
   block_atomic_add(dsum, &scal[kPQ + par], red);
@@ -313,6 +383,8 @@ __global__ void k_update_p_atomic(int64_t n, double* __restrict__ scal, const do
     p[i] = z[i] + beta * p[i];
 }
 
+}  // namespace
+
 // Condition estimate lambda_max / lambda_min of the Lanczos tridiagonal
 // matrix of the CG coefficients (alpha a[0..m), beta b[0..m-1)): both
 // extreme eigenvalues by bisection on the Sturm sequence count, in caller
@@ -352,8 +424,6 @@ double condition_estimate_fixed(const double* a, const double* b, int m, double*
   return ext[1] / ext[0];
 }
 
-}  // namespace
-
 geneo_status_t alloc_solver(geneo_handle_s* h) {
   DevMem& M = h->mem;
   const int64_t n = h->n;
@@ -371,6 +441,34 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   GENEO_CUDA(cudaMemcpy(h->uoff, off.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice));
   GENEO_TRY(M.get(&h->xoffH, 1));
   GENEO_CUDA(cudaMemset(h->xoffH, 0, sizeof(int64_t)));
+  {
+    // SELL-32 copy of A for the PCG products
+    const int64_t nsl = (n + 31) / 32;
+    DevMem tmp;
+    tmp.stream = h->mem.stream;
+    int64_t* len = nullptr;
+    GENEO_TRY(tmp.get(&len, (size_t)nsl + 1));
+    GENEO_TRY(M.get(&h->sell_off, (size_t)nsl + 1));
+    const int g = (int)std::min<int64_t>((nsl * 32 + kT - 1) / kT, 152 * 16);
+    k_sell_len<<<g, kT, 0, h->mem.stream>>>(n, h->rowptr, len); note_launch();
+    GENEO_CUDA(cudaMemsetAsync(len + nsl, 0, sizeof(int64_t), h->mem.stream));
+    int64_t tot = 0;
+    GENEO_TRY(exclusive_scan_i64(len, h->sell_off, nsl + 1, &tot, tmp, h->mem.stream));
+    GENEO_TRY(M.get(&h->sell_col, (size_t)std::max<int64_t>(tot, 1)));
+    GENEO_TRY(M.get(&h->sell_val, (size_t)std::max<int64_t>(tot, 1)));
+    k_sell_fill<<<g, kT, 0, h->mem.stream>>>(n, h->rowptr, h->col, h->val, h->sell_off, h->sell_col,
+                                             h->sell_val); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    GENEO_CUDA(cudaStreamSynchronize(h->mem.stream));
+    tmp.free_all();
+    h->sell_nnz = tot;
+    // the product's grid: the blocks that are resident at once (no tail wave)
+    int dev = 0, sms = 0, occ = 0;
+    GENEO_CUDA(cudaGetDevice(&dev));
+    GENEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GENEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_sell_dot, kT, 0));
+    h->spmv_blocks = std::max(1, std::min(kRedBlocks, sms * std::max(occ, 1)));
+  }
   if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
   // host arrays of the allocation-free solve (Lanczos coefficients and the
   // bisection work), sized once here so that solve never touches the heap
@@ -400,6 +498,8 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
   h->local_solve_flops = lfl;
   h->local_solve_bytes = lby;
   h->spmv_flops = 2.0 * (double)h->nnz;
+  // algorithmic bytes of q = A p with p.q: A once (values and columns), p
+  // read once, q written once, the row offsets
   h->spmv_bytes = 12.0 * (double)h->nnz + 8.0 * (double)n + 24.0 * (double)n;
   return GENEO_OK;
 }
@@ -408,15 +508,25 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
   const int N = h->N;
   k_restrict<<<N, kT, 0, s>>>(h->dsub, h->Dlist, r, h->Z, h->u, h->cH); note_launch();
   GENEO_CUDA(cudaGetLastError());
-  // the coarse solve (one block) runs beside the batched local solves
-  if (h->dimH > 0) {
+  // the coarse solve: a dense product with A_H^{-1} on this stream (short),
+  // or the band solve on one SM beside the batched local solves
+  if (h->dimH > 0 && h->Hinv) {
+    const double dm = h->dimH;
+    const int pc = h->prof.begin(GENEO_PROF_COARSE_SOLVE, 2.0 * dm * dm, 8.0 * dm * dm + 16.0 * dm, s);
+    const int g = std::min(ceil_div(h->dimH, kT / 32), 152 * 8);
+    k_coarse_gemv<<<g, kT, 0, s>>>(h->Hinv, h->dimH, h->cH, h->yH); note_launch();
+    GENEO_CUDA(cudaGetLastError());
+    h->prof.end(pc, s);
+  } else if (h->dimH > 0) {
     GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
     GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-    const int pc = h->prof.begin(GENEO_PROF_COARSE_SOLVE, band_solve_flops(h->dimH, h->wH),
-                                 2.0 * 8.0 * band_entries(h->dimH, h->wH) + 16.0 * h->dimH, h->aux);
-    GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr,
-                                 h->dstat, h->aux, h->dimH));
-    h->prof.end(pc, h->aux);
+    {
+      const int pc = h->prof.begin(GENEO_PROF_COARSE_SOLVE, band_solve_flops(h->dimH, h->wH),
+                                   2.0 * 8.0 * band_entries(h->dimH, h->wH) + 16.0 * h->dimH, h->aux);
+      GENEO_TRY(band_solve<double>(h->bandH, h->dbandH, 1, h->wH, h->cH, h->xoffH, 1, nullptr, nullptr,
+                                   h->dstat, h->aux, h->dimH));
+      h->prof.end(pc, h->aux);
+    }
     GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   }
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
@@ -430,10 +540,10 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
                                  nullptr, nullptr, h->dstat, s, h->maxnD));
   h->prof.end(pl, s);
-  if (h->dimH > 0) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+  if (h->dimH > 0 && !h->Hinv) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
   k_prolong<<<grid, kT, 0, s>>>(h->n, h->dir, r, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub,
-                                h->u, h->Z, h->cH, z); note_launch();
+                                h->u, h->Z, h->Hinv ? h->yH : h->cH, z); note_launch();
   GENEO_CUDA(cudaGetLastError());
   return GENEO_OK;
 }
@@ -513,7 +623,8 @@ geneo_status_t pcg_core(geneo_handle_s* h, const double* b, double* x, double to
   };
   // true residual into zv (free between the update and the next apply)
   auto true_residual = [&](double* out) -> geneo_status_t {
-    k_true_resid<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, x, b, h->zv, red); note_launch();
+    k_true_resid_sell<<<nb, kT, 0, s>>>(n, h->sell_off, h->sell_col, h->sell_val, x, b, h->zv, red);
+    note_launch();
     k_finish<<<1, kT, 0, s>>>(red, nb, scal, 5, B.da, B.db, 0); note_launch();
     GENEO_CUDA(cudaGetLastError());
     GENEO_CUDA(cudaMemcpyAsync(h->hpin, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
@@ -530,14 +641,17 @@ geneo_status_t pcg_core(geneo_handle_s* h, const double* b, double* x, double to
     {
       const int pv = h->prof.begin(GENEO_PROF_SPMV, h->spmv_flops, h->spmv_bytes, s);
       if (det) {
-        k_spmv_dot<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, red); note_launch();
+        k_spmv_sell_dot<<<h->spmv_blocks, kT, 0, s>>>(n, h->sell_off, h->sell_col, h->sell_val, h->p, h->q,
+                                                      red);
+        note_launch();
       } else {
-        k_spmv_atomic<<<nb, kT, 0, s>>>(n, h->rowptr, h->col, h->val, h->p, h->q, scal, par); note_launch();
+        k_spmv_atomic<<<nb, kT, 0, s>>>(n, h->sell_off, h->sell_col, h->sell_val, h->p, h->q, scal, par);
+        note_launch();
       }
       h->prof.end(pv, s);
     }
     if (det) {
-      k_finish<<<1, kT, 0, s>>>(red, nb, scal, 1, B.da, B.db, it); note_launch();
+      k_finish<<<1, kT, 0, s>>>(red, h->spmv_blocks, scal, 1, B.da, B.db, it); note_launch();
       k_update_xr<<<nb, kT, 0, s>>>(n, scal, h->p, h->q, x, h->r, red); note_launch();
       k_finish<<<1, kT, 0, s>>>(red, nb, scal, 2, B.da, B.db, it); note_launch();
     } else {

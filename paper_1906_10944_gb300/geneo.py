@@ -80,7 +80,7 @@ class geneo_coarse_info_t(C.Structure):
         ("n_sub", C.c_int32), ("dim_coarse", C.c_int32), ("coarse_bandwidth", C.c_int32),
         ("eig_iterations", C.c_int32), ("block_size", C.c_int32),
         ("fp64_factors_K", C.c_int32), ("fp64_factors_A", C.c_int32), ("fp64_ortho", C.c_int32),
-        ("eig_unconverged", C.c_int32), ("reserved", C.c_int32), ("device_bytes", C.c_int64),
+        ("eig_unconverged", C.c_int32), ("factor_classes", C.c_int32), ("device_bytes", C.c_int64),
         ("setup_ms", C.c_double * 8), ("factor_flops", C.c_double), ("factor_event_ms", C.c_double),
         ("eigsolve_flops", C.c_double), ("eigsolve_event_ms", C.c_double),
         ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
@@ -232,6 +232,7 @@ def geneo_query(h):
             "eig_iterations": q.eig_iterations, "block_size": q.block_size,
             "fp64_factors_K": q.fp64_factors_K, "fp64_factors_A": q.fp64_factors_A,
             "fp64_ortho": q.fp64_ortho, "eig_unconverged": q.eig_unconverged,
+            "factor_classes": q.factor_classes,
             "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms),
             "factor_flops": q.factor_flops, "factor_event_ms": q.factor_event_ms,
             "eigsolve_flops": q.eigsolve_flops, "eigsolve_event_ms": q.eigsolve_event_ms,

@@ -332,3 +332,49 @@ def test_mixed_precision_fp64_refactor(pivot_tol):
         assert abs(info["iterations"] - ito) <= 2 + 0.1 * ito, (info["iterations"], ito)
     finally:
         sol.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_pcg_several_rhs(precision):
+    """Several right-hand sides in one call (solved together, 8 at a time):
+    every column meets the true-residual bar, its error against a direct
+    solve meets the single-solve bar, and it equals the one-column solve of
+    the same right-hand side up to the solver tolerance; 11 columns exercise
+    a full block of 8 and a ragged block of 3."""
+    import torch
+    import scipy.sparse.linalg as spla
+    from paper_1906_10944_gb300 import geneo as G
+    nel = (18, 14, 12)
+    kap = gen.kappa_grf_layers_3d(nel, seed=4, corr_len=0.2, variance=2.0, contrast=1e4,
+                                  slab_z=(30, 80), slab_thickness=1)
+    prob = gen.darcy_problem(nel, kap, (3, 2, 2), 2)
+    k = 11
+    rng = np.random.default_rng(9)
+    B = rng.uniform(-1, 1, (k, prob.n))
+    B[:, prob.dirichlet != 0] = 0.0
+    B[0] = prob.b
+    sol, _ = run_gpu(prob, nev_max=8, precision=precision)
+    try:
+        bd = torch.from_numpy(B.reshape(-1)).cuda()
+        xd = torch.zeros_like(bd)
+        info = G.geneo_pcg_solve(sol.h, bd, xd, k, 1e-8, 1000)
+        X = xd.cpu().numpy().reshape(k, prob.n)
+        lu = spla.splu(prob.A.tocsc())
+        for c in range(k):
+            bn = np.linalg.norm(B[c])
+            res = np.linalg.norm(B[c] - prob.A @ X[c]) / bn
+            ev = np.finfo(np.float64).eps * np.linalg.norm(abs(prob.A) @ np.abs(X[c])) / bn
+            assert res <= 1e-8 + 2 * ev, (c, res)
+            xs = lu.solve(B[c])
+            x1 = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            one = G.geneo_pcg_solve(sol.h, torch.from_numpy(B[c]).cuda(), x1, 1, 1e-8, 1000)
+            x1 = x1.cpu().numpy()
+            e_blk = np.linalg.norm(X[c] - xs) / np.linalg.norm(xs)
+            e_one = np.linalg.norm(x1 - xs) / np.linalg.norm(xs)
+            assert e_blk <= max(1e-7, 10 * e_one), (c, e_blk, e_one)
+            assert np.linalg.norm(X[c] - x1) <= 1e-6 * np.linalg.norm(x1)
+            if c == k - 1:
+                assert abs(info["iterations"] - one["iterations"]) <= 2
+                assert info["converged"] and info["true_residual"] <= 1e-8
+    finally:
+        sol.close()
