@@ -478,6 +478,132 @@ def serve_measure(n_requests, warmup, tol):
     return out
 
 
+C4_DESC = ("uneven batching: 3D Darcy Q1 160^3 elements (4,173,281 dofs), 1024 boxes of an irregular "
+           "k-d partition (sides 6-20 elements, seed 3), overlap 1-3 per box, one inclusion of "
+           "log-uniform contrast 1e4-1e8 per box, nev<=20, tau=0.3, PCG rel-res 1e-8")
+
+
+def c4_measure(tol):
+    """One setup and solve of the uneven batch (FP32 factors with per-subdomain
+    FP64 fallback), the factorisation in size classes of the half bandwidth,
+    each class one persistent launch."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_1906_10944_gb300 import geneo as G
+    t0 = time.perf_counter()
+    prob = gen.uneven_darcy_problem((160, 160, 160), 1024, 6, 20, seed=3)
+    t_gen = time.perf_counter() - t0
+    dev = {k: torch.from_numpy(v).cuda() for k, v in G.problem_arrays(prob).items()}
+    p = G.make_problem(dev, prob.n, prob.n_sub, prob.elem_dofs.shape[1], prob.ndn, G.GENEO_MEM_DEVICE)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    out = {"workload": C4_DESC, "dofs": int(prob.n), "host_generation_s": t_gen}
+    for prec, name in ((G.GENEO_PREC_FP32, "mixed"), (G.GENEO_PREC_FP64, "fp64")):
+        opts = G.geneo_default_options(nev_max=20, tau=0.3, precision=prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = G.geneo_setup(p, opts, stream)
+        try:
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            info = G.geneo_pcg_solve(h, b, x, 1, tol, 2000, G.GENEO_MEM_DEVICE, stream=stream,
+                                     raise_on_error=False)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            q = G.geneo_query(h)
+        finally:
+            G.geneo_destroy(h)
+        xr = x.cpu().numpy()
+        bn = np.linalg.norm(prob.b)
+        res = float(np.linalg.norm(prob.b - prob.A @ xr) / bn)
+        floor = float(np.finfo(np.float64).eps * np.linalg.norm(abs(prob.A) @ np.abs(xr)) / bn)
+        out[name] = {"setup_s": t2 - t1, "solve_s": t3 - t2, "value": prob.n / (t3 - t1), "unit": UNIT,
+                     "pcg_iterations": info["iterations"], "status": info["status"],
+                     "true_residual": res, "fp64_residual_floor": floor,
+                     "kappa_estimate": info["kappa_estimate"], "dim_coarse": q["dim_coarse"],
+                     "eig_iterations": q["eig_iterations"], "eig_unconverged": q["eig_unconverged"],
+                     "factor_classes": q["factor_classes"], "fp64_factors_K": q["fp64_factors_K"],
+                     "fp64_factors_A": q["fp64_factors_A"],
+                     "setup_ms": dict(zip(["structure", "assembly", "factor", "eigensolve", "basis",
+                                           "coarse_matrix", "coarse_factor", "total"],
+                                          [round(v, 1) for v in q["setup_ms"]]))}
+    return out
+
+
+def robustness_curves(tol):
+    """Section 5.2 (Fig. 4) and Section 5.1 (Fig. 3) as arrays, computed by
+    the library on 2D Darcy, 800 x 800 Q1 elements, u = 1 on top and 0 at
+    the bottom, Neumann elsewhere, 8 x 8 subdomains grown by one element
+    layer (a two-element overlap zone): the Lanczos estimate of
+    kappa(M^{-1} A) for a fixed number of eigenvectors per subdomain against
+    the contrast (skyscrapers: 6-14 eigenvectors; 40 layers: 2-5), and the
+    coarse approximation error ||u - u_H||_A / ||u||_A of the skyscraper
+    problem at contrast 1e6 with 1, 2 and 4 eigenvectors (u_H = the A-
+    orthogonal projection of u onto V_H, from the library's Z blocks)."""
+    import numpy as np
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    import torch
+    import gen
+    from paper_1906_10944_gb300 import geneo as G
+    nel = (800, 800)
+    contrasts = [10.0 ** e for e in range(0, 7)]
+    out = {"grid": "800x800 Q1, 8x8 subdomains, overlap 1 (two-element zone), fixed eigenvector count",
+           "contrast": contrasts}
+
+    def kappa_of(prob, nev):
+        sol = G.GenEO(prob, nev_max=nev, fixed_nev=1, precision=G.GENEO_PREC_FP64)
+        try:
+            b = torch.from_numpy(prob.b).cuda()
+            x = torch.zeros_like(b)
+            info = sol.solve(b, x, tol=tol, maxit=5000, raise_on_error=False)
+            return info["kappa_estimate"], info["iterations"]
+        finally:
+            sol.close()
+
+    for name, nevs, field in (("skyscrapers", (6, 8, 10, 12, 14), lambda c: gen.kappa_skyscrapers_2d(nel, c, seed=0)),
+                              ("layers", (2, 3, 4, 5), lambda c: gen.kappa_layers_2d(nel, c, n_layers=40))):
+        curves = {}
+        for nev in nevs:
+            ks, its = [], []
+            for c in contrasts:
+                prob = gen.darcy_problem(nel, field(c), (8, 8), 1, dirichlet="top1_bottom0")
+                k, it = kappa_of(prob, nev)
+                ks.append(k)
+                its.append(it)
+            curves["%d EV" % nev] = {"kappa": ks, "iterations": its}
+        out[name] = curves
+    # coarse approximation error (Fig. 3)
+    prob = gen.darcy_problem(nel, gen.kappa_skyscrapers_2d(nel, 1e6, seed=0), (8, 8), 1, dirichlet="top1_bottom0")
+    import scipy.sparse.linalg as spla
+    u = spla.spsolve(prob.A.tocsc(), prob.b)
+    Au = prob.A @ u
+    un = float(np.sqrt(u @ Au))
+    errs = {}
+    for nev in (1, 2, 4):
+        sol = G.GenEO(prob, nev_max=nev, fixed_nev=1, precision=G.GENEO_PREC_FP64)
+        try:
+            rows, cols, vals, off = [], [], [], 0
+            for j in range(prob.n_sub):
+                g = sol.subdomain(j)
+                for k in range(g["m"]):
+                    rows.append(g["D"])
+                    cols.append(np.full(g["D"].size, off + k))
+                    vals.append(g["Z"][:, k])
+                off += g["m"]
+        finally:
+            sol.close()
+        Zg = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(prob.n, off))
+        AH = (Zg.T @ (prob.A @ Zg)).toarray()
+        uh = Zg @ sla.cho_solve(sla.cho_factor(AH), Zg.T @ Au)
+        e = u - uh
+        errs["%d EV" % nev] = float(np.sqrt(e @ (prob.A @ e))) / un
+    out["coarse_error_skyscrapers_1e6"] = errs
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,6 +625,10 @@ def main():
     ap.add_argument("--eig-solve-tf32", type=int, default=0,
                     help="mixed path: eigensolver block solves in one TF32 pass (1) or three (0)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
+    ap.add_argument("--no-c4", action="store_true", help="skip the uneven-batch (160^3, 1024 boxes) leg")
+    ap.add_argument("--robustness", action="store_true",
+                    help="only print the Section 5.1/5.2 arrays (condition number against contrast, "
+                         "coarse approximation error) as one JSON line")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-warmup", type=int, default=50)
     args = ap.parse_args()
@@ -508,7 +638,7 @@ def main():
     import numpy as np
     rank0 = int(os.environ.get("RANK", "0")) == 0
     cpu_base = None
-    if rank0 and not args.no_cpu_baseline:
+    if rank0 and not args.no_cpu_baseline and not args.robustness:
         # the oracle's process pool (spawn) and its coarse timings come
         # before this process touches the GPU
         cpu_base = OracleBaseline(args.workload, make_problem(args.workload))
@@ -516,6 +646,9 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_1906_10944_gb300 import geneo as G
+    if args.robustness:
+        print(json.dumps(robustness_curves(args.tol)))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -655,6 +788,10 @@ def main():
                "phases_s": {"setup": r["setup_s"], "solve": r["solve_s"],
                             "coarse": cpu_base.t_coarse_matrix + cpu_base.t_coarse_factor}}
 
+    c4 = None
+    if rank == 0 and not args.no_c4:
+        c4 = c4_measure(args.tol)
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_measure(args.serve_requests, args.serve_warmup, args.tol)
@@ -675,6 +812,7 @@ def main():
             "e2e": e2e, "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
             "roofline": roofline, "cpu_baseline": cpu,
             "compare": compare,
+            "uneven_batch": c4,
             "serve": serve,
             "detail": {"pcg_iterations": info_m["iterations"], "rel_residual_true": main_run["res"],
                        "kappa_estimate": info_m["kappa_estimate"], "dim_coarse": qm["dim_coarse"],

@@ -169,6 +169,9 @@ typedef struct {
  *             meets a pivot <= this value (the bands are equilibrated to a
  *             unit diagonal) is factored and solved in FP64 instead
  *             (adaptive precision per subdomain; default 1e-4, in [0, 1)).
+ *             A factorisation on the tensor cores (three-pass TF32
+ *             products, error up to 12 times an FP32 FMA's) tests its
+ *             pivots against 12 * fp32_pivot_tol.
  *             Those subdomains also run the eigensolver's block products
  *             and orthogonalisation in FP64 (the others in double-single
  *             arithmetic and, for the first pass, FP32).
@@ -192,7 +195,21 @@ typedef struct {
  *  factor_kernel  GENEO_PREC_FP32 only: 0 (default) factors the bands on the
  *             fifth-generation tensor cores (tcgen05 MMAs, TMEM accumulators,
  *             tensor-map copies) when the batch's half bandwidth fits that
- *             kernel (up to 640); 1 always uses the warp-level MMA kernel.
+ *             kernel; 1 always uses the warp-level MMA kernel.
+ *  autotune   1 (default): at the end of the first setup of each batch
+ *             shape (precision, largest A_j band width and order, number of
+ *             subdomains) in the process, the preconditioner's local solve
+ *             is timed at each pipeline depth on a scratch vector and the
+ *             fastest is kept for every later apply (reported in
+ *             geneo_coarse_info_t.local_solve_stages); 0: the depth follows
+ *             from shared memory alone.
+ *  factor_bf16  GENEO_PREC_FP32 only, a precision study: 1 rounds the
+ *             equilibrated matrices and every factor panel to BF16 (the
+ *             fifth-generation kernel's planes hold BF16 values exactly),
+ *             so the local solves and the eigensolver's shift-and-invert
+ *             operator use BF16 factors (stored in FP32); matrices with a
+ *             pivot at or below fp32_pivot_tol are factored in FP64 as in
+ *             FP32 mode.  Widths the kernel does not take stay FP32.
  *  reserved   must be 0.
  */
 typedef struct {
@@ -218,6 +235,8 @@ typedef struct {
   int32_t deterministic;
   int32_t eig_solve_tf32;
   int32_t factor_kernel;
+  int32_t autotune;
+  int32_t factor_bf16;
   int32_t reserved;
 } geneo_options_t;
 
@@ -301,6 +320,9 @@ typedef struct {
   double prof_flops[GENEO_PROF_COUNT];
   double prof_bytes[GENEO_PROF_COUNT];
   int64_t prof_launches[GENEO_PROF_COUNT];
+  int32_t local_solve_stages; /* pipeline depth of the local solve (2-4) the
+                                autotuner chose; 0 if it did not run */
+  int32_t reserved;
 } geneo_coarse_info_t;
 
 

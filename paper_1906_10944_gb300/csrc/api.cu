@@ -143,6 +143,7 @@ geneo_status_t setup_impl(geneo_handle_s* h, const geneo_problem_t* p, cudaStrea
   GENEO_TRY(geneo::refactor_weak_A(h, asmb, tmp, s));
   GENEO_TRY(geneo::alloc_solver(h));
   GENEO_TRY(geneo::check_status(h, s));
+  if (h->opt.autotune) GENEO_TRY(geneo::tune_local_solve(h));
   h->setup_ms[7] = ms_since(t_all);
   h->prof.collect();
   return GENEO_OK;
@@ -172,6 +173,8 @@ void geneo_default_options(geneo_options_t* o) {
   o->deterministic = 1;
   o->eig_solve_tf32 = 0;
   o->factor_kernel = 0;
+  o->autotune = 1;
+  o->factor_bf16 = 0;
   o->reserved = 0;
 }
 
@@ -195,7 +198,7 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
       (o.pu_kind != GENEO_PU_STANDARD && o.pu_kind != GENEO_PU_SARKIS) ||
       (o.eig_strict != 0 && o.eig_strict != 1) || (o.deterministic != 0 && o.deterministic != 1) ||
       (o.eig_solve_tf32 != 0 && o.eig_solve_tf32 != 1) || (o.factor_kernel != 0 && o.factor_kernel != 1) ||
-      o.reserved != 0)
+      (o.autotune != 0 && o.autotune != 1) || (o.factor_bf16 != 0 && o.factor_bf16 != 1) || o.reserved != 0)
     return GENEO_ERR_ARG;
   // keep freed device memory in the stream-ordered pool for the next setup
   {
@@ -330,6 +333,7 @@ geneo_status_t geneo_query(geneo_handle_t h, geneo_coarse_info_t* info) {
   info->fp64_ortho = h->eig_o64;
   info->eig_unconverged = h->eig_unconv;
   info->factor_classes = h->factor_classes;
+  info->local_solve_stages = h->local_stages;
   info->device_bytes = h->mem.bytes;
   for (int i = 0; i < 8; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->factor_flops = h->factor_flops;

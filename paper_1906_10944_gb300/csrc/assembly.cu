@@ -484,8 +484,8 @@ struct FactorBatch {
 // band to more than 1/0.6 of its own width (rounded up to 32), each class
 // with its own tiled-band planes; the widths it does not take form one
 // batch for the older kernels.  Without the kernel: one batch.
-geneo_status_t factor_batches(const std::vector<BandDesc>& sorted, bool tc5_on, DevMem& tmp, cudaStream_t s,
-                              std::vector<FactorBatch>& out) {
+geneo_status_t factor_batches(const std::vector<BandDesc>& sorted, bool tc5_on, bool bf16, DevMem& tmp,
+                              cudaStream_t s, std::vector<FactorBatch>& out) {
   out.clear();
   std::vector<std::vector<BandDesc>> groups;
   std::vector<BandDesc> rest;
@@ -525,7 +525,10 @@ geneo_status_t factor_batches(const std::vector<BandDesc>& sorted, bool tc5_on, 
     GENEO_TRY(tmp.get(&fb.d, fb.h.size()));
     GENEO_CUDA(cudaMemcpyAsync(fb.d, fb.h.data(), sizeof(BandDesc) * fb.h.size(), cudaMemcpyHostToDevice, s));
     const bool is_rest = tc5_on && gi + 1 == groups.size() && !rest.empty();
-    if (tc5_on && !is_rest) GENEO_TRY(tc5_prepare(fb.h.data(), (int)fb.h.size(), fb.maxw, tmp, s, &fb.plan));
+    if (tc5_on && !is_rest) {
+      GENEO_TRY(tc5_prepare(fb.h.data(), (int)fb.h.size(), fb.maxw, tmp, s, &fb.plan));
+      fb.plan.bf16 = bf16;
+    }
     out.push_back(std::move(fb));
   }
   return GENEO_OK;
@@ -781,8 +784,9 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   // W), their tiled-band planes allocated on the main stream before the fork
   std::vector<FactorBatch> batK, batA;
   const bool tc5_on = h->fp32 && h->opt.factor_kernel != 1;
-  GENEO_TRY(factor_batches(bkf, tc5_on, tmp, s, batK));
-  GENEO_TRY(factor_batches(baf, tc5_on, tmp, s, batA));
+  const bool bf16 = h->fp32 && h->opt.factor_bf16;
+  GENEO_TRY(factor_batches(bkf, tc5_on || bf16, bf16, tmp, s, batK));
+  GENEO_TRY(factor_batches(baf, tc5_on || bf16, bf16, tmp, s, batA));
   // K_j on the main stream, A_j concurrently on the auxiliary stream
   GENEO_CUDA(cudaEventRecord(h->ev_fork, s));
   GENEO_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));

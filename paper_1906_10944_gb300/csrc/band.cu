@@ -421,25 +421,20 @@ k_band_dinv(T* __restrict__ base, const BandDesc* __restrict__ descs) {
 // panel's own rows (staged once per panel) and the rows r (streamed in
 // chunks of 16 by bulk copies, two buffers).  For each chunk's 16 x 32 tile
 // every warp takes an eighth of the k range and accumulates it with m16n8k8
-// TF32 MMAs in three passes (hi*hi + hi*lo + lo*hi with x = hi + lo,
-// hi = tf32(x)), which keeps about FP32 accuracy; the eight partial tiles go
+// TF32 MMAs in three passes (hi*hi + hi*lo + lo*hi with x = hi + lo, both
+// TF32, split_tf32_rn), which keeps close to FP32 accuracy; the eight partial tiles go
 // to one of two shared buffers and are summed in a fixed order while the next
 // chunk multiplies (one block barrier per chunk).  Then the 32 x 32 diagonal
 // block is factored by one warp in registers and the rows below by
 // substitution, one row per thread.  Only the panel columns are written; the
 // trailing window is never rewritten.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-// x = hi + lo with hi the TF32 truncation of x (low 13 mantissa bits
-// cleared); the MMA reads the TF32 bits of lo the same way, so the product
-// error is of the order of the dropped lo * lo term
+// x = hi + lo, both TF32 (split_tf32_rn), as the MMA's operand bits
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = __float_as_uint(x) & 0xffffe000u;
-  lo = __float_as_uint(x - __uint_as_float(hi));
+  float h, l;
+  split_tf32_rn(x, h, l);
+  hi = __float_as_uint(h);
+  lo = __float_as_uint(l);
 }
 __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -1593,7 +1588,7 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
         k_band_equil_s<T><<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(base, d_desc); note_launch();
         GENEO_CUDA(cudaGetLastError());
       }
-      GENEO_TRY(tc5_factor(*tc5, base, d_desc, st, s, weak, weak_tol));
+      GENEO_TRY(tc5_factor(*tc5, base, d_desc, st, s, weak, weak_tol * kTf32PivotScale));
       if (max_n > 0) {
         const int nb = (max_n + 15) / 16;
         k_band_dinv<T><<<dim3((nb + 15) / 16, count), 256, 0, s>>>(base, d_desc); note_launch();
@@ -1613,7 +1608,8 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
     const size_t tc_smem = potrf_tc_smem(max_w);
     if (tc_smem <= 227 * 1024) {
       GENEO_CUDA(allow_smem(k_band_potrf_tc));
-      k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st, weak, weak_tol); note_launch();
+      k_band_potrf_tc<<<count, kThreads, tc_smem, s>>>(base, d_desc, st, weak, weak_tol * kTf32PivotScale);
+      note_launch();
       GENEO_CUDA(cudaGetLastError());
       if (max_n > 0) {
         const int nb = (max_n + 15) / 16;
@@ -1808,7 +1804,8 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes) {
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
+                          int res_stages) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
   // One right-hand side (the preconditioner's local solves): two stages and
   // one register slot per warp keep the block small enough for several
@@ -1822,6 +1819,9 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
       const size_t budget = (sizeof(T) == 4 && count > 152) ? 112 * 1024 : 226 * 1024;
       int stages = 4;
       while (stages > 2 && res_smem<T>(max_w, max_n, 16, stages) > budget) --stages;
+      // a depth chosen by the autotuner (solve.cu) when it fits
+      if (res_stages >= 2 && res_stages <= 4 && res_smem<T>(max_w, max_n, 16, res_stages) <= 227 * 1024)
+        stages = res_stages;
       const size_t smem = res_smem<T>(max_w, max_n, 16, stages);
       if (smem <= 227 * 1024) {
         auto kern = stages == 4 ? k_band_solve_res<T, 4>
@@ -1873,9 +1873,9 @@ template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, int
                                           cudaStream_t, bool, int32_t*, float, const Tc5Plan*);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
-                                           DevStatus*, cudaStream_t, int, int);
+                                           DevStatus*, cudaStream_t, int, int, int);
 template geneo_status_t band_solve<float>(const float*, const BandDesc*, int, int, double*,
                                           const int64_t*, int, const int32_t*, const int32_t*,
-                                          DevStatus*, cudaStream_t, int, int);
+                                          DevStatus*, cudaStream_t, int, int, int);
 
 }  // namespace geneo

@@ -12,10 +12,9 @@
 // rounded up to 32, row-major.  Entries outside the band are zero and stay
 // zero.  In this layout the columns [c - W, c) of any row block form a plain
 // 2D box, so the panel update of a left-looking Cholesky is a sequence of
-// boxed tiles.  Each value x is kept in two planes, hi = x with the low 13
-// mantissa bits cleared (a TF32 value) and lo = x - hi (exact), so the
-// three-pass TF32 product hi*hi + hi*lo + lo*hi, about FP32 accuracy, needs no
-// splitting on chip.  The row blocks of a whole batch form one 3D tensor
+// boxed tiles.  Each value x is kept in two planes, hi and lo, both TF32
+// (split_tf32_rn), so the three-pass TF32 product hi*hi + hi*lo + lo*hi
+// (error at most 3 * 2^-22 of the product) needs no splitting on chip.  The row blocks of a whole batch form one 3D tensor
 // (x: W + 32 columns, y: 32 rows, z: row block) described by two tensor maps
 // (hi, lo) with 128-byte swizzle, the layout the MMA descriptors read.
 //
@@ -26,7 +25,12 @@
 // block I: box x = 32 (J + q - I), negative x reads zeros) and B(q) = row
 // block J at box x = 32 q.  Each tile is four K = 8 steps times three passes
 // of tcgen05.mma kind::tf32.  Tiles whose row blocks all lie outside the
-// band (4 h > q) are skipped.  Thread 0 issues the copies and thread 32 the
+// band (4 h > q) are skipped.  The tensor cores add each MMA's products into
+// the FP32 accumulator with truncation, a bias that grows with the number of
+// MMAs summed into one accumulator; so every chunk has 1 + P accumulators:
+// slot 0 takes the small terms (lo*hi + hi*lo), slot 1 + (q mod P) the
+// hi*hi terms of k-chunk q, and the panel threads add the slots in FP32
+// (small terms first).  Thread 0 issues the copies and thread 32 the
 // MMAs through a ring of kStages stages (full / empty mbarriers;
 // tcgen05.commit releases a stage and finally signals the accumulators).
 // Then every thread reads its TMEM lane (tcgen05.ld), forms U = A - D in
@@ -64,6 +68,7 @@ constexpr uint32_t kTileB5 = kBox5;            // 32 rows x 32 columns
 constexpr uint32_t kStageA5 = 2 * kTileA5;     // hi and lo of an A tile: 32 KB
 constexpr uint32_t kStageB5 = 2 * kTileB5;     // hi and lo of a B tile: 8 KB
 constexpr uint32_t kIdesc5 = umma_idesc_tf32(128, 32);
+constexpr int kMaxPar5 = 7;                    // at most this many hi*hi accumulators per chunk
 // afull, aempty, bfull, bempty, acc_full[2], acc_empty[2], pdone, fin
 constexpr int kBars5 = 2 * kStA5 + 2 * kStB5 + 2 + 2 + 2;
 
@@ -92,9 +97,24 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 
 __device__ __forceinline__ bool finite_pos5(float v) { return v > 0.f && isfinite(v); }
 
+// x into the two planes: hi = x rounded to TF32, lo = x - hi rounded to
+// TF32 (split_tf32_rn); with bf16 = 1 the value is first rounded to BF16 (to nearest, ties
+// to even, by integer arithmetic on the bit pattern), which a TF32 plane
+// holds exactly, and lo is 0 (the factor then holds BF16 values)
+__device__ __forceinline__ void split5(float x, int bf16, float& h, float& l) {
+  if (bf16) {
+    uint32_t u = __float_as_uint(x);
+    if (isfinite(x)) u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    h = __uint_as_float(u);
+    l = 0.f;
+  } else {
+    split_tf32_rn(x, h, l);
+  }
+}
+
 // Warp-specialised: warp 8 (one lane) streams the tiles of panel after
-// panel, warp 9 (one lane) issues the MMAs into one of two TMEM
-// accumulators (panel J uses buffer J % 2), and warps 0-7 run the panel
+// panel, warp 9 (one lane) issues the MMAs into one of nbuf (1 or 2) TMEM
+// accumulator buffers (panel G uses buffer G % nbuf), and warps 0-7 run the panel
 // steps.  A tiles go through a ring of kStA5 stages, the B tile of each
 // k-chunk (shared by the chunk's row tiles) through a ring of kStB5.  The
 // tiles of panel J + 1 that do not read panel J's columns (all k-chunks but
@@ -107,10 +127,12 @@ __global__ void __launch_bounds__(kT5, 1)
 k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  float* __restrict__ phi, float* __restrict__ plo, const BandDesc* __restrict__ descs,
                  const int64_t* __restrict__ zoff, int count, int32_t* __restrict__ queue, int W,
-                 uint32_t tmem_cols, DevStatus* st, int32_t* __restrict__ weak, float weak_tol) {
+                 uint32_t tmem_cols, int nbuf, int P, DevStatus* st, int32_t* __restrict__ weak, float weak_tol,
+                 int bf16) {
   const int Wt = W + kPB5;
-  const int QW = W / kPB5;                 // k-chunks in a full window
-  const uint32_t bufcols = tmem_cols / 2;  // columns of one accumulator buffer
+  const int QW = W / kPB5;                    // k-chunks in a full window
+  const uint32_t bufcols = tmem_cols / nbuf;  // columns of one accumulator buffer
+  const uint32_t chcols = 32u * (1 + P);      // columns of one chunk's accumulators
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -218,11 +240,11 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
           const int nh = ((R + 31) / 32 + 3) / 4;
           const int q0 = max(0, QW - J);
           const int G = pb + J;  // panel index over this CTA's matrices
-          const int b = G & 1;
-          if (G >= 2 && !*abort) wait5(&acc_empty[b], ((G >> 1) - 1) & 1, abort, st, d.id, c0);
+          const int b = G % nbuf;
+          if (G >= nbuf && !*abort) wait5(&acc_empty[b], ((G / nbuf) - 1) & 1, abort, st, d.id, c0);
           tc_fence_after();
           const uint32_t dbuf = tmem + (uint32_t)b * bufcols;
-          uint32_t inited = 0;
+          uint64_t inited = 0;  // bit (1 + P) hh + slot: accumulator written
           for (int q = q0; q < QW; ++q, ++tb) {
             const uint32_t sb = tb % kStB5;
             const bool bok = !*abort && wait5(&bfull[sb], (tb / kStB5) & 1, abort, st, d.id, c0);
@@ -233,19 +255,21 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
               if (!bok || *abort || !wait5(&afull[sa], (ta / kStA5) & 1, abort, st, d.id, c0)) continue;
               tc_fence_after();
               const uint32_t asa = smem_u32(stA + sa * kStageA5);
-              const uint32_t dt = dbuf + 32u * hh;
+              const int ss = 1 + q % P;  // the hi*hi slot of this k-chunk
+              const int bs = (1 + P) * hh, bb = bs + ss;
+              const uint32_t ds = dbuf + chcols * hh, db = ds + 32u * ss;
+              const uint32_t acs = (uint32_t)((inited >> bs) & 1u), acb = (uint32_t)((inited >> bb) & 1u);
   #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t ah = umma_desc_sw128(asa + 32 * kk);
                 const uint64_t al = umma_desc_sw128(asa + kTileA5 + 32 * kk);
                 const uint64_t bh = umma_desc_sw128(bsa + 32 * kk);
                 const uint64_t bl = umma_desc_sw128(bsa + kTileB5 + 32 * kk);
-                const uint32_t acc = ((inited >> hh) & 1u) | (kk > 0 ? 1u : 0u);
-                umma_tf32(dt, al, bh, kIdesc5, acc);
-                umma_tf32(dt, ah, bl, kIdesc5, 1u);
-                umma_tf32(dt, ah, bh, kIdesc5, 1u);
+                umma_tf32(ds, al, bh, kIdesc5, acs | (kk > 0 ? 1u : 0u));
+                umma_tf32(ds, ah, bl, kIdesc5, 1u);
+                umma_tf32(db, ah, bh, kIdesc5, acb | (kk > 0 ? 1u : 0u));
               }
-              inited |= 1u << hh;
+              inited |= (1ull << bs) | (1ull << bb);
               umma_commit(&aempty[sa]);
             }
             if (bok) umma_commit(&bempty[sb]);  // the k-chunk's row tiles are all issued
@@ -262,7 +286,7 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         const int nh = ((R + 31) / 32 + 3) / 4;
         const int q0 = max(0, QW - J);
         const int G = pb + J;
-        const int buf = G & 1;
+        const int buf = G % nbuf;
         // the panel's entries of A (both planes) into Us: eight lanes per row,
         // four columns each (16-byte loads), four row groups of 32 rows per
         // batch in flight; entries outside the band are zero in the planes
@@ -295,17 +319,27 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
             }
           }
         }
-        if (!*abort) wait5(&acc_full[buf], (G >> 1) & 1, abort, st, d.id, c0);
+        if (!*abort) wait5(&acc_full[buf], (G / nbuf) & 1, abort, st, d.id, c0);
         tc_fence_after();
         epi_sync();
         // U = A - D.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 of the
         // chunks h = w / 4, w / 4 + 2, ...; chunk h holds data when one of its
-        // tiles was multiplied (some k-chunk q >= 4 h exists)
+        // tiles was multiplied (some k-chunk q >= 4 h exists), and its hi*hi
+        // slot 1 + r when one of those q has q mod P = r.  D = small terms +
+        // the hi*hi slots, summed in FP32.
         __syncwarp();
         for (int hh = wid >> 2; hh < nh; hh += 2) {
-          if (!(q0 < QW && 4 * hh <= QW - 1)) continue;
-          float dv[32];
-          tmem_ld32(tmem + (uint32_t)buf * bufcols + ((uint32_t)(32 * (wid & 3)) << 16) + 32u * hh, dv);
+          const int qlo = max(q0, 4 * hh);
+          if (qlo >= QW) continue;
+          const uint32_t ta0 = tmem + (uint32_t)buf * bufcols + ((uint32_t)(32 * (wid & 3)) << 16) + chcols * hh;
+          float dv[32], dt[32];
+          tmem_ld32(ta0, dv);
+          for (int r = 0; r < P; ++r) {
+            if (qlo + ((r - qlo % P) + P) % P >= QW) continue;  // no k-chunk of this parity
+            tmem_ld32(ta0 + 32u * (1 + r), dt);
+  #pragma unroll
+            for (int col = 0; col < 32; ++col) dv[col] += dt[col];
+          }
           const int row = 128 * hh + 32 * (wid & 3) + lane;
           if (row < R) {
             float* ur = Us + (size_t)row * kUS5;
@@ -393,10 +427,10 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
             const int64_t o = ((z0 + I) * 32 + (i & 31)) * (int64_t)Wt + (W - 32 * (I - J)) + cg;
             const float* ur = Us + (size_t)i * kUS5 + cg;
             float4 xh, xl;
-            xh.x = __uint_as_float(__float_as_uint(ur[0]) & 0xffffe000u); xl.x = ur[0] - xh.x;
-            xh.y = __uint_as_float(__float_as_uint(ur[1]) & 0xffffe000u); xl.y = ur[1] - xh.y;
-            xh.z = __uint_as_float(__float_as_uint(ur[2]) & 0xffffe000u); xl.z = ur[2] - xh.z;
-            xh.w = __uint_as_float(__float_as_uint(ur[3]) & 0xffffe000u); xl.w = ur[3] - xh.w;
+            split5(ur[0], bf16, xh.x, xl.x);
+            split5(ur[1], bf16, xh.y, xl.y);
+            split5(ur[2], bf16, xh.z, xl.z);
+            split5(ur[3], bf16, xh.w, xl.w);
             *reinterpret_cast<float4*>(phi + o) = xh;
             *reinterpret_cast<float4*>(plo + o) = xl;
           }
@@ -439,7 +473,7 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
 // equilibrated matrix S A S.
 __global__ void __launch_bounds__(256)
 k_tb_pack(const float* __restrict__ band, const BandDesc* __restrict__ descs, const int64_t* __restrict__ zoff,
-          int W, float* __restrict__ phi, float* __restrict__ plo) {
+          int W, float* __restrict__ phi, float* __restrict__ plo, int bf16) {
   const BandDesc d = descs[blockIdx.y];
   const int Wt = W + kPB5;
   const int lane = threadIdx.x & 31;
@@ -458,9 +492,10 @@ k_tb_pack(const float* __restrict__ band, const BandDesc* __restrict__ descs, co
         x = src[c - r + d.w];
         if (S) x *= sr * S[c];
       }
-      const float xh = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+      float xh, xl;
+      split5(x, bf16, xh, xl);
       phi[o + xx] = xh;
-      plo[o + xx] = x - xh;
+      plo[o + xx] = xl;
     }
   }
 }
@@ -516,10 +551,27 @@ bool encode_tb_map(CUtensorMap* m, float* base, int W, int64_t Z) {
 
 }  // namespace
 
+// TMEM layout of the accumulators for nh 128-row chunks: two buffers when
+// each buffer can hold at least one hi*hi slot next to the small-term slot,
+// else one; then as many hi*hi slots per chunk (P <= kMaxPar5) as the 512
+// columns allow.  False when not even one buffer with P = 1 fits.
+bool tc5_acc_layout(int nh, int* nbuf, int* P) {
+  for (int nb = 2; nb >= 1; --nb) {
+    const int slots = 512 / (nb * 32 * nh);  // 1 + P
+    if (slots >= 2) {
+      *nbuf = nb;
+      *P = std::min(kMaxPar5, slots - 1);
+      return true;
+    }
+  }
+  return false;
+}
+
 bool tc5_fits(int w) {
   const int W = (w + 31) & ~31;
   const int nh = (kPB5 + W + 127) / 128;
-  return W >= kPB5 && tc5_smem(W) <= 227 * 1024 && 2 * 32 * nh <= 512;
+  int nb = 0, P = 0;
+  return W >= kPB5 && tc5_smem(W) <= 227 * 1024 && tc5_acc_layout(nh, &nb, &P);
 }
 
 geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
@@ -530,8 +582,10 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   const size_t smem = tc5_smem(W);
   if (W < kPB5 || smem > 227 * 1024) return GENEO_OK;  // the older kernels take it
   const int nh = (kPB5 + W + 127) / 128;
+  int nbuf = 0, P = 0;
+  if (!tc5_acc_layout(nh, &nbuf, &P)) return GENEO_OK;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * 32 * nh)) cols <<= 1;  // two accumulator buffers
+  while (cols < (uint32_t)(nbuf * 32 * nh * (1 + P))) cols <<= 1;
   if (cols > 512) return GENEO_OK;
   std::vector<int64_t> zo(count);
   int64_t Z = 0;
@@ -551,6 +605,8 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   GENEO_CUDA(cudaMemcpyAsync(p->dz, zo.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, s));
   p->W = W;
   p->cols = cols;
+  p->nbuf = nbuf;
+  p->par = P;
   p->smem = smem;
   p->count = count;
   p->max_n = max_n;
@@ -560,8 +616,9 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
 
 geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc, DevStatus* st, cudaStream_t s,
                           int32_t* weak, float weak_tol) {
+  const int bf16 = p.bf16 ? 1 : 0;
   const dim3 gp((unsigned)std::min(64, (p.max_n + 7) / 8), (unsigned)p.count);
-  k_tb_pack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo); note_launch();
+  k_tb_pack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo, bf16); note_launch();
   GENEO_CUDA(cudaGetLastError());
   GENEO_CUDA(allow_smem(k_band_potrf_tc5));
   // persistent CTAs, one per SM (the shared memory allows no more), taking
@@ -571,7 +628,8 @@ geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc,
   GENEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   GENEO_CUDA(cudaMemsetAsync(p.queue, 0, sizeof(int32_t), s));
   k_band_potrf_tc5<<<std::min(p.count, sms), kT5, p.smem, s>>>(p.mhi, p.mlo, p.phi, p.plo, d_desc, p.dz, p.count,
-                                                                p.queue, p.W, p.cols, st, weak, weak_tol);
+                                                                p.queue, p.W, p.cols, p.nbuf, p.par, st, weak,
+                                                                weak_tol, bf16);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
   k_tb_unpack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo); note_launch();

@@ -206,6 +206,26 @@ __device__ T block_sum(T v, T* red) {
   return r;
 }
 
+// x = hi + lo for three-pass TF32 tensor-core products: hi = x rounded to
+// TF32 (10 explicit mantissa bits, to nearest), lo = x - hi (exact in FP32)
+// rounded to TF32 too, so both are exact MMA operands.  hi*y_hi + hi*y_lo +
+// lo*y_hi then differs from x*y by the dropped lo*y_lo and the two roundings
+// of lo: at most 3 * 2^-22 |x y|, of either sign (no bias from truncation).
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split_tf32_rn(float x, float& hi, float& lo) {
+  hi = tf32_rn(x);
+  lo = tf32_rn(x - hi);
+}
+// A matrix factored with those products is sent to FP64 when a pivot is at
+// or below this multiple of the FP32 pivot tolerance: the tolerance stands
+// for (condition) x (unit roundoff), and the product error bound above is
+// 12 times an FP32 FMA's 2^-24.
+constexpr float kTf32PivotScale = 12.f;
+
 // SplitMix64 (Steele, Lea, Flood 2014): counter -> 64 random bits.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -292,12 +312,15 @@ struct Tc5Plan {
   CUtensorMap mhi, mlo;
   bool ok = false;
   int W = 0, count = 0, max_n = 0;
-  uint32_t cols = 0;
+  uint32_t cols = 0;  // TMEM columns allocated
+  int nbuf = 0;       // accumulator buffers (panels in flight)
+  int par = 0;        // hi*hi accumulators per 128-row chunk
   size_t smem = 0;
   float* phi = nullptr;
   float* plo = nullptr;
   int64_t* dz = nullptr;
   int32_t* queue = nullptr;  // work counter of the persistent launch
+  bool bf16 = false;         // factor values rounded to BF16 (precision study)
 };
 geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
                            Tc5Plan* p);
@@ -327,11 +350,13 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
 // max_n (largest matrix order, 0 if unknown) enables the one-right-hand-side
 // solve with the vector resident in shared memory.  tc_passes (FP32 factors,
 // several right-hand sides): 3 = each tensor-core product as three TF32
-// passes (about FP32 accuracy), 1 = one TF32 pass.
+// passes (about FP32 accuracy), 1 = one TF32 pass.  res_stages (one
+// right-hand side with the vector resident, 2-4; 0 = by shared memory): the
+// pipeline depth of that kernel, as an autotuner picked it.
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0,
-                          int tc_passes = 3);
+                          int tc_passes = 3, int res_stages = 0);
 
 }  // namespace geneo

@@ -49,6 +49,7 @@ struct geneo_handle_s {
   std::vector<uint8_t> a64;        // [N] 1: A_j factored in FP64
   int nK64 = 0;                    // the same count for K_j (setup only)
   int factor_classes = 0;          // FP32: factorisation batches (size classes) of K_j and A_j
+  int local_stages = 0;            // pipeline depth of the local solve picked by the autotuner
 
   // coarse space
   int dimH = 0, wH = 0;
@@ -152,6 +153,8 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& a, const doubl
 // matrix of CG coefficients a[0..m), b[0..m-1) (bisection; work d, e of m).
 double condition_estimate_fixed(const double* a, const double* b, int m, double* d, double* e);
 geneo_status_t alloc_solver(geneo_handle_s* h);
+// time the local solve's pipeline depths on this batch once per shape
+geneo_status_t tune_local_solve(geneo_handle_s* h);
 geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStream_t s);
 geneo_status_t pcg(geneo_handle_s* h, const double* b, double* x, double tol, int maxit,
                    geneo_solve_info_t* info, cudaStream_t s);

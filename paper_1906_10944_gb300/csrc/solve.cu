@@ -14,7 +14,9 @@
 // reproducible run to run.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "handle.cuh"
@@ -424,6 +426,70 @@ double condition_estimate_fixed(const double* a, const double* b, int m, double*
   return ext[1] / ext[0];
 }
 
+// Autotuner of the preconditioner's local solve (the one-right-hand-side
+// band solve with the vector resident in shared memory): each pipeline
+// depth (2, 3, 4 stages; deeper stages take more shared memory and so fewer
+// blocks per SM) is timed on this batch, on a scratch copy of the subdomain
+// vectors (one warm-up and three timed launches each, CUDA events), and the
+// fastest is kept for the process, keyed by (precision, largest band width,
+// largest order, batch size).  Runs once per key at the end of a setup.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+}  // namespace
+
+geneo_status_t tune_local_solve(geneo_handle_s* h) {
+  const auto key = std::make_tuple(h->fp32 ? 1 : 0, h->maxwA, h->maxnD, h->N);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h->local_stages = it->second;
+      return GENEO_OK;
+    }
+  }
+  cudaStream_t s = h->mem.stream;
+  DevMem tmp;
+  tmp.stream = s;
+  double* scratch = nullptr;
+  GENEO_TRY(tmp.get(&scratch, (size_t)std::max<int64_t>(h->sumN, 1)));
+  GENEO_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double) * h->sumN, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GENEO_CUDA(cudaEventCreate(&e0));
+  GENEO_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int stages = 2; stages <= 4; ++stages) {
+    auto run = [&]() -> geneo_status_t {
+      if (h->fp32)
+        return band_solve<float>((const float*)h->bandA, h->dbandA, h->N, h->maxwA, scratch, h->uoff, 1,
+                                 nullptr, nullptr, h->dstat, s, h->maxnD, 3, stages);
+      return band_solve<double>((const double*)h->bandA, h->dbandA, h->N, h->maxwA, scratch, h->uoff, 1,
+                                nullptr, nullptr, h->dstat, s, h->maxnD, 3, stages);
+    };
+    geneo_status_t st = run();
+    if (st != GENEO_OK) break;
+    GENEO_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3 && st == GENEO_OK; ++r) st = run();
+    GENEO_CUDA(cudaEventRecord(e1, s));
+    GENEO_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GENEO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (st == GENEO_OK && ms < best_ms) {
+      best_ms = ms;
+      best = stages;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  tmp.free_all();
+  h->local_stages = best;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  return GENEO_OK;
+}
+
 geneo_status_t alloc_solver(geneo_handle_s* h) {
   DevMem& M = h->mem;
   const int64_t n = h->n;
@@ -532,13 +598,13 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
   if (h->fp32) {
     GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                nullptr, nullptr, h->dstat, s, h->maxnD));
+                                nullptr, nullptr, h->dstat, s, h->maxnD, 3, h->local_stages));
     if (h->nA64)  // the A_j factored in FP64 (their FP32 descriptors have n = 0)
       GENEO_TRY(band_solve<double>(h->bandA64, h->dbandA64, h->nA64, h->maxwA64, h->u, h->uoff, 1,
                                    nullptr, nullptr, h->dstat, s, h->maxnA64));
   } else
     GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                 nullptr, nullptr, h->dstat, s, h->maxnD));
+                                 nullptr, nullptr, h->dstat, s, h->maxnD, 3, h->local_stages));
   h->prof.end(pl, s);
   if (h->dimH > 0 && !h->Hinv) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);

@@ -62,7 +62,8 @@ class geneo_options_t(C.Structure):
         ("profile", C.c_int32), ("first_nev", C.c_int32), ("seed", C.c_uint64),
         ("fp32_pivot_tol", C.c_double), ("pu_kind", C.c_int32), ("eig_strict", C.c_int32),
         ("deterministic", C.c_int32), ("eig_solve_tf32", C.c_int32),
-        ("factor_kernel", C.c_int32), ("reserved", C.c_int32),
+        ("factor_kernel", C.c_int32), ("autotune", C.c_int32),
+        ("factor_bf16", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -86,6 +87,7 @@ class geneo_coarse_info_t(C.Structure):
         ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
         ("prof_ms", C.c_double * NPROF), ("prof_flops", C.c_double * NPROF),
         ("prof_bytes", C.c_double * NPROF), ("prof_launches", C.c_int64 * NPROF),
+        ("local_solve_stages", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -232,7 +234,7 @@ def geneo_query(h):
             "eig_iterations": q.eig_iterations, "block_size": q.block_size,
             "fp64_factors_K": q.fp64_factors_K, "fp64_factors_A": q.fp64_factors_A,
             "fp64_ortho": q.fp64_ortho, "eig_unconverged": q.eig_unconverged,
-            "factor_classes": q.factor_classes,
+            "factor_classes": q.factor_classes, "local_solve_stages": q.local_solve_stages,
             "device_bytes": q.device_bytes, "setup_ms": list(q.setup_ms),
             "factor_flops": q.factor_flops, "factor_event_ms": q.factor_event_ms,
             "eigsolve_flops": q.eigsolve_flops, "eigsolve_event_ms": q.eigsolve_event_ms,
