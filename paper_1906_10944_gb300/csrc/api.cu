@@ -226,11 +226,19 @@ geneo_status_t geneo_setup(const geneo_problem_t* prob, const geneo_options_t* o
   if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_afac, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_afac, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->solve_streams.fork, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     geneo_destroy(h);
     return GENEO_ERR_CUDA;
   }
+  for (int i = 0; i < geneo::kSolveStreams; ++i)
+    if (cudaStreamCreateWithFlags(&h->solve_streams.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->solve_streams.ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      geneo_destroy(h);
+      return GENEO_ERR_CUDA;
+    }
   geneo_status_t st = setup_impl(h, prob, h->stream);
   if (st != GENEO_OK) {
     cudaStreamSynchronize(h->stream);
@@ -391,9 +399,16 @@ void geneo_destroy(geneo_handle_t h) {
   // the handle's memory goes back to the pool in the order of the stream of
   // its last call, after that call's work
   if (h->aux) cudaStreamSynchronize(h->aux);
+  for (int i = 0; i < geneo::kSolveStreams; ++i)
+    if (h->solve_streams.s[i]) cudaStreamSynchronize(h->solve_streams.s[i]);
   cudaStreamSynchronize(h->mem.stream);
   h->mem.free_all();
   cudaStreamSynchronize(h->mem.stream);
+  for (int i = 0; i < geneo::kSolveStreams; ++i) {
+    if (h->solve_streams.ev[i]) cudaEventDestroy(h->solve_streams.ev[i]);
+    if (h->solve_streams.s[i]) cudaStreamDestroy(h->solve_streams.s[i]);
+  }
+  if (h->solve_streams.fork) cudaEventDestroy(h->solve_streams.fork);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_afac) cudaEventDestroy(h->ev_afac);

@@ -1287,19 +1287,27 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
 //           sums added in a fixed order;
 //  backward (w x 16) x (16 x k): ring rows above the block minus L^T x, one
 //           16-row tile per warp at a time, the ring values as the MMA's C.
-// k <= 8 NT columns per launch; the ring row stride KP puts the four k-rows
-// of a B fragment in distinct eight-bank groups.
+// k <= 8 NT columns per launch.  The ring holds row r at slot r mod ring
+// (ring a power of two >= w + 2 SNB); its row stride RP puts the four
+// k-rows of a B fragment in distinct eight-bank groups: by padding (8, 24,
+// 40 values for NT = 1, 3, 4) or, for NT = 2, with 16 values and the column
+// halves swapped (column c at c ^ 8) on slots with bit 1 set.  With NT <= 2
+// the block is sized for two resident blocks per SM.
 template <int NT>
 struct MtcKP { static constexpr int v = NT == 1 ? 8 : (NT == 4 ? 40 : 24); };
+template <int NT>
+struct MtcRP { static constexpr int v = NT == 2 ? 16 : MtcKP<NT>::v; };
 
 template <int NT, int kStages, int PASSES>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, NT <= 2 ? 2 : 1)
 k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ descs,
                  double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
                  const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
                  DevStatus* st) {
   constexpr int SNB = 16;
-  constexpr int KP = MtcKP<NT>::v;
+  constexpr int KP = MtcKP<NT>::v;   // row stride of zb and of the partial sums
+  constexpr int RP = MtcRP<NT>::v;   // row stride of the ring
+  constexpr bool SWZ = NT == 2;
   constexpr int NW = kThreads / 32;
   const BandDesc d = descs[blockIdx.x];
   // vectors, counts and skip flags are indexed by the subdomain id (a
@@ -1315,14 +1323,15 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
   const float* L = base + d.off;
   const float* Dg = base + d.dinv;
   double* X = xbase + xoff[mi] + (int64_t)col0 * n;
-  const int rmask = ring - 1;  // ring: power of two >= w + 2 SNB
+  const int rmask = ring - 1;
+  auto slot = [&](int r) { return r & rmask; };
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);      // kStages
   float* stage = reinterpret_cast<float*>(smem_raw + 128);     // kStages * SNB * ld
   float* dstage = stage + (size_t)kStages * SNB * ld;          // kStages * 256
-  float* win = dstage + (size_t)kStages * 256;                 // ring * KP
-  float* red = win + (size_t)ring * KP;                        // NW * SNB * KP
+  float* win = dstage + (size_t)kStages * 256;                 // ring * RP
+  float* red = win + (size_t)ring * RP;                        // NW * SNB * KP
   float* zb = red + (size_t)NW * SNB * KP;                     // SNB * KP
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int g = lane >> 2, tg = lane & 3;
@@ -1330,7 +1339,11 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
   const int nvis = 2 * nb;
 
   // columns >= k stay zero in the ring and in zb
-  for (int idx = tid; idx < ring * KP; idx += kThreads) win[idx] = 0.f;
+  for (int idx = tid; idx < ring * RP; idx += kThreads) win[idx] = 0.f;
+  auto rptr = [&](int r, int c) -> float* {
+    const int sl = slot(r);
+    return win + (size_t)sl * RP + (SWZ ? (c ^ ((sl << 2) & 8)) : c);
+  };
   for (int idx = tid; idx < SNB * KP; idx += kThreads) zb[idx] = 0.f;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
@@ -1426,13 +1439,15 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
           uint32_t ah[4], al[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) split_tf32(x[q], ah[q], al[q]);
-          const float* r1 = win + (size_t)((kb - w + k1) & rmask) * KP + g;
-          const float* r2 = win + (size_t)((kb - w + k2) & rmask) * KP + g;
+          const int sl1 = slot(kb - w + k1), sl2 = slot(kb - w + k2);
+          const float* r1 = win + (size_t)sl1 * RP + g;
+          const float* r2 = win + (size_t)sl2 * RP + g;
+          const int x1 = SWZ ? ((sl1 >> 1) & 1) : 0, x2 = SWZ ? ((sl2 >> 1) & 1) : 0;
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             uint32_t bh[2], bl[2];
-            split_tf32(r1[8 * nt], bh[0], bl[0]);
-            split_tf32(r2[8 * nt], bh[1], bl[1]);
+            split_tf32(r1[8 * (nt ^ x1)], bh[0], bl[0]);
+            split_tf32(r2[8 * (nt ^ x2)], bh[1], bl[1]);
             if (PASSES == 3) {
               mma_tf32(acc[nt][0], al, bh);
               mma_tf32(acc[nt][1], ah, bl);
@@ -1466,7 +1481,7 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
 #pragma unroll
           for (int t = 0; t < SNB; ++t)
             if (t <= i) y += D[t * SNB + i] * zb[t * KP + c];
-          win[(size_t)((kb + i) & rmask) * KP + c] = y;
+          *rptr(kb + i, c) = y;
           X[(int64_t)c * n + kb + i] = (double)y;
         }
       }
@@ -1488,7 +1503,7 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
 #pragma unroll
           for (int j = 0; j < SNB; ++j) {
             const int i = (t + j) & (SNB - 1);  // rotated: conflict-free reads of M
-            if (i >= t && i < b) x += D[t * SNB + i] * win[(size_t)((kb + i) & rmask) * KP + c];
+            if (i >= t && i < b) x += D[t * SNB + i] * *rptr(kb + i, c);
           }
           X[(int64_t)c * n + kb + t] = Sg ? (double)(x * Sg[kb + t]) : (double)x;
         }
@@ -1513,10 +1528,8 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             const int col = 8 * nt + 2 * tg;
-            const float2 ya = ra < kb ? *reinterpret_cast<const float2*>(win + (size_t)(ra & rmask) * KP + col)
-                                      : make_float2(0.f, 0.f);
-            const float2 yb = rb < kb ? *reinterpret_cast<const float2*>(win + (size_t)(rb & rmask) * KP + col)
-                                      : make_float2(0.f, 0.f);
+            const float2 ya = ra < kb ? *reinterpret_cast<const float2*>(rptr(ra, col)) : make_float2(0.f, 0.f);
+            const float2 yb = rb < kb ? *reinterpret_cast<const float2*>(rptr(rb, col)) : make_float2(0.f, 0.f);
             cacc[nt][0] = ya.x; cacc[nt][1] = ya.y; cacc[nt][2] = yb.x; cacc[nt][3] = yb.y;
           }
 #pragma unroll
@@ -1545,15 +1558,15 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             const int col = 8 * nt + 2 * tg;
-            if (ra < kb) *reinterpret_cast<float2*>(win + (size_t)(ra & rmask) * KP + col) = make_float2(cacc[nt][0], cacc[nt][1]);
-            if (rb < kb) *reinterpret_cast<float2*>(win + (size_t)(rb & rmask) * KP + col) = make_float2(cacc[nt][2], cacc[nt][3]);
+            if (ra < kb) *reinterpret_cast<float2*>(rptr(ra, col)) = make_float2(cacc[nt][0], cacc[nt][1]);
+            if (rb < kb) *reinterpret_cast<float2*>(rptr(rb, col)) = make_float2(cacc[nt][2], cacc[nt][3]);
           }
         }
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
-        if (c < k && t < lo - nlo) win[(size_t)((nlo + t) & rmask) * KP + c] = er[e];
+        if (c < k && t < lo - nlo) *rptr(nlo + t, c) = er[e];
       }
       lo = nlo;
     }
@@ -1703,13 +1716,17 @@ geneo_status_t launch_multi(int CT, int stages, int count, size_t smem, cudaStre
   return GENEO_ERR_ARG;
 }
 
-// Shared memory of the tensor-core multi-right-hand-side solve.
+// Shared memory of the tensor-core multi-right-hand-side solve (ring and
+// partial-sum strides as in MtcRP / MtcKP).
 inline size_t mtc_smem(int max_w, int ring, int NT, int stages) {
   const int ld = band_ld(max_w);
   const int KP = NT == 1 ? 8 : (NT == 4 ? 40 : 24);
-  return 128 + sizeof(float) * ((size_t)stages * (16 * ld + 256) + (size_t)ring * KP +
+  const int RP = NT == 2 ? 16 : KP;
+  return 128 + sizeof(float) * ((size_t)stages * (16 * ld + 256) + (size_t)ring * RP +
                                 (size_t)(kThreads / 32 + 1) * 16 * KP);
 }
+// Shared memory per block that still lets two blocks share an SM.
+constexpr size_t kTwoPerSm = 112 * 1024;
 
 template <int NT, int kStages, int PASSES>
 geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float* base, const BandDesc* d_desc,
@@ -1842,8 +1859,13 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
         int NT = (kc + 7) / 8;
         while (NT > 1 && mtc_smem(max_w, ring, NT, 2) > 227 * 1024) --NT;
         const int kk = std::min(kc, 8 * NT);
+        // the deepest pipeline that keeps two blocks per SM when the batch
+        // fills more than one wave of single blocks (NT <= 2), else the
+        // deepest that fits
         int stages = 4;
-        while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > 227 * 1024) --stages;
+        const size_t cap = (NT <= 2 && count > 152 && mtc_smem(max_w, ring, NT, 2) <= kTwoPerSm) ? kTwoPerSm
+                                                                                                : 227 * 1024;
+        while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > cap) --stages;
         GENEO_TRY(launch_mtc(NT, stages, tc_passes, count, mtc_smem(max_w, ring, NT, stages), s, base,
                              d_desc, xbase, xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
         if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch

@@ -359,4 +359,40 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0,
                           int tc_passes = 3, int res_stages = 0);
 
+// solve_set.cu
+// A batch of band factors cut into classes of similar half bandwidth for
+// band_solve (each class launched with its own widest band and longest
+// vector), the classes spread over lanes: lane 0 = the caller's stream,
+// lane l > 0 = SolveStreams::s[l - 1].
+struct SolveClass {
+  const void* base = nullptr;  // float or double band storage
+  bool f64 = false;
+  BandDesc* d = nullptr;       // the class's descriptors (device), largest sweep first
+  int count = 0, max_w = 0, max_n = 0;
+  double cost = 0.0;           // bytes of one forward and backward sweep over the class
+  int lane = 0;
+};
+struct SolveSet {
+  std::vector<SolveClass> cls;
+  int lanes = 1;
+};
+constexpr int kSolveStreams = 4;
+struct SolveStreams {
+  cudaStream_t s[kSolveStreams] = {};
+  cudaEvent_t ev[kSolveStreams] = {};
+  cudaEvent_t fork = nullptr;
+};
+// The classes of the band batch (base, f64, d_desc, count) and, in FP32 mode,
+// of the FP64 refactorisations (base64, d_desc64, count64; may be empty);
+// descriptors with n = 0 are left out.  Device descriptor arrays come from
+// mem; the call synchronises s once (it reads the descriptors back).
+geneo_status_t make_solve_set(const void* base, bool f64, const BandDesc* d_desc, int count,
+                              const double* base64, const BandDesc* d_desc64, int count64, DevMem& mem,
+                              cudaStream_t s, SolveSet* out);
+// band_solve over every class, ordered after the work already on s; the
+// work of every lane is joined back into s before the call returns.
+geneo_status_t solve_set_run(const SolveSet& ss, const SolveStreams& pool, double* xbase, const int64_t* xoff,
+                             int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev, DevStatus* st,
+                             cudaStream_t s, int tc_passes = 3, int res_stages = 0);
+
 }  // namespace geneo

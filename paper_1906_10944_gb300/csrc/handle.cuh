@@ -10,6 +10,8 @@ struct geneo_handle_s {
   cudaStream_t aux = nullptr;       // second stream (coarse solve, concurrent factorisations)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_afac = nullptr;   // end of the A_j factorisation on the aux stream
+  geneo::SolveStreams solve_streams;  // lanes of the size-class band solves
+  geneo::SolveSet setA;               // the A_j factors in size classes (local solves)
   geneo_options_t opt{};
   bool fp32 = false;
 

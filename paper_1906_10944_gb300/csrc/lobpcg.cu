@@ -282,7 +282,10 @@ __global__ void k_build_ell(const SubDesc* __restrict__ sub, const int64_t* __re
 
 // Y1 = V1 X (and Y2 = V2 X when v2 is given) in double-single arithmetic from
 // the ELLPACK layout, results stored in FP64; one row per thread, four
-// columns per pass.  Each entry and operand value is one 8-byte (hi, lo) load.
+// columns per pass (more columns per pass cost occupancy, which this
+// gather-bound loop needs more), the entry loop unrolled three times so that
+// the loads of several entries are in flight before their gathers.  Each
+// entry and operand value is one 8-byte (hi, lo) load.
 __global__ void __launch_bounds__(kT)
 k_spmm_ds(const SubDesc* __restrict__ sub, int L, const int32_t* __restrict__ ecol,
           const float2* __restrict__ v1, const float2* __restrict__ v2, ColRefT<float2> X2, ColRef Y1,
@@ -298,19 +301,21 @@ k_spmm_ds(const SubDesc* __restrict__ sub, int L, const int32_t* __restrict__ ec
   double* y2 = v2 ? cr_ptr(Y2, d, j) : nullptr;
   const int64_t nn = d.nN;
   const int64_t base = d.offN * (int64_t)L + a;
-  for (int c = 0; c < w; c += 4) {
-    const int nc = min(4, w - c);
-    DS s1[4], s2[4];
+  constexpr int CP = 4;
+  for (int c = 0; c < w; c += CP) {
+    const int nc = min(CP, w - c);
+    DS s1[CP], s2[CP];
 #pragma unroll
-    for (int z = 0; z < 4; ++z) s1[z] = s2[z] = DS{0.f, 0.f};
+    for (int z = 0; z < CP; ++z) s1[z] = s2[z] = DS{0.f, 0.f};
     const float2* xc = x2 + (int64_t)c * nn;
+#pragma unroll 3
     for (int t = 0; t < L; ++t) {
       const int64_t o = base + (int64_t)t * nn;
       const int col = ecol[o];
       const float2 va = v1[o];
       const float2 vb = v2 ? v2[o] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int z = 0; z < 4; ++z) {
+      for (int z = 0; z < CP; ++z) {
         if (z < nc) {
           const float2 xv = xc[z * nn + col];
           ds_fma(s1[z], va.x, va.y, xv.x, xv.y);
@@ -319,7 +324,7 @@ k_spmm_ds(const SubDesc* __restrict__ sub, int L, const int32_t* __restrict__ ec
       }
     }
 #pragma unroll
-    for (int z = 0; z < 4; ++z) {
+    for (int z = 0; z < CP; ++z) {
       if (z < nc) {
         y1[(c + z) * nn + a] = acc_value(s1[z]);
         if (v2) y2[(c + z) * nn + a] = acc_value(s2[z]);
@@ -1427,18 +1432,14 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   std::vector<double> kflops(N);
   for (int j = 0; j < N; ++j) kflops[j] = band_solve_flops(h->hsub[j].nN, h->hsub[j].wK);
   h->eig_flops = 0.0;
+  // the K_j factors (FP32 and FP64 refactorisations) in size classes
+  SolveSet setK;
+  GENEO_TRY(make_solve_set(asmb.bandK, !f32, asmb.dbandK, N, f32 ? asmb.bandK64 : nullptr,
+                           f32 ? asmb.dbandK64 : nullptr, f32 ? asmb.nK64 : 0, tmp, st, &setK));
   auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip,
                         int kmax) -> geneo_status_t {
-    if (f32) {
-      GENEO_TRY(band_solve<float>((const float*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff, kmax,
-                                  ncols, skip, h->dstat, st, maxn, o.eig_solve_tf32 ? 1 : 3));
-      if (asmb.nK64)  // the K_j factored in FP64 (their FP32 descriptors have n = 0)
-        GENEO_TRY(band_solve<double>(asmb.bandK64, asmb.dbandK64, asmb.nK64, asmb.maxwK64, S, xoff, kmax,
-                                     ncols, skip, h->dstat, st, asmb.maxnK64));
-      return GENEO_OK;
-    }
-    return band_solve<double>((const double*)asmb.bandK, asmb.dbandK, N, asmb.maxwK, S, xoff,
-                              kmax, ncols, skip, h->dstat, st, maxn);
+    return solve_set_run(setK, h->solve_streams, S, xoff, kmax, ncols, skip, h->dstat, st,
+                         o.eig_solve_tf32 ? 1 : 3);
   };
   // timed with CUDA events; flops from the per-subdomain column counts
   auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {

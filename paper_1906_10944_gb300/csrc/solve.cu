@@ -461,11 +461,8 @@ geneo_status_t tune_local_solve(geneo_handle_s* h) {
   float best_ms = 1e30f;
   for (int stages = 2; stages <= 4; ++stages) {
     auto run = [&]() -> geneo_status_t {
-      if (h->fp32)
-        return band_solve<float>((const float*)h->bandA, h->dbandA, h->N, h->maxwA, scratch, h->uoff, 1,
-                                 nullptr, nullptr, h->dstat, s, h->maxnD, 3, stages);
-      return band_solve<double>((const double*)h->bandA, h->dbandA, h->N, h->maxwA, scratch, h->uoff, 1,
-                                nullptr, nullptr, h->dstat, s, h->maxnD, 3, stages);
+      return solve_set_run(h->setA, h->solve_streams, scratch, h->uoff, 1, nullptr, nullptr, h->dstat, s, 3,
+                           stages);
     };
     geneo_status_t st = run();
     if (st != GENEO_OK) break;
@@ -536,6 +533,9 @@ geneo_status_t alloc_solver(geneo_handle_s* h) {
     h->spmv_blocks = std::max(1, std::min(kRedBlocks, sms * std::max(occ, 1)));
   }
   if (!h->hpin) GENEO_CUDA(cudaMallocHost(&h->hpin, 16 * sizeof(double)));
+  // the A_j factors in size classes for the local solves
+  GENEO_TRY(make_solve_set(h->bandA, !h->fp32, h->dbandA, h->N, h->fp32 ? h->bandA64 : nullptr,
+                           h->fp32 ? h->dbandA64 : nullptr, h->fp32 ? h->nA64 : 0, M, M.stream, &h->setA));
   // host arrays of the allocation-free solve (Lanczos coefficients and the
   // bisection work), sized once here so that solve never touches the heap
   h->pcg_host.assign(4 * (size_t)(kNoAllocMaxIt + 1), 0.0);
@@ -596,15 +596,9 @@ geneo_status_t apply_prec(geneo_handle_s* h, const double* r, double* z, cudaStr
     GENEO_CUDA(cudaEventRecord(h->ev_join, h->aux));
   }
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops, h->local_solve_bytes, s);
-  if (h->fp32) {
-    GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                nullptr, nullptr, h->dstat, s, h->maxnD, 3, h->local_stages));
-    if (h->nA64)  // the A_j factored in FP64 (their FP32 descriptors have n = 0)
-      GENEO_TRY(band_solve<double>(h->bandA64, h->dbandA64, h->nA64, h->maxwA64, h->u, h->uoff, 1,
-                                   nullptr, nullptr, h->dstat, s, h->maxnA64));
-  } else
-    GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->u, h->uoff, 1,
-                                 nullptr, nullptr, h->dstat, s, h->maxnD, 3, h->local_stages));
+  // size classes of the A_j (FP32 and FP64 factors) on the solve lanes
+  GENEO_TRY(solve_set_run(h->setA, h->solve_streams, h->u, h->uoff, 1, nullptr, nullptr, h->dstat, s, 3,
+                          h->local_stages));
   h->prof.end(pl, s);
   if (h->dimH > 0 && !h->Hinv) GENEO_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);

@@ -318,16 +318,7 @@ geneo_status_t apply_prec_cols(geneo_handle_s* h, const double* R, double* Zo, i
     Y = h->blk_y;
   }
   const int pl = h->prof.begin(GENEO_PROF_LOCAL_SOLVE, h->local_solve_flops * k, h->local_solve_bytes, s);
-  if (h->fp32) {
-    GENEO_TRY(band_solve<float>((const float*)h->bandA, h->dbandA, N, h->maxwA, h->blk_u, h->blk_uoff, k,
-                                nullptr, nullptr, h->dstat, s, h->maxnD));
-    if (h->nA64)
-      GENEO_TRY(band_solve<double>(h->bandA64, h->dbandA64, h->nA64, h->maxwA64, h->blk_u, h->blk_uoff, k,
-                                   nullptr, nullptr, h->dstat, s, h->maxnA64));
-  } else {
-    GENEO_TRY(band_solve<double>((const double*)h->bandA, h->dbandA, N, h->maxwA, h->blk_u, h->blk_uoff, k,
-                                 nullptr, nullptr, h->dstat, s, h->maxnD));
-  }
+  GENEO_TRY(solve_set_run(h->setA, h->solve_streams, h->blk_u, h->blk_uoff, k, nullptr, nullptr, h->dstat, s));
   h->prof.end(pl, s);
   const int grid = (int)std::min<int64_t>((h->n + kT - 1) / kT, 152 * 8);
   k_prolong_cols<<<grid, kT, 0, s>>>(h->n, h->dir, R, h->invD_ptr, h->invD_sub, h->invD_loc, h->dsub, h->blk_u,
