@@ -622,7 +622,7 @@ def main():
                     help="PCG iterations the reference arm extrapolates to (default: the "
                          "oracle's own count from tests/golden, else a fixed estimate)")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--eig-solve-tf32", type=int, default=0,
+    ap.add_argument("--eig-solve-tf32", type=int, default=1,
                     help="mixed path: eigensolver block solves in one TF32 pass (1) or three (0)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--no-c4", action="store_true", help="skip the uneven-batch (160^3, 1024 boxes) leg")

@@ -186,12 +186,13 @@ typedef struct {
  *             inner products are accumulated with atomic additions (one
  *             launch fewer each); results then vary in the last bits from
  *             run to run.
- *  eig_solve_tf32  GENEO_PREC_FP32 only: 1 runs the eigensolver's block
- *             solves with K_j (the shift-and-invert operator of Section 4.4)
- *             as one TF32 tensor-core pass per product instead of three
- *             (about 1e-3 relative error in K_j^{-1} R; the residuals,
- *             Rayleigh-Ritz and convergence test stay FP64, so only the
- *             search directions change); 0 (default) keeps FP32 accuracy.
+ *  eig_solve_tf32  GENEO_PREC_FP32 only: 1 (default) runs the eigensolver's
+ *             block solves with K_j (the shift-and-invert operator of
+ *             Section 4.4) as one TF32 tensor-core pass per product instead
+ *             of three (about 1e-3 relative error in K_j^{-1} R; the
+ *             residuals, Rayleigh-Ritz and convergence test stay FP64, so
+ *             only the search directions change and the eigenpairs meet the
+ *             same tolerance); 0 keeps FP32 accuracy in those solves.
  *  factor_kernel  GENEO_PREC_FP32 only: 0 (default) factors the bands on the
  *             fifth-generation tensor cores (tcgen05 MMAs, TMEM accumulators,
  *             tensor-map copies) when the batch's half bandwidth fits that

@@ -171,7 +171,7 @@ void geneo_default_options(geneo_options_t* o) {
   o->pu_kind = GENEO_PU_STANDARD;
   o->eig_strict = 0;
   o->deterministic = 1;
-  o->eig_solve_tf32 = 0;
+  o->eig_solve_tf32 = 1;
   o->factor_kernel = 0;
   o->autotune = 1;
   o->factor_bf16 = 0;

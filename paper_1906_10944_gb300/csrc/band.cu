@@ -1073,6 +1073,207 @@ k_band_solve_res(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   for (int i = tid; i < n; i += kThreads) X[i] = Sg ? (double)(vec[i] * Sg[i]) : (double)vec[i];
 }
 
+// One right-hand side for bands whose whole vector does not fit in shared
+// memory next to the staged rows (wide bands, long subdomains, FP64).  The
+// sweeps are those of k_band_solve_res (forward left-looking with the
+// inverted 16 x 16 diagonal blocks, backward right-looking), with the
+// vector kept as a window of the rows [kb - w - 16, kb + 16) in a ring of
+// `ring` slots (a power of two >= w + 32): the forward results go to X as
+// they are formed and come back into the ring during the backward sweep, one
+// block ahead.  The band rows stream in as half blocks of 8 rows through kHS
+// shared stages; warp 8 (one lane) issues the bulk copies as soon as a stage
+// is released (full / empty mbarriers, the empty ones counted by the 256
+// compute threads), so a stage is refilled while the other half of the
+// block is still being used.  The first half block of every block also
+// carries that block's inverted diagonal block.  Every wait is bounded; a
+// wait that gives up records GENEO_ERR_TIMEOUT and raises a block-wide
+// abort flag, and the copies already issued are waited for before exit.
+template <typename T, int kHS>
+__global__ void __launch_bounds__(kThreads + 32, 1)
+k_band_solve_ring(const T* __restrict__ base, const BandDesc* __restrict__ descs,
+                  double* __restrict__ xbase, const int64_t* __restrict__ xoff,
+                  const int32_t* __restrict__ nrhs_dev, const int32_t* __restrict__ skip, int ring,
+                  DevStatus* st) {
+  constexpr int SNB = 16, HB = 8;
+  const BandDesc d = descs[blockIdx.x];
+  const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
+  if (skip && skip[mi]) return;
+  if (nrhs_dev && nrhs_dev[mi] <= 0) return;
+  const int n = d.n, w = d.w;
+  if (n <= 0) return;
+  const int ld = d.ld;
+  const T* L = base + d.off;
+  const T* Dg = base + d.dinv;
+  const T* Sg = d.scl >= 0 ? base + d.scl : nullptr;  // equilibrated band: solve with S A S
+  double* X = xbase + xoff[mi];
+  const int rmask = ring - 1;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);  // kHS
+  uint64_t* empty = full + kHS;                             // kHS
+  volatile int* abort = reinterpret_cast<volatile int*>(empty + kHS);
+  T* stage = reinterpret_cast<T*>(smem_raw + 256);          // kHS * (HB * ld + 256)
+  const size_t hs_len = (size_t)HB * ld + 256;              // rows, then the diagonal block
+  T* vec = stage + (size_t)kHS * hs_len;                    // ring
+  T* zb = vec + ring;                                       // SNB
+  T* xs = zb + SNB;                                         // SNB
+  T* rhs = xs + SNB;                                        // SNB: right-hand side of the next block
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = (n + SNB - 1) / SNB;
+  const int nvis = 2 * nb;
+  const int nhv = 2 * nvis;
+
+  if (tid == 0) {
+    for (int i = 0; i < kHS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kThreads);
+    }
+    *abort = 0;
+    fence_barrier_init();
+  }
+  for (int i = tid; i < ring; i += blockDim.x) vec[i] = T(0);
+  for (int i = tid; i < SNB; i += blockDim.x) rhs[i] = (i < n) ? (Sg ? (T)X[i] * Sg[i] : (T)X[i]) : T(0);
+  __syncthreads();
+
+  auto bounded = [&](uint64_t* bar, uint32_t parity, int64_t where) -> bool {
+    for (int it = 0; it < (1 << 22); ++it) {
+      if (mbar_try_wait(bar, parity)) return true;
+      if ((it & 1023) == 1023 && *abort) return false;
+    }
+    *abort = 1;
+    record_error(st, GENEO_ERR_TIMEOUT, d.id, where);
+    return false;
+  };
+
+  if (wid == kThreads / 32) {
+    // ------------------------------------------------------------ copies
+    if (lane == 0) {
+      uint32_t iss[kHS];
+#pragma unroll
+      for (int i = 0; i < kHS; ++i) iss[i] = 0;
+      for (int hv = 0; hv < nhv && !*abort; ++hv) {
+        const int sl = hv % kHS;
+        if (hv >= kHS && !bounded(&empty[sl], (uint32_t)((hv / kHS - 1) & 1), hv)) break;
+        const int v = hv >> 1, h = hv & 1;
+        const int blk = visit_block(v, nb), kb = blk * SNB;
+        const int r0 = kb + HB * h, rows = max(0, min(HB, n - r0));
+        const uint32_t bytes = (uint32_t)((size_t)rows * ld * sizeof(T));
+        const uint32_t dbytes = h == 0 ? 256u * (uint32_t)sizeof(T) : 0u;
+        T* dst = stage + (size_t)sl * hs_len;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[sl], bytes + dbytes);
+        if (bytes) bulk_load(dst, L + (int64_t)r0 * ld, bytes, &full[sl]);
+        if (dbytes) bulk_load(dst + (size_t)HB * ld, Dg + (int64_t)blk * 256, dbytes, &full[sl]);
+        ++iss[sl];
+      }
+      // let every copy issued land before the block exits
+#pragma unroll
+      for (int i = 0; i < kHS; ++i)
+        if (iss[i] > 0)
+          for (int it = 0; it < (1 << 22) && !mbar_try_wait(&full[i], (iss[i] - 1) & 1); ++it) {
+          }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ sweeps
+  int lo = n;  // lowest row in the ring during the backward sweep
+  for (int v = 0; v < nvis; ++v) {
+    const int kb = visit_block(v, nb) * SNB;
+    const int b = min(SNB, n - kb);
+    const int hv0 = 2 * v, s0 = hv0 % kHS, s1 = (hv0 + 1) % kHS;
+    const uint32_t p0 = (uint32_t)((hv0 / kHS) & 1), p1 = (uint32_t)(((hv0 + 1) / kHS) & 1);
+    const T* H0 = stage + (size_t)s0 * hs_len;  // rows kb .. kb + 7, then M
+    const T* H1 = stage + (size_t)s1 * hs_len;  // rows kb + 8 .. kb + 15
+    const T* D = H0 + (size_t)HB * ld;           // M(i, t) at D[16 t + i]
+    if (v < nb) {
+      // ---------------- forward: z_i = b_i - sum_{c < kb} L(kb+i, c) y_c
+      T nxt = T(0);  // right-hand side of the next block (thread i < 16)
+      if (tid < SNB && v + 1 < nb && kb + SNB + tid < n) {
+        const int r = kb + SNB + tid;
+        nxt = Sg ? (T)X[r] * Sg[r] : (T)X[r];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!*abort) bounded(h ? &full[s1] : &full[s0], h ? p1 : p0, v);
+        const T* S = h ? H1 : H0;
+        const int i = HB * h + wid;  // one row per warp
+        T acc = T(0);
+        if (i < b) {
+          const int r = kb + i;
+          const int olo = max(0, w - r), ohi = w - i;  // band offsets of the columns [r - w, kb)
+          const T* sp = S + (size_t)wid * ld;
+          T a1 = T(0);
+          int j = olo + lane;
+          for (; j + 32 < ohi; j += 64) {
+            acc += sp[j] * vec[(r - w + j) & rmask];
+            a1 += sp[j + 32] * vec[(r - w + j + 32) & rmask];
+          }
+          if (j < ohi) acc += sp[j] * vec[(r - w + j) & rmask];
+          acc += a1;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0 && i < b) zb[i] = rhs[i] - acc;
+        if (h == 1) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s1])) : "memory");
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // y = M z
+      if (tid < b) {
+        T y = T(0);
+#pragma unroll
+        for (int t = 0; t < SNB; ++t)
+          if (t <= tid) y += D[t * SNB + tid] * zb[t];
+        vec[(kb + tid) & rmask] = y;
+        X[kb + tid] = (double)y;
+      }
+      if (tid < SNB) rhs[tid] = nxt;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s0])) : "memory");
+      if (v == nb - 1) lo = max(0, kb - w);
+    } else {
+      // ---------------- backward: x = M^T y, then rows above the block
+      const int nlo = max(0, kb - SNB - w);
+      T er = T(0);  // row entering the ring (forward result)
+      if (tid < lo - nlo) er = (T)X[nlo + tid];
+      if (!*abort) bounded(&full[s0], p0, v);
+      if (!*abort) bounded(&full[s1], p1, v);
+      if (tid < b) {
+        T x = T(0);
+#pragma unroll
+        for (int j = 0; j < SNB; ++j) {
+          const int i = (tid + j) & (SNB - 1);  // rotated: conflict-free reads of M
+          if (i >= tid && i < b) x += D[tid * SNB + i] * vec[(kb + i) & rmask];
+        }
+        xs[tid] = x;
+        X[kb + tid] = Sg ? (double)(x * Sg[kb + tid]) : (double)x;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // y_rr -= sum_t L(kb + t, rr) x_t for rr in [lo, kb)
+      for (int rr = lo + tid; rr < kb; rr += kThreads) {
+        const int tmax = min(b - 1, rr - kb + w);
+        T a0 = T(0), a1 = T(0);
+        int t = 0;
+        for (; t + 1 <= tmax; t += 2) {
+          const T* r0p = t < HB ? H0 + (size_t)t * ld : H1 + (size_t)(t - HB) * ld;
+          const T* r1p = t + 1 < HB ? H0 + (size_t)(t + 1) * ld : H1 + (size_t)(t + 1 - HB) * ld;
+          a0 += r0p[rr - kb - t + w] * xs[t];
+          a1 += r1p[rr - kb - t - 1 + w] * xs[t + 1];
+        }
+        if (t <= tmax) {
+          const T* r0p = t < HB ? H0 + (size_t)t * ld : H1 + (size_t)(t - HB) * ld;
+          a0 += r0p[rr - kb - t + w] * xs[t];
+        }
+        vec[rr & rmask] -= a0 + a1;
+      }
+      if (tid < lo - nlo) vec[(nlo + tid) & rmask] = er;
+      lo = nlo;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s0])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s1])) : "memory");
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+  }
+}
+
 // Several right-hand sides (the eigensolver's K_j^{-1} blocks), at most
 // 2 CT per launch.  The solved rows of the last w + 32 block rows sit in a
 // shared ring stored row-major (row stride KP = 2 CT + 4 values, so rows
@@ -1763,6 +1964,14 @@ size_t res_smem(int max_w, int max_n, int snb, int stages) {
   return 128 + sizeof(T) * ((size_t)stages * (snb * ld + 256) + (size_t)((max_n + 3) & ~3) + snb);
 }
 
+// Shared memory of the ring one-right-hand-side solve: barriers, hs half
+// blocks of 8 rows with a diagonal block each, the ring, three 16-vectors.
+template <typename T>
+size_t ring_smem(int max_w, int ring, int hs) {
+  const int ld = band_ld(max_w);
+  return 256 + sizeof(T) * ((size_t)hs * (8 * (size_t)ld + 256) + (size_t)ring + 48);
+}
+
 // Solves with the kernels that do not apply a band's row scaling (the
 // caller scales the vectors around them).
 template <typename T>
@@ -1848,6 +2057,22 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
         GENEO_CUDA(cudaGetLastError());
         return GENEO_OK;
       }
+    }
+    // the vector does not fit: a window of it in a ring, the band in
+    // half-block stages, as many as fit
+    const int ring = next_pow2(max_w + 32);
+    int hs = 6;
+    while (hs > 2 && ring_smem<T>(max_w, ring, hs) > 227 * 1024) hs = hs == 6 ? 4 : hs - 1;
+    const size_t smem = ring_smem<T>(max_w, ring, hs);
+    if (smem <= 227 * 1024) {
+      auto kern = hs == 6 ? k_band_solve_ring<T, 6>
+                : hs == 4 ? k_band_solve_ring<T, 4>
+                : hs == 3 ? k_band_solve_ring<T, 3> : k_band_solve_ring<T, 2>;
+      GENEO_CUDA(allow_smem(kern));
+      kern<<<count, kThreads + 32, smem, s>>>(base, d_desc, xbase, xoff, nrhs_dev, skip_dev, ring, st);
+      note_launch();
+      GENEO_CUDA(cudaGetLastError());
+      return GENEO_OK;
     }
   }
   // FP32 factors: tensor-core kernel, up to 32 columns per launch

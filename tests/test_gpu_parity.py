@@ -111,6 +111,38 @@ def test_one_level_apply_exact():
         sol.close()
 
 
+def test_long_subdomains_ring_solve():
+    """Two subdomains of 1202 x 49 nodes (2D Darcy 2400 x 48, channels):
+    the local vectors no longer fit in shared memory beside the staged band
+    rows, so the local solves take the ring kernel.  FP64: the one-level
+    apply equals the oracle's sparse-LU apply to rounding.  FP32 factors:
+    PCG with the one-level method reaches the true residual 1e-8 in the
+    oracle's iteration count up to the mixed-precision bar."""
+    import torch
+    k = gen.kappa_channels_2d((2400, 48), seed=3, contrast=1e2)
+    prob = gen.darcy_problem((2400, 48), k, (2, 1), 1)
+    orc = oracle.GenEOOracle(prob, oracle.OracleOptions(nev_max=0))
+    sol, _ = run_gpu(prob, nev_max=0)
+    try:
+        rng = np.random.default_rng(4)
+        for _ in range(2):
+            r = rng.standard_normal(prob.n)
+            z = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            sol.apply(torch.from_numpy(r).cuda(), z)
+            zo = orc.apply(r)
+            assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+    finally:
+        sol.close()
+    _, its_o, _, _ = orc.solve(prob.b, tol=1e-8, maxit=4000)
+    sol, _ = run_gpu(prob, nev_max=0, precision=1)
+    try:
+        x, info = gpu_solve(sol, prob, tol=1e-8, maxit=4000)
+        check_residual(prob, x, info, 1e-8)
+        assert abs(info["iterations"] - its_o) <= 0.1 * its_o + 2, (info["iterations"], its_o)
+    finally:
+        sol.close()
+
+
 def test_two_level_apply_matches_oracle():
     """Two-level apply vs the oracle's; the coarse vectors come from an
     iterative eigensolve (residual 1e-6), hence the looser tolerance."""
