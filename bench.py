@@ -354,6 +354,26 @@ def ds_peak():
     return 152 * 128 / 12 * 2 * 2070e6
 
 
+# DRAM traffic of a family's kernel from one ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum) on the 64^3 case, whose 64 subdomains have the same
+# size as the 128^3 ones; it is scaled to a launch of the timed workload by the
+# ratio of traffic to algorithmic bytes (both grow with the band entries
+# read).  Command and figures: profiles/k_band_solve_res_darcy3d_64.md.
+MEASURED_TRAFFIC = {
+    ("local_solve", "mixed"): {"kernel": "k_band_solve_res<float, 3>", "capture": "darcy3d_64",
+                               "dram_bytes_per_launch": 1.0333e9, "algorithmic_bytes_per_launch": 1.008916e9},
+}
+
+
+def measured_traffic(name, precision, alg_bytes_per_launch):
+    m = MEASURED_TRAFFIC.get((name, precision))
+    if m is None:
+        return None, None
+    ratio = m["dram_bytes_per_launch"] / m["algorithmic_bytes_per_launch"]
+    return ratio * alg_bytes_per_launch, "ncu capture of %s on %s, DRAM/algorithmic = %.3f, scaled" % (
+        m["kernel"], m["capture"], ratio)
+
+
 def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
     bound = FAMILY_BOUND.get(name, "alu-fp64")
     if bound == "tensor" and precision != "mixed":
@@ -363,9 +383,14 @@ def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
     ms = rec["ms"] if ms is None else ms
     if bound == "hbm":
         ach = rec["bytes"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src,
-                "algorithmic_bytes_per_launch": rec["bytes"] / max(rec["launches"], 1)}
+        alg = rec["bytes"] / max(rec["launches"], 1)
+        traffic, tsrc = measured_traffic(name, precision, alg)
+        out = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+               "frac": ach / hbm_peak, "traffic": traffic, "peak_source": hbm_src,
+               "algorithmic_bytes_per_launch": alg}
+        if tsrc:
+            out["traffic_source"] = tsrc
+        return out
     ach = rec["flops"] / (ms / 1e3) if ms > 0 else 0.0
     if bound == "tensor" and rec["bytes"] > 0:
         # roofline: the attainable rate is min(tensor peak, intensity x HBM);
@@ -385,8 +410,8 @@ def family_roofline(name, rec, precision, hbm_peak, hbm_src, ms=None):
         peak, src = tf32_peak()
         return {"bound": "tensor", "kernel": name, "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src,
-                "note": "achieved counts the algorithmic FP32 flops; each product runs as three "
-                        "TF32 MMA passes on the warp-level MMA path",
+                "note": "achieved counts the algorithmic FP32 flops; each product runs as TF32 MMA "
+                        "passes (tcgen05 for the factorisation, mma.sync for the block solves)",
                 "algorithmic_flops_per_launch": rec["flops"] / max(rec["launches"], 1)}
     if bound == "alu-ds":
         peak = ds_peak()

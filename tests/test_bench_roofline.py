@@ -56,3 +56,16 @@ def test_hbm_families_report_bandwidth():
     r = bench.family_roofline("local_solve", rec, "mixed", HBM, "measured")
     assert r["bound"] == "hbm"
     assert math.isclose(r["achieved"], 9.23e9 / 0.002 / 1e9)
+
+
+def test_local_solve_traffic_scaled_from_the_capture():
+    # the mixed local solve carries the DRAM bytes of its ncu capture, scaled
+    # by the launch's algorithmic bytes; other families report none
+    rec = {"ms": 100.0, "flops": 1.0e11, "bytes": 60 * 9.23e9, "launches": 60}
+    r = bench.family_roofline("local_solve", rec, "mixed", HBM, "measured")
+    m = bench.MEASURED_TRAFFIC[("local_solve", "mixed")]
+    ratio = m["dram_bytes_per_launch"] / m["algorithmic_bytes_per_launch"]
+    assert math.isclose(r["traffic"], ratio * 9.23e9)
+    assert 0.9 < ratio < 1.2
+    assert bench.family_roofline("spmv", rec, "mixed", HBM, "measured")["traffic"] is None
+    assert bench.family_roofline("local_solve", rec, "fp64", HBM, "measured")["traffic"] is None
