@@ -717,6 +717,12 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   // batch may hold a subset of the subdomains)
   const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
+  // column split: block y of gridDim.y takes its share of the kcap columns
+  {
+    const int cpp = (kcap + (int)gridDim.y - 1) / (int)gridDim.y;
+    col0 += (int)blockIdx.y * cpp;
+    kcap = min(cpp, kcap - (int)blockIdx.y * cpp);
+  }
   int k = kcap;
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
@@ -1301,6 +1307,9 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
   // batch may hold a subset of the subdomains)
   const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
+  // column split: block y takes the columns [2 CT y, 2 CT (y + 1)) of the kcap
+  col0 += (int)blockIdx.y * 2 * CT;
+  kcap -= (int)blockIdx.y * 2 * CT;
   int k = min(kcap, 2 * CT);
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
@@ -1515,6 +1524,9 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
   // batch may hold a subset of the subdomains)
   const int mi = d.id >= 0 ? d.id : (int)blockIdx.x;
   if (skip && skip[mi]) return;
+  // column split: block y takes the columns [8 NT y, 8 NT (y + 1)) of the kcap
+  col0 += (int)blockIdx.y * 8 * NT;
+  kcap -= (int)blockIdx.y * 8 * NT;
   int k = min(kcap, 8 * NT);
   if (nrhs_dev) k = min(k, nrhs_dev[mi] - col0);
   if (k <= 0) return;
@@ -1889,25 +1901,46 @@ size_t multi_smem(int max_w, int ring, int CT, int stages) {
                             (size_t)(kThreads / 32 + 1) * 16 * KP);
 }
 
+// Column split of a multi-right-hand-side launch: when a batch holds at most
+// half as many matrices as the GPU has SMs, each matrix's columns are cut
+// into parts (grid y) that run on otherwise idle SMs, each part a shorter
+// dependent sweep with less work per step; at most `units` parts and no more
+// blocks than SMs.
+inline int sm_count() {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms[dev];
+}
+inline int split_parts(int count, int units) {
+  const int sms = sm_count();
+  if (count <= 0 || 2 * count > sms || units <= 1) return 1;
+  return std::max(1, std::min(units, sms / count));
+}
+
 template <typename T, int CT, int kStages>
-geneo_status_t launch_multi_t(int count, size_t smem, cudaStream_t s, const T* base, const BandDesc* d_desc,
+geneo_status_t launch_multi_t(dim3 grid, size_t smem, cudaStream_t s, const T* base, const BandDesc* d_desc,
                               double* xbase, const int64_t* xoff, int c0, int kc,
                               const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
   auto kern = k_band_solve_multi<T, CT, kStages>;
   GENEO_CUDA(allow_smem(kern));
-  kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
+  kern<<<grid, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
   return GENEO_OK;
 }
 
 template <typename T>
-geneo_status_t launch_multi(int CT, int stages, int count, size_t smem, cudaStream_t s, const T* base,
+geneo_status_t launch_multi(int CT, int stages, dim3 grid, size_t smem, cudaStream_t s, const T* base,
                             const BandDesc* d_desc, double* xbase, const int64_t* xoff, int c0, int kc,
                             const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
 #define GENEO_MULTI(ct, sg)                                                                       \
   if (CT == ct && stages == sg)                                                                  \
-    return launch_multi_t<T, ct, sg>(count, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, \
+    return launch_multi_t<T, ct, sg>(grid, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, \
                                      skip_dev, ring, st);
   GENEO_MULTI(4, 2) GENEO_MULTI(4, 4) GENEO_MULTI(8, 2) GENEO_MULTI(8, 4)
   if constexpr (sizeof(T) == 4) {
@@ -1930,26 +1963,26 @@ inline size_t mtc_smem(int max_w, int ring, int NT, int stages) {
 constexpr size_t kTwoPerSm = 112 * 1024;
 
 template <int NT, int kStages, int PASSES>
-geneo_status_t launch_mtc_t(int count, size_t smem, cudaStream_t s, const float* base, const BandDesc* d_desc,
+geneo_status_t launch_mtc_t(dim3 grid, size_t smem, cudaStream_t s, const float* base, const BandDesc* d_desc,
                             double* xbase, const int64_t* xoff, int c0, int kc,
                             const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
   auto kern = k_band_solve_mtc<NT, kStages, PASSES>;
   GENEO_CUDA(allow_smem(kern));
-  kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
+  kern<<<grid, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
   return GENEO_OK;
 }
 
-geneo_status_t launch_mtc(int NT, int stages, int passes, int count, size_t smem, cudaStream_t s,
+geneo_status_t launch_mtc(int NT, int stages, int passes, dim3 grid, size_t smem, cudaStream_t s,
                           const float* base, const BandDesc* d_desc, double* xbase, const int64_t* xoff,
                           int c0, int kc, const int32_t* nrhs_dev, const int32_t* skip_dev, int ring,
                           DevStatus* st) {
 #define GENEO_MTC(nt, sg)                                                                              \
   if (NT == nt && stages == sg)                                                                        \
-    return passes == 1 ? launch_mtc_t<nt, sg, 1>(count, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
+    return passes == 1 ? launch_mtc_t<nt, sg, 1>(grid, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
                                                  nrhs_dev, skip_dev, ring, st)                         \
-                       : launch_mtc_t<nt, sg, 3>(count, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
+                       : launch_mtc_t<nt, sg, 3>(grid, smem, s, base, d_desc, xbase, xoff, c0, kc,    \
                                                  nrhs_dev, skip_dev, ring, st);
   GENEO_MTC(1, 2) GENEO_MTC(1, 3) GENEO_MTC(1, 4) GENEO_MTC(2, 2) GENEO_MTC(2, 3) GENEO_MTC(2, 4)
   GENEO_MTC(3, 2) GENEO_MTC(3, 3) GENEO_MTC(3, 4) GENEO_MTC(4, 2) GENEO_MTC(4, 3) GENEO_MTC(4, 4)
@@ -1998,10 +2031,17 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
     if (multi_smem<T>(max_w, ring, CT0, 2) <= 227 * 1024) {
       for (int c0 = 0; c0 < nrhs; c0 += kmax) {
         const int kc = std::min(kmax, nrhs - c0);
-        const int CT = (((kc + 1) / 2) + 3) & ~3;
+        int CT = (((kc + 1) / 2) + 3) & ~3;
+        // parts of 8 k columns (CT a multiple of 4)
+        const int units = (kc + 7) / 8, parts = split_parts(count, units);
+        int nsplit = 1;
+        if (parts > 1) {
+          CT = 4 * ((units + parts - 1) / parts);
+          nsplit = (kc + 2 * CT - 1) / (2 * CT);
+        }
         const int stages = multi_smem<T>(max_w, ring, CT, 4) <= 227 * 1024 ? 4 : 2;
-        GENEO_TRY(launch_multi<T>(CT, stages, count, multi_smem<T>(max_w, ring, CT, stages), s, base,
-                                  d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st));
+        GENEO_TRY(launch_multi<T>(CT, stages, dim3(count, nsplit), multi_smem<T>(max_w, ring, CT, stages), s,
+                                  base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st));
       }
       return GENEO_OK;
     }
@@ -2021,7 +2061,10 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
   GENEO_CUDA(allow_smem(kern));
   for (int c0 = 0; c0 < nrhs; c0 += kmax) {
     const int kc = std::min(kmax, nrhs - c0);
-    kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st); note_launch();
+    const int nsplit = split_parts(count, (kc + 3) / 4);  // parts of at least 4 columns
+    kern<<<dim3(count, nsplit), kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring,
+                                                     st);
+    note_launch();
     GENEO_CUDA(cudaGetLastError());
   }
   return GENEO_OK;
@@ -2084,6 +2127,15 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
         int NT = (kc + 7) / 8;
         while (NT > 1 && mtc_smem(max_w, ring, NT, 2) > 227 * 1024) --NT;
         const int kk = std::min(kc, 8 * NT);
+        // column parts of 8 NT columns for small batches
+        int nsplit = 1;
+        {
+          const int parts = split_parts(count, NT);
+          if (parts > 1) {
+            NT = (NT + parts - 1) / parts;
+            nsplit = (kk + 8 * NT - 1) / (8 * NT);
+          }
+        }
         // the deepest pipeline that keeps two blocks per SM when the batch
         // fills more than one wave of single blocks (NT <= 2), else the
         // deepest that fits
@@ -2091,8 +2143,8 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
         const size_t cap = (NT <= 2 && count > 152 && mtc_smem(max_w, ring, NT, 2) <= kTwoPerSm) ? kTwoPerSm
                                                                                                 : 227 * 1024;
         while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > cap) --stages;
-        GENEO_TRY(launch_mtc(NT, stages, tc_passes, count, mtc_smem(max_w, ring, NT, stages), s, base,
-                             d_desc, xbase, xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
+        GENEO_TRY(launch_mtc(NT, stages, tc_passes, dim3(count, nsplit), mtc_smem(max_w, ring, NT, stages), s,
+                             base, d_desc, xbase, xoff, c0, kk, nrhs_dev, skip_dev, ring, st));
         if (kk < kc) c0 -= kc - kk;  // the rest of this chunk goes in the next launch
       }
       return GENEO_OK;
