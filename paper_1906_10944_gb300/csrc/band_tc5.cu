@@ -59,7 +59,7 @@ namespace {
 constexpr int kEpi5 = 256;                     // epilogue / panel threads (warps 0-7)
 constexpr int kT5 = kEpi5 + 64;                // + copy warp 8 + MMA warp 9
 constexpr int kPB5 = 32;                       // panel width = row block height
-constexpr int kStA5 = 4;                       // A-tile stages
+constexpr int kMaxStA5 = 4;                    // A-tile stages (4, or fewer for the widest bands)
 constexpr int kStB5 = 2;                       // B-tile stages
 constexpr int kUS5 = kPB5 + 1;                 // row stride of the panel block in shared memory
 constexpr uint32_t kBox5 = 32u * 32u * 4u;     // one 32 x 32 FP32 box (4 KB)
@@ -70,11 +70,18 @@ constexpr uint32_t kStageB5 = 2 * kTileB5;     // hi and lo of a B tile: 8 KB
 constexpr uint32_t kIdesc5 = umma_idesc_tf32(128, 32);
 constexpr int kMaxPar5 = 7;                    // at most this many hi*hi accumulators per chunk
 // afull, aempty, bfull, bempty, acc_full[2], acc_empty[2], pdone, fin
-constexpr int kBars5 = 2 * kStA5 + 2 * kStB5 + 2 + 2 + 2;
+constexpr int bars5(int sta) { return 2 * sta + 2 * kStB5 + 2 + 2 + 2; }
 
-size_t tc5_smem(int W) {
-  return 1024 + (size_t)kStA5 * kStageA5 + (size_t)kStB5 * kStageB5 + (size_t)(kPB5 + W) * kUS5 * sizeof(float) +
-         2 * kPB5 * sizeof(float) + kBars5 * sizeof(uint64_t) + 16;
+size_t tc5_smem(int W, int sta) {
+  return 1024 + (size_t)sta * kStageA5 + (size_t)kStB5 * kStageB5 + (size_t)(kPB5 + W) * kUS5 * sizeof(float) +
+         2 * kPB5 * sizeof(float) + bars5(sta) * sizeof(uint64_t) + 16;
+}
+// the most A stages (4, 3, 2) whose shared memory fits a class of width W;
+// 0 when none does
+int tc5_stages(int W) {
+  for (int sta = kMaxStA5; sta >= 2; --sta)
+    if (tc5_smem(W, sta) <= 227 * 1024) return sta;
+  return 0;
 }
 
 // Bounded wait that also gives up early once another role has aborted.
@@ -115,7 +122,8 @@ __device__ __forceinline__ void split5(float x, int bf16, float& h, float& l) {
 // Warp-specialised: warp 8 (one lane) streams the tiles of panel after
 // panel, warp 9 (one lane) issues the MMAs into one of nbuf (1 or 2) TMEM
 // accumulator buffers (panel G uses buffer G % nbuf), and warps 0-7 run the panel
-// steps.  A tiles go through a ring of kStA5 stages, the B tile of each
+// steps.  A tiles go through a ring of kStA5 stages (4, or 3 or 2 for the
+// widest classes, whose panel block takes the room), the B tile of each
 // k-chunk (shared by the chunk's row tiles) through a ring of kStB5.  The
 // tiles of panel J + 1 that do not read panel J's columns (all k-chunks but
 // the last) are loaded and multiplied while panel J is being factored; the
@@ -123,6 +131,7 @@ __device__ __forceinline__ void split5(float x, int bf16, float& h, float& l) {
 // aempty and bfull / bempty (stage rings), acc_full[b] (MMA -> panel
 // threads), acc_empty[b] (panel threads -> MMA: buffer b read), pdone
 // (panel written).
+template <int kStA5>
 __global__ void __launch_bounds__(kT5, 1)
 k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  float* __restrict__ phi, float* __restrict__ plo, const BandDesc* __restrict__ descs,
@@ -178,7 +187,9 @@ k_band_potrf_tc5(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
   const uint32_t tmem = *tslot;
 
   // role state carried over the matrices this CTA takes from the queue
-  uint32_t issA[kStA5] = {0, 0, 0, 0}, issB[kStB5] = {0, 0};  // copy lane: arms per stage
+  uint32_t issA[kStA5], issB[kStB5] = {0, 0};  // copy lane: arms per stage
+#pragma unroll
+  for (int i = 0; i < kStA5; ++i) issA[i] = 0;
   uint32_t ta = 0, tb = 0;  // copy and MMA lanes: A tiles and B tiles so far
   int pb = 0;               // panels of the earlier matrices (barrier phases run on)
   for (;;) {
@@ -571,7 +582,7 @@ bool tc5_fits(int w) {
   const int W = (w + 31) & ~31;
   const int nh = (kPB5 + W + 127) / 128;
   int nb = 0, P = 0;
-  return W >= kPB5 && tc5_smem(W) <= 227 * 1024 && tc5_acc_layout(nh, &nb, &P);
+  return W >= kPB5 && tc5_stages(W) > 0 && tc5_acc_layout(nh, &nb, &P);
 }
 
 geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem& tmp, cudaStream_t s,
@@ -579,8 +590,9 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   p->ok = false;
   if (count <= 0) return GENEO_OK;
   const int W = (max_w + 31) & ~31;
-  const size_t smem = tc5_smem(W);
-  if (W < kPB5 || smem > 227 * 1024) return GENEO_OK;  // the older kernels take it
+  const int sta = tc5_stages(W);
+  if (W < kPB5 || sta == 0) return GENEO_OK;  // the older kernels take it
+  const size_t smem = tc5_smem(W, sta);
   const int nh = (kPB5 + W + 127) / 128;
   int nbuf = 0, P = 0;
   if (!tc5_acc_layout(nh, &nbuf, &P)) return GENEO_OK;
@@ -608,6 +620,7 @@ geneo_status_t tc5_prepare(const BandDesc* h_desc, int count, int max_w, DevMem&
   p->nbuf = nbuf;
   p->par = P;
   p->smem = smem;
+  p->sta = sta;
   p->count = count;
   p->max_n = max_n;
   p->ok = true;
@@ -620,16 +633,16 @@ geneo_status_t tc5_factor(const Tc5Plan& p, float* band, const BandDesc* d_desc,
   const dim3 gp((unsigned)std::min(64, (p.max_n + 7) / 8), (unsigned)p.count);
   k_tb_pack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo, bf16); note_launch();
   GENEO_CUDA(cudaGetLastError());
-  GENEO_CUDA(allow_smem(k_band_potrf_tc5));
+  auto kern = p.sta == 4 ? k_band_potrf_tc5<4> : p.sta == 3 ? k_band_potrf_tc5<3> : k_band_potrf_tc5<2>;
+  GENEO_CUDA(allow_smem(kern));
   // persistent CTAs, one per SM (the shared memory allows no more), taking
   // matrices from the queue in batch order
   int dev = 0, sms = 0;
   GENEO_CUDA(cudaGetDevice(&dev));
   GENEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   GENEO_CUDA(cudaMemsetAsync(p.queue, 0, sizeof(int32_t), s));
-  k_band_potrf_tc5<<<std::min(p.count, sms), kT5, p.smem, s>>>(p.mhi, p.mlo, p.phi, p.plo, d_desc, p.dz, p.count,
-                                                                p.queue, p.W, p.cols, p.nbuf, p.par, st, weak,
-                                                                weak_tol, bf16);
+  kern<<<std::min(p.count, sms), kT5, p.smem, s>>>(p.mhi, p.mlo, p.phi, p.plo, d_desc, p.dz, p.count, p.queue, p.W,
+                                                    p.cols, p.nbuf, p.par, st, weak, weak_tol, bf16);
   note_launch();
   GENEO_CUDA(cudaGetLastError());
   k_tb_unpack<<<gp, 256, 0, s>>>(band, d_desc, p.dz, p.W, p.phi, p.plo); note_launch();

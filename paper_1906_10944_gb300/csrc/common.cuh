@@ -314,6 +314,7 @@ struct Tc5Plan {
   int W = 0, count = 0, max_n = 0;
   uint32_t cols = 0;  // TMEM columns allocated
   int nbuf = 0;       // accumulator buffers (panels in flight)
+  int sta = 4;        // A-tile stages of the kernel
   int par = 0;        // hi*hi accumulators per 128-row chunk
   size_t smem = 0;
   float* phi = nullptr;

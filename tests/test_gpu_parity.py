@@ -194,6 +194,18 @@ def test_darcy_3d_ragged_mixed_precision():
     _full_check(prob, nev=8, name="darcy3d-ragged", precision=1, iter_slack=0.1)
 
 
+def test_wide_bands_mixed_precision():
+    """3D Darcy 60 x 26 x 26 in two subdomains of about 19,000 dofs: half
+    bandwidths 807 (K_j) and 781 (A_j), too wide for four A-tile stages next
+    to the panel block, so the tensor-core factorisation runs with two and
+    three stages.  FP32 factors against the FP64 oracle (mixed bar)."""
+    nel = (60, 26, 26)
+    kap = gen.kappa_grf_layers_3d(nel, seed=6, corr_len=0.2, variance=2.0, contrast=1e3,
+                                  slab_z=(30, 80), slab_thickness=1)
+    prob = gen.darcy_problem(nel, kap, (2, 1, 1), 1)
+    _full_check(prob, nev=8, name="wide-bands", precision=1, iter_slack=0.1)
+
+
 def test_c1_mixed_precision():
     """FP32 factors (local solves and the eigensolver's shift-invert operator)
     with FP64 residuals, Rayleigh-Ritz, coarse problem and PCG."""
