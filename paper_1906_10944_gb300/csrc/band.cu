@@ -22,6 +22,7 @@
 // updated in the shared ring); diagonal blocks are solved by warp shuffles.
 // The factor is read once per sweep; b and x once each.
 #include "common.cuh"
+#include "ds.cuh"
 #include "ptx.cuh"
 
 namespace geneo {
@@ -50,6 +51,16 @@ __device__ __forceinline__ void store4(float* p, const float* o) {
 __device__ __forceinline__ void store4(double* p, const double* o) {
   *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
   *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+}
+
+__device__ __forceinline__ void load4(const dsv* p, dsv* o) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 c = *reinterpret_cast<const float4*>(p + 2);
+  o[0] = dsv(a.x, a.y); o[1] = dsv(a.z, a.w); o[2] = dsv(c.x, c.y); o[3] = dsv(c.z, c.w);
+}
+__device__ __forceinline__ void store4(dsv* p, const dsv* o) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+  *reinterpret_cast<float4*>(p + 2) = make_float4(o[2].h, o[2].l, o[3].h, o[3].l);
 }
 
 __device__ __forceinline__ int64_t bidx(int r, int c, int w, int64_t ld) {
@@ -706,7 +717,7 @@ template <typename T> struct Stages { static constexpr int v = 2; };
 // Block v of the visit order 0..nb-1 (forward), nb-1..0 (backward).
 __device__ __forceinline__ int visit_block(int v, int nb) { return v < nb ? v : 2 * nb - 1 - v; }
 
-template <typename T, int kSNB, int kMaxRhsPerWarp, int kStages>
+template <typename T, typename A, int kSNB, int kMaxRhsPerWarp, int kStages>
 __global__ void __launch_bounds__(kThreads, kMaxRhsPerWarp == 1 ? (sizeof(T) == 4 ? 4 : 2) : 2)
 k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
              double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
@@ -736,14 +747,14 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                      // kStages
   T* stage = reinterpret_cast<T*>(smem_raw + 128);                             // kStages * SNB * ld
-  T* win = stage + (size_t)kStages * kSNB * ld;                                // k columns of ring rows
-  T* blk = win + (size_t)ring * k;                                             // SNB * k
-  T* red = blk + (size_t)kSNB * k;                                             // 4 * kThreads
+  A* win = reinterpret_cast<A*>(stage + (size_t)kStages * kSNB * ld);         // k columns of ring rows
+  A* blk = win + (size_t)ring * k;                                             // SNB * k
+  A* red = blk + (size_t)kSNB * k;                                             // 4 * kThreads
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kThreads >> 5;
   const int nb = (n + kSNB - 1) / kSNB;
   const int nvis = 2 * nb;
 
-  for (int idx = tid; idx < ring * k; idx += kThreads) win[idx] = T(0);
+  for (int idx = tid; idx < ring * k; idx += kThreads) win[idx] = A();
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
@@ -775,11 +786,11 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
       // ---------------- forward, rows kb..kb+b-1 (left-looking)
       // right-hand sides of this block, fetched before the wait (lane i of
       // the warp owning right-hand side c holds b[kb + i][c])
-      T xb[kMaxRhsPerWarp];
+      A xb[kMaxRhsPerWarp];
 #pragma unroll
       for (int u = 0; u < kMaxRhsPerWarp; ++u) {
         const int c = wid + u * nw;
-        xb[u] = (c < k && lane < b) ? (T)X[(int64_t)c * n + kb + lane] : T(0);
+        xb[u] = (c < k && lane < b) ? to_arith<A>(X[(int64_t)c * n + kb + lane]) : A();
       }
       if (ok) {
         ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
@@ -803,25 +814,25 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         const int s0 = olo + (int)((int64_t)len * seg / nseg);
         const int s1 = olo + (int)((int64_t)len * (seg + 1) / nseg);
         const T* srow = S + (size_t)i * ld;
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        A a0 = A(), a1 = A(), a2 = A(), a3 = A();
         if (ct == 1) {
-          const T* wc = win + (size_t)c0 * ring;
+          const A* wc = win + (size_t)c0 * ring;
           int oo = s0;
           for (; oo + 1 < s1; oo += 2) {
-            a0 += srow[oo] * wc[(r - w + oo) & rmask];
-            a1 += srow[oo + 1] * wc[(r - w + oo + 1) & rmask];
+            a0 += to_arith<A>(srow[oo]) * wc[(r - w + oo) & rmask];
+            a1 += to_arith<A>(srow[oo + 1]) * wc[(r - w + oo + 1) & rmask];
           }
-          if (oo < s1) a0 += srow[oo] * wc[(r - w + oo) & rmask];
+          if (oo < s1) a0 += to_arith<A>(srow[oo]) * wc[(r - w + oo) & rmask];
           a0 += a1;
-          a1 = T(0);
+          a1 = A();
         } else {
-          const T* w0 = win + (size_t)c0 * ring;
+          const A* w0 = win + (size_t)c0 * ring;
           const bool h1 = c0 + 1 < k, h2 = c0 + 2 < k, h3 = c0 + 3 < k;
-          const T* w1 = h1 ? w0 + ring : w0;
-          const T* w2 = h2 ? w0 + 2 * ring : w0;
-          const T* w3 = h3 ? w0 + 3 * ring : w0;
+          const A* w1 = h1 ? w0 + ring : w0;
+          const A* w2 = h2 ? w0 + 2 * ring : w0;
+          const A* w3 = h3 ? w0 + 3 * ring : w0;
           for (int oo = s0; oo < s1; ++oo) {
-            const T sv = srow[oo];
+            const A sv = to_arith<A>(srow[oo]);
             const int q = (r - w + oo) & rmask;
             a0 += sv * w0[q];
             a1 += sv * w1[q];
@@ -829,7 +840,7 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
             a3 += sv * w3[q];
           }
         }
-        T* rd = red + (size_t)(seg * ntiles + tile) * 4;
+        A* rd = red + (size_t)(seg * ntiles + tile) * 4;
         rd[0] = a0;
         rd[1] = a1;
         rd[2] = a2;
@@ -838,19 +849,19 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
       __syncthreads();
       // diagonal block by the warp owning each right-hand side: row of L and
       // the reciprocal pivot in registers, substitution by shuffles
-      T lrow[kSNB];
+      A lrow[kSNB];
 #pragma unroll
       for (int t = 0; t < kSNB; ++t)
-        lrow[t] = (lane < b && t < lane && lane - t <= w) ? S[lane * ld + (w - lane + t)] : T(0);
-      const T dinv = lane < b ? T(1) / S[lane * ld + w] : T(0);
+        lrow[t] = (lane < b && t < lane && lane - t <= w) ? to_arith<A>(S[lane * ld + (w - lane + t)]) : A();
+      const A dinv = lane < b ? recip_arith<A>(S[lane * ld + w]) : A();
 #pragma unroll
       for (int u = 0; u < kMaxRhsPerWarp; ++u) {
         const int c = wid + u * nw;
         if (c >= k) break;
-        T y = T(0);
+        A y = A();
         if (lane < b) {
           const int tile = lane + (c / ct) * b, q = c % ct;
-          T acc = T(0);
+          A acc = A();
           for (int seg = 0; seg < nseg; ++seg) acc += red[(size_t)(seg * ntiles + tile) * 4 + q];
           y = xb[u] - acc;
         }
@@ -858,13 +869,13 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         for (int t = 0; t < kSNB; ++t) {
           if (t < b) {
             if (lane == t) y *= dinv;
-            const T yt = __shfl_sync(0xffffffffu, y, t);
+            const A yt = shfl(y, t);
             if (lane > t) y -= lrow[t] * yt;
           }
         }
         if (lane < b) {
           win[(size_t)c * ring + ((kb + lane) & rmask)] = y;
-          X[(int64_t)c * n + kb + lane] = (double)y;
+          X[(int64_t)c * n + kb + lane] = to_double(y);
         }
       }
       if (v == nb - 1) lo = max(0, kb - w);  // the ring holds rows [lo, n) for the backward sweep
@@ -875,24 +886,24 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         waited += ok ? 1 : 0;
       }
       const T* S = stage + (size_t)s * kSNB * ld;
-      T lcol[kSNB];
+      A lcol[kSNB];
 #pragma unroll
       for (int t = 0; t < kSNB; ++t)
-        lcol[t] = (t < b && lane < t && t - lane <= w) ? S[t * ld + (w - t + lane)] : T(0);
-      const T dinv = lane < b ? T(1) / S[lane * ld + w] : T(0);
+        lcol[t] = (t < b && lane < t && t - lane <= w) ? to_arith<A>(S[t * ld + (w - t + lane)]) : A();
+      const A dinv = lane < b ? recip_arith<A>(S[lane * ld + w]) : A();
       for (int c = wid; c < k; c += nw) {
-        T y = lane < b ? win[(size_t)c * ring + ((kb + lane) & rmask)] : T(0);
+        A y = lane < b ? win[(size_t)c * ring + ((kb + lane) & rmask)] : A();
 #pragma unroll
         for (int t = kSNB - 1; t >= 0; --t) {
           if (t < b) {
             if (lane == t) y *= dinv;
-            const T xt = __shfl_sync(0xffffffffu, y, t);
+            const A xt = shfl(y, t);
             if (lane < t) y -= lcol[t] * xt;
           }
         }
         if (lane < b) {
           blk[lane * k + c] = y;
-          X[(int64_t)c * n + kb + lane] = (double)y;
+          X[(int64_t)c * n + kb + lane] = to_double(y);
         }
       }
       __syncthreads();
@@ -903,11 +914,11 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
       const int ncg = (k + 3) / 4;
       for (int idx = tid; idx < cnt * ncg; idx += kThreads) {
         const int rr = lo + idx % cnt, c0 = (idx / cnt) * 4;
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        A a0 = A(), a1 = A(), a2 = A(), a3 = A();
         const int tmax = min(b - 1, rr - kb + w);
         for (int t = 0; t <= tmax; ++t) {
-          const T sv = S[t * ld + (rr - kb - t + w)];
-          const T* bt = blk + t * k + c0;
+          const A sv = to_arith<A>(S[t * ld + (rr - kb - t + w)]);
+          const A* bt = blk + t * k + c0;
           a0 += sv * bt[0];
           if (c0 + 1 < k) a1 += sv * bt[1];
           if (c0 + 2 < k) a2 += sv * bt[2];
@@ -924,7 +935,7 @@ k_band_solve(const T* __restrict__ base, const BandDesc* __restrict__ descs,
         const int ncnt = lo - nlo;
         for (int idx = tid; idx < ncnt * k; idx += kThreads) {
           const int rr = nlo + idx % ncnt, c = idx / ncnt;
-          win[(size_t)c * ring + (rr & rmask)] = (T)X[(int64_t)c * n + rr];
+          win[(size_t)c * ring + (rr & rmask)] = to_arith<A>(X[(int64_t)c * n + rr]);
         }
         lo = nlo;
       }
@@ -1293,7 +1304,7 @@ k_band_solve_ring(const T* __restrict__ base, const BandDesc* __restrict__ descs
 // rows above the block are updated, one (row, four columns) item per thread.
 // Right-hand sides of the next block and the rows that enter the ring are
 // loaded one block ahead.
-template <typename T, int CT, int kStages>
+template <typename T, typename A, int CT, int kStages>
 __global__ void __launch_bounds__(kThreads, 1)
 k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ descs,
                    double* __restrict__ xbase, const int64_t* __restrict__ xoff, int col0, int kcap,
@@ -1325,14 +1336,14 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);      // kStages
   T* stage = reinterpret_cast<T*>(smem_raw + 128);             // kStages * SNB * ld
   T* dstage = stage + (size_t)kStages * SNB * ld;              // kStages * 256
-  T* win = dstage + (size_t)kStages * 256;                     // ring * KP
-  T* red = win + (size_t)ring * KP;                            // NW * SNB * KP
-  T* zb = red + (size_t)NW * SNB * KP;                         // SNB * KP
+  A* win = reinterpret_cast<A*>(dstage + (size_t)kStages * 256);  // ring * KP
+  A* red = win + (size_t)ring * KP;                               // NW * SNB * KP
+  A* zb = red + (size_t)NW * SNB * KP;                            // SNB * KP
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = (n + SNB - 1) / SNB;
   const int nvis = 2 * nb;
 
-  for (int idx = tid; idx < ring * KP; idx += kThreads) win[idx] = T(0);
+  for (int idx = tid; idx < ring * KP; idx += kThreads) win[idx] = A();
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
@@ -1353,14 +1364,14 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
     for (; issued < min(kStages - 1, nvis); ++issued) issue(issued);
   // element e of a (16 rows x k columns) block handled by this thread:
   // idx = tid + e * kThreads, column idx >> 4, row idx & 15
-  auto load_rows = [&](int r0, int cnt, T* out) {
+  auto load_rows = [&](int r0, int cnt, A* out) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
-      out[e] = (c < k && t < cnt) ? (T)X[(int64_t)c * n + r0 + t] : T(0);
+      out[e] = (c < k && t < cnt) ? to_arith<A>(X[(int64_t)c * n + r0 + t]) : A();
     }
   };
-  T xr[2];
+  A xr[2];
   load_rows(0, min(SNB, n), xr);
   bool ok = true;
   int waited = 0;
@@ -1388,33 +1399,33 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
       }
       {
         const int i = lane & 15, g = lane >> 4;
-        T acc[CT];
+        A acc[CT];
 #pragma unroll
-        for (int c = 0; c < CT; ++c) acc[c] = T(0);
+        for (int c = 0; c < CT; ++c) acc[c] = A();
         if (i < b) {
           const int ua = (int)((int64_t)w * wid / NW), ub = (int)((int64_t)w * (wid + 1) / NW);
           const int u0 = max(ua, max(i, w - kb));
           const T* srow = S + (size_t)i * ld - i;   // srow[u] = L(kb + i, kb - w + u)
           for (int u = u0; u < ub; ++u) {
-            const T a = srow[u];
-            const T* rr = win + (size_t)((kb - w + u) & rmask) * KP + g * CT;
+            const A a = to_arith<A>(srow[u]);
+            const A* rr = win + (size_t)((kb - w + u) & rmask) * KP + g * CT;
 #pragma unroll
             for (int q = 0; q < CT / 4; ++q) {
-              T xv[4];
+              A xv[4];
               load4(rr + 4 * q, xv);
 #pragma unroll
               for (int z = 0; z < 4; ++z) acc[4 * q + z] += a * xv[z];
             }
           }
         }
-        T* rp = red + (size_t)(wid * SNB + i) * KP + g * CT;
+        A* rp = red + (size_t)(wid * SNB + i) * KP + g * CT;
 #pragma unroll
         for (int q = 0; q < CT / 4; ++q) store4(rp + 4 * q, acc + 4 * q);
       }
       __syncthreads();
       for (int idx = tid; idx < SNB * k; idx += kThreads) {
         const int c = idx >> 4, t = idx & 15;
-        T sum = T(0);
+        A sum = A();
 #pragma unroll
         for (int ww = 0; ww < NW; ++ww) sum += red[(size_t)(ww * SNB + t) * KP + c];
         zb[t * KP + c] -= sum;
@@ -1424,19 +1435,19 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
       for (int idx = tid; idx < SNB * k; idx += kThreads) {
         const int c = idx >> 4, i = idx & 15;
         if (i < b) {
-          T y = T(0);
+          A y = A();
 #pragma unroll
           for (int t = 0; t < SNB; ++t)
-            if (t <= i) y += D[t * SNB + i] * zb[t * KP + c];
+            if (t <= i) y += to_arith<A>(D[t * SNB + i]) * zb[t * KP + c];
           win[(size_t)((kb + i) & rmask) * KP + c] = y;
-          X[(int64_t)c * n + kb + i] = (double)y;
+          X[(int64_t)c * n + kb + i] = to_double(y);
         }
       }
       if (v == nb - 1) lo = max(0, kb - w);
     } else {
       // ---------------- backward
       const int nlo = max(0, kb - SNB - w);
-      T er[2];
+      A er[2];
       load_rows(nlo, lo - nlo, er);  // rows entering the ring (forward results)
       if (ok) {
         ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
@@ -1445,14 +1456,14 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
       // x = M^T y into zb (the ring rows of the block are not needed again)
       for (int idx = tid; idx < SNB * k; idx += kThreads) {
         const int c = idx >> 4, t = idx & 15;
-        T x = T(0);
+        A x = A();
         if (t < b) {
 #pragma unroll
           for (int j = 0; j < SNB; ++j) {
             const int i = (t + j) & (SNB - 1);  // rotated: conflict-free reads of M
-            if (i >= t && i < b) x += D[t * SNB + i] * win[(size_t)((kb + i) & rmask) * KP + c];
+            if (i >= t && i < b) x += to_arith<A>(D[t * SNB + i]) * win[(size_t)((kb + i) & rmask) * KP + c];
           }
-          X[(int64_t)c * n + kb + t] = (double)x;
+          X[(int64_t)c * n + kb + t] = to_double(x);
         }
         zb[t * KP + c] = x;
       }
@@ -1462,12 +1473,12 @@ k_band_solve_multi(const T* __restrict__ base, const BandDesc* __restrict__ desc
       for (int it = tid; it < cnt * nq; it += kThreads) {
         const int rr = lo + it % cnt, q = it / cnt;
         const int tmax = min(b - 1, rr - kb + w);
-        T* yrow = win + (size_t)(rr & rmask) * KP + 4 * q;
-        T acc[4];
+        A* yrow = win + (size_t)(rr & rmask) * KP + 4 * q;
+        A acc[4];
         load4(yrow, acc);
         for (int t = 0; t <= tmax; ++t) {
-          const T lv = S[t * ld + (rr - kb - t + w)];
-          T xv[4];
+          const A lv = to_arith<A>(S[t * ld + (rr - kb - t + w)]);
+          A xv[4];
           load4(zb + t * KP + 4 * q, xv);
 #pragma unroll
           for (int z = 0; z < 4; ++z) acc[z] -= lv * xv[z];
@@ -1922,11 +1933,11 @@ inline int split_parts(int count, int units) {
   return std::max(1, std::min(units, sms / count));
 }
 
-template <typename T, int CT, int kStages>
+template <typename T, typename A, int CT, int kStages>
 geneo_status_t launch_multi_t(dim3 grid, size_t smem, cudaStream_t s, const T* base, const BandDesc* d_desc,
                               double* xbase, const int64_t* xoff, int c0, int kc,
                               const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
-  auto kern = k_band_solve_multi<T, CT, kStages>;
+  auto kern = k_band_solve_multi<T, A, CT, kStages>;
   GENEO_CUDA(allow_smem(kern));
   kern<<<grid, kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
   note_launch();
@@ -1934,13 +1945,13 @@ geneo_status_t launch_multi_t(dim3 grid, size_t smem, cudaStream_t s, const T* b
   return GENEO_OK;
 }
 
-template <typename T>
+template <typename T, typename A = T>
 geneo_status_t launch_multi(int CT, int stages, dim3 grid, size_t smem, cudaStream_t s, const T* base,
                             const BandDesc* d_desc, double* xbase, const int64_t* xoff, int c0, int kc,
                             const int32_t* nrhs_dev, const int32_t* skip_dev, int ring, DevStatus* st) {
 #define GENEO_MULTI(ct, sg)                                                                       \
   if (CT == ct && stages == sg)                                                                  \
-    return launch_multi_t<T, ct, sg>(grid, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, \
+    return launch_multi_t<T, A, ct, sg>(grid, smem, s, base, d_desc, xbase, xoff, c0, kc, nrhs_dev, \
                                      skip_dev, ring, st);
   GENEO_MULTI(4, 2) GENEO_MULTI(4, 4) GENEO_MULTI(8, 2) GENEO_MULTI(8, 4)
   if constexpr (sizeof(T) == 4) {
@@ -2007,7 +2018,7 @@ size_t ring_smem(int max_w, int ring, int hs) {
 
 // Solves with the kernels that do not apply a band's row scaling (the
 // caller scales the vectors around them).
-template <typename T>
+template <typename T, typename A = T>
 geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count, int max_w,
                                 double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                                 const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
@@ -2017,7 +2028,7 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
     const int ring = next_pow2(max_w + 2 * snb);
     const size_t smem = solve_smem<T>(max_w, 1, ring, snb, 2);
     if (smem > 227 * 1024) return GENEO_ERR_ARG;
-    auto kern = snb == 16 ? k_band_solve<T, 16, 1, 2> : k_band_solve<T, 4, 1, 2>;
+    auto kern = snb == 16 ? k_band_solve<T, A, 16, 1, 2> : k_band_solve<T, A, 4, 1, 2>;
     GENEO_CUDA(allow_smem(kern));
     kern<<<count, kThreads, smem, s>>>(base, d_desc, xbase, xoff, 0, 1, nrhs_dev, skip_dev, ring, st); note_launch();
     GENEO_CUDA(cudaGetLastError());
@@ -2040,8 +2051,10 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
           nsplit = (kc + 2 * CT - 1) / (2 * CT);
         }
         const int stages = multi_smem<T>(max_w, ring, CT, 4) <= 227 * 1024 ? 4 : 2;
-        GENEO_TRY(launch_multi<T>(CT, stages, dim3(count, nsplit), multi_smem<T>(max_w, ring, CT, stages), s,
-                                  base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st));
+        const geneo_status_t rc = launch_multi<T, A>(CT, stages, dim3(count, nsplit),
+                                                      multi_smem<T>(max_w, ring, CT, stages), s, base, d_desc,
+                                                      xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring, st);
+        if (rc != GENEO_OK) return rc;
       }
       return GENEO_OK;
     }
@@ -2057,7 +2070,7 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
   while (kmax > 1 && solve_smem<T>(max_w, kmax, ring, snb, stg) > kSmemCap) kmax = (kmax + 1) / 2;
   const size_t smem = solve_smem<T>(max_w, kmax, ring, snb, stg);
   if (smem > 227 * 1024) return GENEO_ERR_ARG;  // band too wide for the streamed solve
-  auto kern = snb == 16 ? k_band_solve<T, 16, 8, stg> : k_band_solve<T, 4, 8, stg>;
+  auto kern = snb == 16 ? k_band_solve<T, A, 16, 8, stg> : k_band_solve<T, A, 4, 8, stg>;
   GENEO_CUDA(allow_smem(kern));
   for (int c0 = 0; c0 < nrhs; c0 += kmax) {
     const int kc = std::min(kmax, nrhs - c0);
@@ -2070,12 +2083,19 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
   return GENEO_OK;
 }
 
-template <typename T>
-geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
-                          double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
-                          int res_stages) {
+template <typename T, typename A>
+geneo_status_t band_solve_impl(const T* base, const BandDesc* d_desc, int count, int max_w,
+                               double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
+                               const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
+                               int res_stages) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
+  // double-single arithmetic covers the multi-column solves; one right-hand
+  // side keeps the FP64 kernels
+  if constexpr (!std::is_same_v<A, T>) {
+    if (nrhs == 1)
+      return band_solve_impl<T, T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, max_n,
+                                   tc_passes, res_stages);
+  }
   // One right-hand side (the preconditioner's local solves): two stages and
   // one register slot per warp keep the block small enough for several
   // blocks per SM, which hides the latency of the sequential sweep.
@@ -2162,8 +2182,24 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   } else {
-    return band_solve_plain<T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s);
+    return band_solve_plain<T, A>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s);
   }
+}
+
+template <typename T>
+geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
+                          double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
+                          const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
+                          int res_stages) {
+  return band_solve_impl<T, T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, max_n,
+                               tc_passes, res_stages);
+}
+
+geneo_status_t band_solve_ds(const double* base, const BandDesc* d_desc, int count, int max_w, double* xbase,
+                             const int64_t* xoff, int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev,
+                             DevStatus* st, cudaStream_t s, int max_n) {
+  return band_solve_impl<double, dsv>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s,
+                                      max_n, 3, 0);
 }
 
 template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, int, DevStatus*,

@@ -360,6 +360,14 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0,
                           int tc_passes = 3, int res_stages = 0);
 
+// FP64 factors solved in double-single arithmetic on the FP32 pipe (about
+// 46 significant bits) for several right-hand sides: the FP64 fallback
+// factors of the FP32 mode, where FP64's 1/64 rate on GB300 bounds the
+// sweeps; one right-hand side is solved in FP64.
+geneo_status_t band_solve_ds(const double* base, const BandDesc* d_desc, int count, int max_w, double* xbase,
+                             const int64_t* xoff, int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev,
+                             DevStatus* st, cudaStream_t s, int max_n);
+
 // solve_set.cu
 // A batch of band factors cut into classes of similar half bandwidth for
 // band_solve (each class launched with its own widest band and longest
@@ -368,6 +376,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
 struct SolveClass {
   const void* base = nullptr;  // float or double band storage
   bool f64 = false;
+  bool ds = false;             // FP64 factors, several right-hand sides in double-single
   BandDesc* d = nullptr;       // the class's descriptors (device), largest sweep first
   int count = 0, max_w = 0, max_n = 0;
   double cost = 0.0;           // bytes of one forward and backward sweep over the class
@@ -384,12 +393,13 @@ struct SolveStreams {
   cudaEvent_t fork = nullptr;
 };
 // The classes of the band batch (base, f64, d_desc, count) and, in FP32 mode,
-// of the FP64 refactorisations (base64, d_desc64, count64; may be empty);
+// of the FP64 refactorisations (base64, d_desc64, count64; may be empty),
+// whose multi-column solves run in double-single arithmetic when ds64;
 // descriptors with n = 0 are left out.  Device descriptor arrays come from
 // mem; the call synchronises s once (it reads the descriptors back).
 geneo_status_t make_solve_set(const void* base, bool f64, const BandDesc* d_desc, int count,
                               const double* base64, const BandDesc* d_desc64, int count64, DevMem& mem,
-                              cudaStream_t s, SolveSet* out);
+                              cudaStream_t s, SolveSet* out, bool ds64 = false);
 // band_solve over every class, ordered after the work already on s; the
 // work of every lane is joined back into s before the call returns.
 geneo_status_t solve_set_run(const SolveSet& ss, const SolveStreams& pool, double* xbase, const int64_t* xoff,

@@ -28,6 +28,7 @@
 #include <type_traits>
 #include <cstdio>
 
+#include "ds.cuh"
 #include "handle.cuh"
 
 namespace geneo {
@@ -134,92 +135,16 @@ k_spmm(const SubDesc* __restrict__ sub, const int64_t* __restrict__ lrow,
 }
 
 // ---------------------------------------------------------------------------
-// Double-single SpMM for the FP32 mode.  GB300 issues FP64 at 1/64 of the
-// FP32 rate, so the FP64 products with K_j and B_j are the eigensolver's
-// largest cost.  Here every value is a pair of floats (hi + lo, hi = the
-// value rounded to FP32), and each product is formed with Dekker's exact
-// product by fused multiply-add plus the two cross terms and accumulated with
-// Knuth's two-sum (Dekker 1971; Knuth, TAOCP vol. 2): about 46 significant
-// bits relative to sum |a x|, against the 53 of FP64 and far below the
-// eigensolver's residual tolerance.  The explicit _rn intrinsics keep the
-// compiler from fusing the additions of the two-sum.
+// Double-single SpMM for the FP32 mode (ds.cuh): the FP64 products with K_j
+// and B_j are the eigensolver's largest cost at FP64's 1/64 rate on GB300;
+// about 46 significant bits relative to sum |a x|, far below the
+// eigensolver's residual tolerance.
 // ---------------------------------------------------------------------------
-struct DS {
-  float h, l;
-};
-
-// acc += a * x for double-single a, x, acc
-__device__ __forceinline__ void ds_fma(DS& acc, float ah, float al, float xh, float xl) {
-  const float p = __fmul_rn(ah, xh);
-  float e = __fmaf_rn(ah, xh, -p);          // p + e = ah xh exactly
-  e = __fmaf_rn(ah, xl, e);
-  e = __fmaf_rn(al, xh, e);
-  const float s = __fadd_rn(acc.h, p);      // two-sum of acc.h and p
-  const float bv = __fsub_rn(s, acc.h);
-  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bv)), __fsub_rn(p, bv));
-  acc.h = s;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
-}
-
 // FP64 values rounded to FP32 (the first pass's copy of K)
 __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
-
-// FP64 -> (hi, lo) floats with integer operations only (the FP64 pipe,
-// which also executes conversions, is the scarce unit): hi keeps the sign,
-// the exponent and the top 23 mantissa bits (truncation), lo the next 23
-// of the remaining 29 bits, so hi + lo = x to 2^-46 relative.  Outside
-// 2^-80 <= |x| < 2^128 the plain conversion is used and lo = 0 (below 2^-126
-// both are 0).
-__device__ __forceinline__ float2 split_bits(double x) {
-  const uint32_t hi32 = (uint32_t)__double2hiint(x), lo32 = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi32 & 0x80000000u;
-  const int e = (int)((hi32 >> 20) & 0x7ffu);
-  if (e < 943 || e > 1150) return make_float2(e >= 897 ? (float)x : 0.f, 0.f);
-  const uint32_t mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-  const float h = __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | mh);
-  const uint32_t r = (lo32 & 0x1fffffffu) >> 6;                     // < 2^23
-  const float f = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.0f);  // r exactly
-  const float sc = __uint_as_float(sign | ((uint32_t)(e - 942) << 23));     // +-2^(e - 1069)
-  return make_float2(h, __fmul_rn(f, sc));
-}
-
-// Exact float -> double and round-to-nearest double -> float with integer
-// operations for normal numbers and zero (the same results as the
-// conversions, which run on the FP64 pipe); anything else converts.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (e == 0 || e == 255) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
-}
-__device__ __forceinline__ float d2f_bits(double x) {
-  const uint32_t hi32 = (uint32_t)__double2hiint(x), lo32 = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi32 & 0x80000000u;
-  const int e = (int)((hi32 >> 20) & 0x7ffu);
-  if (e < 897 || e > 1150) {
-    if ((hi32 & 0x7fffffffu) == 0 && lo32 == 0) return __uint_as_float(sign);
-    return (float)x;
-  }
-  uint32_t b = sign | ((uint32_t)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-  const uint32_t rem = lo32 & 0x1fffffffu;
-  if (rem > 0x10000000u || (rem == 0x10000000u && (b & 1u))) ++b;  // nearest, ties to even
-  return __uint_as_float(b);
-}
-template <typename D, typename S>
-__device__ __forceinline__ D cv(S v) {
-  if constexpr (std::is_same_v<D, S>) return v;
-  else if constexpr (std::is_same_v<D, float>) return d2f_bits(v);
-  else return f2d_bits(v);
-}
-
-// value of an accumulator (double-single pairs summed in FP64)
-__device__ __forceinline__ double acc_value(const DS& v) { return f2d_bits(v.h) + f2d_bits(v.l); }
-__device__ __forceinline__ double acc_value(double v) { return v; }
-__device__ __forceinline__ double acc_value(float v) { return f2d_bits(v); }
 
 // FP64 column block -> (hi, lo) float pairs (split_bits): X2 has X's layout
 // (same W and columns)
@@ -1435,7 +1360,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   // the K_j factors (FP32 and FP64 refactorisations) in size classes
   SolveSet setK;
   GENEO_TRY(make_solve_set(asmb.bandK, !f32, asmb.dbandK, N, f32 ? asmb.bandK64 : nullptr,
-                           f32 ? asmb.dbandK64 : nullptr, f32 ? asmb.nK64 : 0, tmp, st, &setK));
+                           f32 ? asmb.dbandK64 : nullptr, f32 ? asmb.nK64 : 0, tmp, st, &setK, true));
   auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip,
                         int kmax) -> geneo_status_t {
     return solve_set_run(setK, h->solve_streams, S, xoff, kmax, ncols, skip, h->dstat, st,

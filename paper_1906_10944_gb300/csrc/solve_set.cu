@@ -28,7 +28,7 @@ double sweep_bytes(const BandDesc& b, double esz) {
   return 2.0 * esz * (double)b.n * (double)(b.w + 1);
 }
 
-geneo_status_t add_part(const void* base, bool f64, const BandDesc* d_desc, int count, DevMem& mem,
+geneo_status_t add_part(const void* base, bool f64, bool ds, const BandDesc* d_desc, int count, DevMem& mem,
                         cudaStream_t s, std::vector<SolveClass>& out) {
   if (!base || !d_desc || count <= 0) return GENEO_OK;
   std::vector<BandDesc> h(count);
@@ -58,6 +58,7 @@ geneo_status_t add_part(const void* base, bool f64, const BandDesc* d_desc, int 
     SolveClass c;
     c.base = base;
     c.f64 = f64;
+    c.ds = ds;
     c.count = (int)g.size();
     for (const BandDesc& b : g) {
       c.max_w = std::max(c.max_w, b.w);
@@ -74,6 +75,9 @@ geneo_status_t add_part(const void* base, bool f64, const BandDesc* d_desc, int 
 geneo_status_t run_class(const SolveClass& c, double* xbase, const int64_t* xoff, int nrhs,
                          const int32_t* nrhs_dev, const int32_t* skip_dev, DevStatus* st, cudaStream_t s,
                          int tc_passes, int res_stages) {
+  if (c.ds && nrhs > 1)
+    return band_solve_ds(static_cast<const double*>(c.base), c.d, c.count, c.max_w, xbase, xoff, nrhs, nrhs_dev,
+                         skip_dev, st, s, c.max_n);
   if (c.f64)
     return band_solve<double>(static_cast<const double*>(c.base), c.d, c.count, c.max_w, xbase, xoff, nrhs,
                               nrhs_dev, skip_dev, st, s, c.max_n, tc_passes, res_stages);
@@ -85,11 +89,11 @@ geneo_status_t run_class(const SolveClass& c, double* xbase, const int64_t* xoff
 
 geneo_status_t make_solve_set(const void* base, bool f64, const BandDesc* d_desc, int count,
                               const double* base64, const BandDesc* d_desc64, int count64, DevMem& mem,
-                              cudaStream_t s, SolveSet* out) {
+                              cudaStream_t s, SolveSet* out, bool ds64) {
   out->cls.clear();
   out->lanes = 1;
-  GENEO_TRY(add_part(base, f64, d_desc, count, mem, s, out->cls));
-  GENEO_TRY(add_part(base64, true, d_desc64, count64, mem, s, out->cls));
+  GENEO_TRY(add_part(base, f64, false, d_desc, count, mem, s, out->cls));
+  GENEO_TRY(add_part(base64, true, ds64, d_desc64, count64, mem, s, out->cls));
   // longest first onto the least loaded lane (lane 0 = the caller's stream)
   std::vector<size_t> order(out->cls.size());
   std::iota(order.begin(), order.end(), 0);
