@@ -557,6 +557,64 @@ def c4_measure(tol):
     return out
 
 
+def c4_variants(tol):
+    """The uneven batch with each factor variant against the FP64 mode: the
+    tcgen05 TF32x3 factorisation (default), FP32 (factor_kernel = 1: the
+    older warp-level and CUDA-core kernels, here the FP32 FMA kernel for the
+    batch's width), and BF16 factor values (factor_bf16); each with setup and
+    solve time, PCG iterations, kappa, the FP64 fallbacks, dim V_H and the
+    largest relative difference of the selected eigenvalues from the FP64
+    run (|lambda - lambda_64| / max(|lambda_64|, 1e-3 tau))."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_1906_10944_gb300 import geneo as G
+    prob = gen.uneven_darcy_problem((160, 160, 160), 1024, 6, 20, seed=3)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in G.problem_arrays(prob).items()}
+    p = G.make_problem(dev, prob.n, prob.n_sub, prob.elem_dofs.shape[1], prob.ndn, G.GENEO_MEM_DEVICE)
+    b = torch.from_numpy(prob.b).cuda()
+    x = torch.zeros_like(b)
+    tau = 0.3
+    out = {"workload": C4_DESC}
+    ref = None
+    for name, kw in (("fp64", dict(precision=G.GENEO_PREC_FP64)),
+                     ("tf32x3", dict(precision=G.GENEO_PREC_FP32)),
+                     ("fp32", dict(precision=G.GENEO_PREC_FP32, factor_kernel=1)),
+                     ("bf16", dict(precision=G.GENEO_PREC_FP32, factor_bf16=1))):
+        opts = G.geneo_default_options(nev_max=20, tau=tau, **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = G.geneo_setup(p, opts)
+        try:
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            info = G.geneo_pcg_solve(h, b, x, 1, tol, 2000, G.GENEO_MEM_DEVICE, raise_on_error=False)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            q = G.geneo_query(h)
+            lam = [G.geneo_get_subdomain(h, j) for j in range(prob.n_sub)]
+        finally:
+            G.geneo_destroy(h)
+        sel = [g["lambda"][:g["m"]] for g in lam]
+        rec = {"setup_s": t2 - t1, "solve_s": t3 - t2, "pcg_iterations": info["iterations"],
+               "kappa_estimate": info["kappa_estimate"], "true_residual": info["true_residual"],
+               "dim_coarse": q["dim_coarse"], "fp64_factors_K": q["fp64_factors_K"],
+               "fp64_factors_A": q["fp64_factors_A"], "eig_unconverged": q["eig_unconverged"]}
+        if ref is None:
+            ref = sel
+        else:
+            err, diff_m = 0.0, 0
+            for a, r in zip(sel, ref):
+                k = min(a.size, r.size)
+                diff_m += int(a.size != r.size)
+                if k:
+                    err = max(err, float(np.max(np.abs(a[:k] - r[:k]) / np.maximum(np.abs(r[:k]), 1e-3 * tau))))
+            rec["eig_rel_diff_vs_fp64"] = err
+            rec["subdomains_with_other_m"] = diff_m
+        out[name] = rec
+    return out
+
+
 def robustness_curves(tol):
     """Section 5.2 (Fig. 4) and Section 5.1 (Fig. 3) as arrays, computed by
     the library on 2D Darcy, 800 x 800 Q1 elements, u = 1 on top and 0 at
@@ -671,6 +729,9 @@ def main():
     ap.add_argument("--robustness", action="store_true",
                     help="only print the Section 5.1/5.2 arrays (condition number against contrast, "
                          "coarse approximation error) as one JSON line")
+    ap.add_argument("--c4-variants", action="store_true",
+                    help="only print the uneven batch with each factor variant (FP64, TF32x3, FP32, BF16) as "
+                         "one JSON line")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-warmup", type=int, default=50)
     args = ap.parse_args()
@@ -680,7 +741,7 @@ def main():
     import numpy as np
     rank0 = int(os.environ.get("RANK", "0")) == 0
     cpu_base = None
-    if rank0 and not args.no_cpu_baseline and not args.robustness:
+    if rank0 and not args.no_cpu_baseline and not args.robustness and not args.c4_variants:
         # the oracle's process pool (spawn) and its coarse timings come
         # before this process touches the GPU
         cpu_base = OracleBaseline(args.workload, make_problem(args.workload))
@@ -690,6 +751,9 @@ def main():
     from paper_1906_10944_gb300 import geneo as G
     if args.robustness:
         print(json.dumps(robustness_curves(args.tol)))
+        return 0
+    if args.c4_variants:
+        print(json.dumps(c4_variants(args.tol)))
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
