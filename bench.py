@@ -458,8 +458,9 @@ def serve_problems():
     return out
 
 
-def serve_measure(n_requests, warmup, tol):
-    """p50/p99 latency and solves/s of the serving trace (see above)."""
+def serve_measure(n_requests, warmup, tol, rate=SERVE_RATE):
+    """p50/p99 latency and solves/s of the serving trace (see above), at an
+    offered `rate` of requests per second."""
     import numpy as np
     import torch
     from paper_1906_10944_gb300 import geneo as G
@@ -482,14 +483,14 @@ def serve_measure(n_requests, warmup, tol):
     torch.cuda.synchronize()
     pool = S.library_pool(problems, SERVE_BUDGET)
     solve = S.resident_solve_fn(problems, rhs, pool, tol=tol)
-    trace = S.poisson_trace(n_requests + warmup, SERVE_RATE, seed=5, choices=len(problems), max_nrhs=8)
+    trace = S.poisson_trace(n_requests + warmup, rate, seed=5, choices=len(problems), max_nrhs=8)
     reqs = [S.Request(i, k, nrhs=m, arrival=t) for i, (t, k, m) in enumerate(trace)]
     S.Server(solve, workers=SERVE_WORKERS, make_stream=torch.cuda.Stream).run(reqs)
     out = S.summarize(reqs, warmup=warmup)
     out.update(pool.stats())
     pool.close()
     bad = sum(1 for r in reqs if r.result and not all(i["converged"] for i in r.result))
-    out.update({"workers": SERVE_WORKERS, "offered_rps": SERVE_RATE, "unconverged": bad,
+    out.update({"workers": SERVE_WORKERS, "offered_rps": rate, "unconverged": bad,
                 "host_generation_s": t_gen,
                 "trace": "%d requests after %d warm-up, Poisson arrivals at %g/s (seed 5); %d problems: 3D "
                          "Darcy %s elements (16^3-element boxes, overlap 2, nev<=20) and laminate "
@@ -497,7 +498,7 @@ def serve_measure(n_requests, warmup, tol):
                          "coefficient samples each, FP32 factors; 1-8 right-hand sides per request in one "
                          "geneo_pcg_solve call; handles resident, admitted by device footprint (budget "
                          "%g GB); latency = arrival to last solution, rel-res %g"
-                         % (n_requests, warmup, SERVE_RATE, len(problems),
+                         % (n_requests, warmup, rate, len(problems),
                             "/".join("%d^3" % n for n in SERVE_DARCY), "/".join("%d^3" % n for n in SERVE_ELAST),
                             SERVE_SAMPLES, SERVE_BUDGET / 1e9, tol)})
     return out
@@ -733,6 +734,7 @@ def main():
                     help="only print the uneven batch with each factor variant (FP64, TF32x3, FP32, BF16) as "
                          "one JSON line")
     ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rate", type=float, default=SERVE_RATE, help="offered requests per second")
     ap.add_argument("--serve-warmup", type=int, default=50)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -900,7 +902,7 @@ def main():
 
     serve = None
     if rank == 0 and not args.no_serve:
-        serve = serve_measure(args.serve_requests, args.serve_warmup, args.tol)
+        serve = serve_measure(args.serve_requests, args.serve_warmup, args.tol, args.serve_rate)
 
     if rank == 0:
         line = {
