@@ -1620,11 +1620,11 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
     const float* D = dstage + (size_t)s * 256;   // M(i, t) at D[16 t + i]
     if (v < nb) {
       // ---------------- forward
+      // right-hand sides of this block (element e of this thread), kept in
+      // registers while the next block's are fetched
+      float bcur[2];
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int idx = tid + e * kThreads, c = idx >> 4, t = idx & 15;
-        if (c < k) zb[t * KP + c] = xr[e];
-      }
+      for (int e = 0; e < 2; ++e) bcur[e] = xr[e];
       if (v + 1 < nb) load_rows(kb + SNB, min(SNB, n - kb - SNB), xr, true);
       if (ok) {
         ok = mbar_wait_bounded(&bars[s], parity, st, d.id, v);
@@ -1689,24 +1689,30 @@ k_band_solve_mtc(const float* __restrict__ base, const BandDesc* __restrict__ de
           }
       }
       __syncthreads();
-      for (int idx = tid; idx < SNB * k; idx += kThreads) {
-        const int c = idx >> 4, t = idx & 15;
-        float sum = 0.f;
+      // z = b - (the warps' partial sums) and y = M z for element (row t,
+      // column c) of this thread: the 16 rows of a column are the 16 lanes
+      // of one half-warp, which pass z to each other by shuffles (rows past
+      // the block end hold z = 0)
 #pragma unroll
-        for (int ww = 0; ww < NW; ++ww) sum += red[(size_t)(ww * SNB + t) * KP + c];
-        zb[t * KP + c] -= sum;
-      }
-      __syncthreads();
-      // y = M z: one (row, column) output per thread
-      for (int idx = tid; idx < SNB * k; idx += kThreads) {
-        const int c = idx >> 4, i = idx & 15;
-        if (i < b) {
+      for (int e = 0; e < 2; ++e) {
+        const int idx = tid + e * kThreads;
+        if (idx < SNB * k) {
+          const int c = idx >> 4, t = idx & 15;
+          float sum = 0.f;
+#pragma unroll
+          for (int ww = 0; ww < NW; ++ww) sum += red[(size_t)(ww * SNB + t) * KP + c];
+          const float z = bcur[e] - sum;
+          const unsigned hm = 0xffffu << (lane & 16);
           float y = 0.f;
 #pragma unroll
-          for (int t = 0; t < SNB; ++t)
-            if (t <= i) y += D[t * SNB + i] * zb[t * KP + c];
-          *rptr(kb + i, c) = y;
-          X[(int64_t)c * n + kb + i] = (double)y;
+          for (int u = 0; u < SNB; ++u) {
+            const float zu = __shfl_sync(hm, z, u, 16);
+            if (u <= t) y += D[u * SNB + t] * zu;
+          }
+          if (t < b) {
+            *rptr(kb + t, c) = y;
+            X[(int64_t)c * n + kb + t] = (double)y;
+          }
         }
       }
       if (v == nb - 1) lo = max(0, kb - w);
