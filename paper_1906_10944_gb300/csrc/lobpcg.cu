@@ -1266,6 +1266,16 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const int wmax = W3;
   const size_t dense_smem = dense_smem_bytes<double>(wmax);
   const size_t dense_smem32 = dense_smem_bytes<float>(wmax);
+  // order and shared memory of the dense kernels in the current pass: three
+  // times the pass's widest block (the narrow first pass needs far less, so
+  // many more blocks share an SM)
+  int wcur = wmax;
+  size_t dsm = dense_smem, dsm32 = dense_smem32;
+  auto set_dense = [&](int w) {
+    wcur = std::max(1, std::min(wmax, w));
+    dsm = dense_smem_bytes<double>(wcur);
+    dsm32 = dense_smem_bytes<float>(wcur);
+  };
   GENEO_CUDA(allow_smem(k_svqb<double>));
   GENEO_CUDA(allow_smem(k_svqb<float>));
   GENEO_CUDA(allow_smem(k_cholqr));
@@ -1608,13 +1618,13 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_TRY(solveK(xoffX, sj, skip));
     spmm(true, false, Xr, KXr, KXr, skip);
     GENEO_TRY(gram(Xr, KXr, 1, skip));
-    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip, wmax); note_launch(); h->prof.end(prs, st); }
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_svqb<double><<<N, kT, dsm, st>>>(G, Tm, ldg, sj, nullptr, rj, 1e-14, skip, wcur); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, rj), 1.0, 0.0, skip));
     k_set_i32<<<ceil_div(N, 128), 128, 0, st>>>(sj, rj, N, skip); note_launch();
     k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     spmm(false, true, Xr, BXr, BXr, skip);
     GENEO_TRY(gram(Xr, BXr, 1, skip));
-    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip, wmax); note_launch(); h->prof.end(prs, st); }
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dsm, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip, wcur); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
     k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
@@ -1672,7 +1682,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
             GENEO_TRY(gram(Qr32, KQr32, 1, s32));
             {
               const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
-              k_svqb<float><<<N, kT, dense_smem32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, s32, wmax); note_launch();
+              k_svqb<float><<<N, kT, dsm32, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, s32, wcur); note_launch();
               h->prof.end(prs, st);
             }
             // Q = Q32 T straight into the FP64 block (no aliasing: T acts on the copy)
@@ -1698,15 +1708,15 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
         {
           const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st);
           if (pass == 0) {
-            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, sp, wmax);
+            k_svqb<double><<<N, kT, dsm, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, sp, wcur);
             note_launch();
           } else {
             // the block is nearly K-orthonormal: Cholesky QR, SVQB where a
             // pivot is too small
             k_fill_i32<<<ceil_div(N, 128), 128, 0, st>>>(rj, -1, N); note_launch();
-            k_cholqr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, rj, 1e-12, done, wmax); note_launch();
+            k_cholqr<<<N, kT, dsm, st>>>(G, Tm, ldg, qj, rj, 1e-12, done, wcur); note_launch();
             k_mark_fallback<<<ceil_div(N, 128), 128, 0, st>>>(rj, done, redo, N); note_launch();
-            k_svqb<double><<<N, kT, dense_smem, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, redo, wmax); note_launch();
+            k_svqb<double><<<N, kT, dsm, st>>>(G, Tm, ldg, qj, nullptr, rj, 1e-12, redo, wcur); note_launch();
             if (f32 && n64 > 0) { k_and_not<<<ceil_div(N, 128), 128, 0, st>>>(redo, o64, N); note_launch(); }
           }
           h->prof.end(prs, st);
@@ -1726,7 +1736,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // only BQ is new
       spmm(false, true, Qr, BQr, BQr, done);
       GENEO_TRY(gram(Sr, BSr, 1, done));
-      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dense_smem, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wmax); note_launch(); h->prof.end(prs, st); }
+      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dsm, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wcur); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       // P only spans the next search block: FP32 arithmetic with FP32 factors
       if (f32) GENEO_TRY(gemm32(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, 0, 0,
@@ -1749,7 +1759,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   const int nev1 = o.fixed_nev ? nev : std::min(nev, o.first_nev > 0 ? o.first_nev : kFirstPassNev);
   {
     std::vector<int32_t> hs1(N), hn1(N, nev1);
-    for (int j = 0; j < N; ++j) hs1[j] = std::min(nev1 + guard, h->hsub[j].nN);
+    int smax = 1;
+    for (int j = 0; j < N; ++j) {
+      hs1[j] = std::min(nev1 + guard, h->hsub[j].nN);
+      smax = std::max(smax, hs1[j]);
+    }
+    set_dense(3 * smax);
     GENEO_CUDA(cudaMemcpyAsync(sj, hs1.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
     GENEO_CUDA(cudaMemcpyAsync(nevj, hn1.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
   }
@@ -1790,6 +1805,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       GENEO_CUDA(cudaMemcpyAsync(nevj, hn2.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
       GENEO_CUDA(cudaMemcpyAsync(done, redo.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
       k_clear_p<<<ceil_div(N, 128), 128, 0, st>>>(spj, done, N); note_launch();
+      set_dense(wmax);
       GENEO_TRY(init_block(done, o.seed ^ 0x9E3779B97F4A7C15ull));
       GENEO_TRY(iterate());
       // a redone subdomain counts by its second pass
