@@ -657,12 +657,15 @@ k_gemm_ds(const SubDesc* __restrict__ sub, ColRef A, const double* __restrict__ 
           ds_fma(acc[z], av.x, av.y, tv.x, tv.y);
         }
     }
+    const bool copy = beta == 0.0 && alpha == 1.0, sub1 = beta == 1.0 && alpha == -1.0;
 #pragma unroll
     for (int z = 0; z < CB; ++z) {
       const int c = c0 + z;
       if (c < q) {
         double* o = cm + (int64_t)c * d.nN + a_row;
-        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc_value(acc[z]);
+        if (copy) *o = acc_value(acc[z]);
+        else if (sub1) *o = *o - acc_value(acc[z]);
+        else *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc_value(acc[z]);
       }
     }
   }
@@ -737,14 +740,21 @@ k_gemm32(const SubDesc* __restrict__ sub, ColRefT<SA> A, const double* __restric
         }
       }
     }
+    // FP64 epilogue without the FP64 multiplications for the two forms the
+    // eigensolver uses (C = A T and C = C - A T): GB300 issues FP64 at 1/64
+    // of the FP32 rate
+    const bool copy = beta == 0.0 && alpha == 1.0, sub1 = beta == 1.0 && alpha == -1.0;
 #pragma unroll
     for (int z = 0; z < 32; ++z) {
       if (z < nc) {
         const int c = c0 + z;
         SO* o = cm + (int64_t)c * d.nN + a_row;
         if (corr || sizeof(SO) == 8) {
-          const double v = f2d_bits(acc[z]) + (addI ? cv<double>(a[(int64_t)c * d.nN + a_row]) : 0.0);
-          *o = cv<SO>((beta == 0.0 ? 0.0 : beta * cv<double>(*o)) + alpha * v);
+          const double pz = f2d_bits(acc[z]);
+          const double v = addI ? pz + cv<double>(a[(int64_t)c * d.nN + a_row]) : pz;
+          if (copy) *o = cv<SO>(v);
+          else if (sub1) *o = cv<SO>(cv<double>(*o) - v);
+          else *o = cv<SO>((beta == 0.0 ? 0.0 : beta * cv<double>(*o)) + alpha * v);
         } else {
           *o = (SO)((beta == 0.0 ? 0.f : (float)beta * (float)*o) + (float)alpha * acc[z]);
         }
