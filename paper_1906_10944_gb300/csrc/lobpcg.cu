@@ -782,86 +782,175 @@ __global__ void k_init_random(const SubDesc* __restrict__ sub, ColRef X, uint64_
 
 // ---------------------------------------------------------------------------
 // Dense symmetric eigensolver: parallel cyclic Jacobi (round-robin pairs) in
-// arithmetic T.  A (m x m, row stride lda) is overwritten by its diagonal
-// form, V receives the eigenvectors (columns).  Whole block participates.
+// arithmetic T (float, double, or double-single dsv).  A (m x m, row stride
+// lda) is overwritten by its diagonal form, V receives the eigenvectors
+// (columns).  Whole block participates.
+//
+// All M/2 rotations of a round are disjoint, so the round is A <- R A R^T
+// with R block diagonal in the pairs: entry block (k, l) of the result (rows
+// of pair k, columns of pair l) is R_k A_kl R_l^T.  A stays exactly
+// symmetric, so only the blocks k <= l are formed and each is written to
+// both of its places; every block is read and written by one thread, in
+// place.  One barrier after the rotations, one after the update.
 // ---------------------------------------------------------------------------
+template <typename T> struct JacobiOps;
+template <> struct JacobiOps<float> {
+  using R = float;  // norms and pivot tests
+  static constexpr float eps_off = 1e-13f, eps_rot = 1e-9f, tiny = 1e-37f;
+  __device__ static float mag(float v) { return v; }
+};
+template <> struct JacobiOps<double> {
+  using R = double;
+  static constexpr double eps_off = 1e-30, eps_rot = 1e-18, tiny = 1e-300;
+  __device__ static double mag(double v) { return v; }
+};
+// double-single: about 46 bits, so the off-diagonal mass stops near 1e-26 of
+// the whole; the sweeps stop at 1e-24 (off-diagonal entries 1e-12 of the
+// norm, far below what the Ritz values and vectors need).  Norms from the
+// high parts in FP32: the caller scales A to |a_ij| <= 1 (a power of two).
+template <> struct JacobiOps<dsv> {
+  using R = float;
+  static constexpr float eps_off = 1e-24f, eps_rot = 1e-14f, tiny = 1e-37f;
+  __device__ static float mag(dsv v) { return v.h; }
+};
+
+// Rotation (c, s) that annihilates a_pq; false when a_pq is negligible.
 template <typename T>
-__device__ void jacobi_eig(T* A, int lda, T* V, int ldv, int m, T* cs, T* sn, T* red) {
-  // stop when the off-diagonal mass is below eps_off of the whole (squared
-  // norms); rotations smaller than eps_rot relative to the pivots are skipped
-  const T eps_off = sizeof(T) == 4 ? T(1e-13) : T(1e-30);
-  const T eps_rot = sizeof(T) == 4 ? T(1e-9) : T(1e-18);
-  const T tiny = sizeof(T) == 4 ? T(1e-37) : T(1e-300);
+__device__ __forceinline__ bool jacobi_rot(T app, T aqq, T apq, T& c, T& s) {
+  using J = JacobiOps<T>;
+  if (!(fabs(apq) > J::tiny && fabs(apq) > J::eps_rot * sqrt(fabs(app * aqq)))) return false;
+  const T theta = (aqq - app) / (T(2) * apq);
+  const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+  c = T(1) / sqrt(t * t + T(1));
+  s = t * c;
+  return s != T(0);
+}
+// Double-single: the angle in FP32 from the double-single difference of the
+// pivots.  An angle good to FP32 leaves a_pq about 1e-7 of its size instead of
+// zero (the next sweep removes the rest, Jacobi converges just as well with
+// such angles); what must hold to double-single precision is c^2 + s^2 = 1:
+// c = (1 + t^2)^(-1/2) from the correctly rounded FP32 value and one Newton
+// step in double-single (error about 3/8 of the square of the FP32 one),
+// s = t c.
+template <>
+__device__ __forceinline__ bool jacobi_rot<dsv>(dsv app, dsv aqq, dsv apq, dsv& c, dsv& s) {
+  using J = JacobiOps<dsv>;
+  const float a = fabsf(apq.h);
+  if (!(a > J::tiny && a > J::eps_rot * sqrtf(fabsf(app.h * aqq.h)))) return false;
+  const float theta = (aqq - app).h / (2.f * apq.h);
+  const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+  if (!(t != 0.f)) return false;
+  const dsv x = dsv(1.f, 0.f) + dsv(t, 0.f) * dsv(t, 0.f);
+  const float r0 = __frsqrt_rn(x.h);
+  const float delta = (dsv(1.f, 0.f) - x * (dsv(r0, 0.f) * dsv(r0, 0.f))).h;
+  c = dsv(r0, 0.f) + dsv(0.5f * r0 * delta, 0.f);
+  s = dsv(t, 0.f) * c;
+  return true;
+}
+
+template <typename T>
+__device__ void jacobi_eig(T* A, int lda, T* V, int ldv, int m, T* cs, T* sn,
+                           typename JacobiOps<T>::R* red) {
+  using J = JacobiOps<T>;
+  using R = typename J::R;
+  __shared__ int jp[kMaxW / 2 + 1], jq[kMaxW / 2 + 1], jact[kMaxW / 2 + 1];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int M = m + (m & 1);
+  const int M = m + (m & 1), H = M / 2;
   for (int idx = tid; idx < m * m; idx += nt) {
     const int r = idx % m, c = idx / m;
-    V[r * ldv + c] = (r == c) ? T(1) : T(0);
+    V[r * ldv + c] = (r == c) ? T(1.0) : T(0.0);
   }
   __syncthreads();
   if (m <= 1) return;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    T off = T(0), all = T(0);
+    R off = R(0), all = R(0);
     for (int idx = tid; idx < m * m; idx += nt) {
       const int r = idx % m, c = idx / m;
-      const T v = A[r * lda + c];
+      const R v = J::mag(A[r * lda + c]);
       all += v * v;
       if (r != c) off += v * v;
     }
     off = block_sum(off, red);
     all = block_sum(all, red);
-    if (off <= eps_off * all || all == T(0)) break;
+    if (off <= J::eps_off * all || all == R(0)) break;
     for (int round = 0; round < M - 1; ++round) {
-      // pair k: (M-1, round) for k = 0; ((round+k)%(M-1), (round-k+M-1)%(M-1)) otherwise
-      for (int k = tid; k < M / 2; k += nt) {
+      // pair k: (M-1, round) for k = 0; ((round+k)%(M-1), (round-k+M-1)%(M-1))
+      // otherwise; q = M - 1 = m is the padding index of odd m
+      for (int k = tid; k < H; k += nt) {
         int pi, qi;
         if (k == 0) { pi = M - 1; qi = round; }
         else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
         if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        T c = T(1), sv = T(0);
-        if (qi < m) {
-          const T apq = A[pi * lda + qi];
-          const T app = A[pi * lda + pi], aqq = A[qi * lda + qi];
-          if (fabs(apq) > tiny && fabs(apq) > eps_rot * sqrt(fabs(app * aqq))) {
-            const T theta = (aqq - app) / (T(2) * apq);
-            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-            c = T(1) / sqrt(t * t + T(1));
-            sv = t * c;
-          }
+        T c = T(1.0), sv = T(0.0);
+        const bool act = qi < m && jacobi_rot(A[pi * lda + pi], A[qi * lda + qi], A[pi * lda + qi], c, sv);
+        jp[k] = pi;
+        jq[k] = qi;
+        jact[k] = act;
+        cs[k] = act ? c : T(1.0);
+        sn[k] = act ? sv : T(0.0);
+      }
+      __syncthreads();
+      // A <- R A R^T over the blocks k <= l
+      for (int idx = tid; idx < H * H; idx += nt) {
+        const int k = idx / H, l = idx % H;
+        if (k > l || !(jact[k] | jact[l])) continue;
+        const int pk = jp[k], qk = jq[k], pl = jp[l], ql = jq[l];
+        const bool hk = qk < m, hl = ql < m;
+        const T z = T(0.0);
+        const T a00 = A[pk * lda + pl];
+        const T a01 = hl ? A[pk * lda + ql] : z;
+        const T a10 = hk ? A[qk * lda + pl] : z;
+        const T a11 = (hk && hl) ? A[qk * lda + ql] : z;
+        T t00 = a00, t01 = a01, t10 = a10, t11 = a11;
+        if (jact[l]) {
+          const T c = cs[l], s = sn[l];
+          t00 = a00 * c - a01 * s;
+          t01 = a00 * s + a01 * c;
+          t10 = a10 * c - a11 * s;
+          t11 = a10 * s + a11 * c;
         }
-        cs[k] = c;
-        sn[k] = sv;
+        T b00 = t00, b01 = t01, b10 = t10, b11 = t11;
+        if (jact[k]) {
+          const T c = cs[k], s = sn[k];
+          b00 = c * t00 - s * t10;
+          b10 = s * t00 + c * t10;
+          b01 = c * t01 - s * t11;
+          b11 = s * t01 + c * t11;
+        }
+        if (k == l) {
+          // the diagonal block: one value for both off-diagonal places
+          A[pk * lda + pk] = b00;
+          if (hk) {
+            A[pk * lda + qk] = b01;
+            A[qk * lda + pk] = b01;
+            A[qk * lda + qk] = b11;
+          }
+          continue;
+        }
+        A[pk * lda + pl] = b00;
+        A[pl * lda + pk] = b00;
+        if (hl) {
+          A[pk * lda + ql] = b01;
+          A[ql * lda + pk] = b01;
+        }
+        if (hk) {
+          A[qk * lda + pl] = b10;
+          A[pl * lda + qk] = b10;
+        }
+        if (hk && hl) {
+          A[qk * lda + ql] = b11;
+          A[ql * lda + qk] = b11;
+        }
       }
-      __syncthreads();
-      // rows: new_p = c p - s q, new_q = s p + c q
-      for (int idx = tid; idx < (M / 2) * m; idx += nt) {
-        const int k = idx / m, col = idx % m;
-        int pi, qi;
-        if (k == 0) { pi = M - 1; qi = round; }
-        else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
-        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        if (qi >= m || sn[k] == T(0)) continue;
-        const T c = cs[k], sv = sn[k];
-        const T ap = A[pi * lda + col], aq = A[qi * lda + col];
-        A[pi * lda + col] = c * ap - sv * aq;
-        A[qi * lda + col] = sv * ap + c * aq;
-      }
-      __syncthreads();
-      // columns of A and of V
-      for (int idx = tid; idx < (M / 2) * m; idx += nt) {
+      // V <- V R^T (columns of the pairs)
+      for (int idx = tid; idx < H * m; idx += nt) {
         const int k = idx / m, row = idx % m;
-        int pi, qi;
-        if (k == 0) { pi = M - 1; qi = round; }
-        else { pi = (round + k) % (M - 1); qi = (round - k + M - 1) % (M - 1); }
-        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
-        if (qi >= m || sn[k] == T(0)) continue;
-        const T c = cs[k], sv = sn[k];
-        const T ap = A[row * lda + pi], aq = A[row * lda + qi];
-        A[row * lda + pi] = c * ap - sv * aq;
-        A[row * lda + qi] = sv * ap + c * aq;
+        if (!jact[k]) continue;
+        const int pi = jp[k], qi = jq[k];
+        const T c = cs[k], s = sn[k];
         const T vp = V[row * ldv + pi], vq = V[row * ldv + qi];
-        V[row * ldv + pi] = c * vp - sv * vq;
-        V[row * ldv + qi] = sv * vp + c * vq;
+        V[row * ldv + pi] = c * vp - s * vq;
+        V[row * ldv + qi] = s * vp + c * vq;
       }
       __syncthreads();
     }
@@ -1026,7 +1115,11 @@ __global__ void k_fill_i32(int32_t* __restrict__ dst, int32_t v, int n) {
 }
 
 // Rayleigh-Ritz: eig of G (m x m, m = s_j + q_j), keep the s_j largest in
-// descending order: nu[0..s_j), U (m x s_j) into Tout.
+// descending order: nu[0..s_j), U (m x s_j) into Tout.  Jacobi in arithmetic
+// T: FP64, or double-single in the FP32 mode (GB300 issues FP64 at 1/64 of
+// the FP32 rate, and the sweeps are most of this kernel).  The double-single
+// sweeps run on G scaled by a power of two to |g_ij| < 1 (exact).
+template <typename T>
 __global__ void __launch_bounds__(kT)
 k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
      const int32_t* __restrict__ sj, const int32_t* __restrict__ qj, double* __restrict__ nu_out,
@@ -1037,22 +1130,40 @@ k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
   const int m = s + (qj ? qj[j] : 0);
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int LD = wmax + 1;
-  double* A = reinterpret_cast<double*>(dsm_raw);
-  double* V = A + (size_t)wmax * LD;
-  double* ev = V + (size_t)wmax * LD;
-  double* cs = ev + wmax;
-  double* sn = cs + wmax;
-  double* red = sn + wmax;
+  static_assert(sizeof(T) == sizeof(double), "layout of dense_smem_bytes<double>");
+  T* A = reinterpret_cast<T*>(dsm_raw);
+  T* V = A + (size_t)wmax * LD;
+  double* ev = reinterpret_cast<double*>(V + (size_t)wmax * LD);
+  T* cs = reinterpret_cast<T*>(ev + wmax);
+  T* sn = cs + wmax;
+  auto* red = reinterpret_cast<typename JacobiOps<T>::R*>(sn + wmax);
   __shared__ int order[kMaxW];
+  __shared__ double wmx[kT / 32];
   if (m <= 0) return;
   const double* G = Gall + (int64_t)j * ldg * ldg;
+  int ex = 0;
+  if constexpr (!std::is_same_v<T, double>) {
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int r = idx % m, c = idx / m;
+      mx = fmax(mx, fabs(0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c])));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) wmx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, wmx[w]);
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &ex);
+  }
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     const int r = idx % m, c = idx / m;
-    A[r * LD + c] = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
+    const double g = 0.5 * (G[(int64_t)c * ldg + r] + G[(int64_t)r * ldg + c]);
+    if constexpr (std::is_same_v<T, double>) A[r * LD + c] = g;
+    else A[r * LD + c] = T(ldexp(g, -ex));
   }
   __syncthreads();
-  jacobi_eig<double>(A, LD, V, LD, m, cs, sn, red);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ev[i] = A[i * LD + i];
+  jacobi_eig<T>(A, LD, V, LD, m, cs, sn, red);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ev[i] = ldexp(to_double(A[i * LD + i]), ex);
   __syncthreads();
   // rank in descending order (ties by index)
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -1064,7 +1175,7 @@ k_rr(const double* __restrict__ Gall, double* __restrict__ Tout, int ldg,
   double* U = Tout + (int64_t)j * ldg * ldg;
   for (int idx = threadIdx.x; idx < m * s; idx += blockDim.x) {
     const int r = idx % m, k = idx / m;
-    U[(int64_t)k * ldg + r] = V[r * LD + order[k]];
+    U[(int64_t)k * ldg + r] = to_double(V[r * LD + order[k]]);
   }
   for (int k = threadIdx.x; k < s; k += blockDim.x) nu_out[(int64_t)j * ldnu + k] = ev[order[k]];
 }
@@ -1289,7 +1400,8 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(allow_smem(k_svqb<double>));
   GENEO_CUDA(allow_smem(k_svqb<float>));
   GENEO_CUDA(allow_smem(k_cholqr));
-  GENEO_CUDA(allow_smem(k_rr));
+  GENEO_CUDA(allow_smem(k_rr<double>));
+  GENEO_CUDA(allow_smem(k_rr<dsv>));
   int32_t* redo = nullptr;
   GENEO_TRY(tmp.get(&redo, (size_t)N));
   const size_t nn_smem = sizeof(double) * W3 * W3;
@@ -1309,6 +1421,12 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   GENEO_CUDA(allow_smem(k_gemm32<double, double>));
 
   const bool f32 = h->fp32;
+  // Rayleigh-Ritz sweeps in double-single arithmetic in the FP32 mode
+  auto rr_launch = [&](const double* Gm, double* Tt, int ld, const int32_t* s_, const int32_t* q_,
+                       double* nu_, int ldnu, const int32_t* skip, int wm) {
+    if (f32) k_rr<dsv><<<N, kT, dsm, st>>>(Gm, Tt, ld, s_, q_, nu_, ldnu, skip, wm);
+    else k_rr<double><<<N, kT, dsm, st>>>(Gm, Tt, ld, s_, q_, nu_, ldnu, skip, wm);
+  };
   // Subdomains whose K_j was factored in FP64 (a weak FP32 pivot: coefficient
   // contrast beyond FP32) also orthogonalise in FP64: their K-norms span
   // that contrast, which FP32 Gram matrices and corrections do not resolve.
@@ -1634,7 +1752,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     spmm(false, true, Xr, BXr, BXr, skip);
     GENEO_TRY(gram(Xr, BXr, 1, skip));
-    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dsm, st>>>(G, Tm, ldg, sj, nullptr, nu, s, skip, wcur); note_launch(); h->prof.end(prs, st); }
+    { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); rr_launch(G, Tm, ldg, sj, nullptr, nu, s, skip, wcur); note_launch(); h->prof.end(prs, st); }
     GENEO_TRY(gemm(Xr, Tm, 0, nullptr, cref(Tmp, W3, 0, nullptr, 0, sj), 1.0, 0.0, skip));
     k_copy_cols<double, double><<<gridR, kT, 0, st>>>(h->dsub, cref(Tmp, W3, 0, nullptr, 0, sj), Xr, skip); note_launch();
     GENEO_CUDA(cudaGetLastError());
@@ -1746,7 +1864,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
       // only BQ is new
       spmm(false, true, Qr, BQr, BQr, done);
       GENEO_TRY(gram(Sr, BSr, 1, done));
-      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); k_rr<<<N, kT, dsm, st>>>(G, Tm, ldg, sj, qj, nu, s, done, wcur); note_launch(); h->prof.end(prs, st); }
+      { const int prs = h->prof.begin(GENEO_PROF_SMALL_EIG, 0.0, 0.0, st); rr_launch(G, Tm, ldg, sj, qj, nu, s, done, wcur); note_launch(); h->prof.end(prs, st); }
       // P = Q U[s_j:, :], X = S U
       // P only spans the next search block: FP32 arithmetic with FP32 factors
       if (f32) GENEO_TRY(gemm32(Qr, Tm, 0, sj, cref(P, s, 0, nullptr, 0, sj), 1.0, 0.0, done, 0, 0,
