@@ -317,12 +317,31 @@ __global__ void k_band_width_A(const SubDesc* __restrict__ sub, const int32_t* _
   if ((threadIdx.x & 31) == 0) atomicMax(&wA[blockIdx.x], wmax);
 }
 
+// Local (N_j) index of every dof of every element of Omega_j, -1 for a
+// global Dirichlet dof: eloc[(offE + e) * ke + b] for element Ej[e].  One
+// lookup per (element, dof) instead of one per (row, element, dof).
+__global__ void k_elem_local(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
+                             const int32_t* __restrict__ sub_elem, const int32_t* __restrict__ elem_dofs,
+                             int ke, int32_t* __restrict__ eloc) {
+  const SubDesc d = sub[blockIdx.x];
+  const int32_t* Nj = Nlist + d.offN;
+  const int32_t* Ej = sub_elem + d.offE;
+  const int64_t items = (int64_t)d.nE * ke;
+  for (int64_t t = threadIdx.x; t < items; t += blockDim.x) {
+    const int64_t e = t / ke;
+    const int b = (int)(t - e * ke);
+    eloc[d.offE * ke + t] = find_i32(Nj, d.nN, elem_dofs[(int64_t)Ej[e] * ke + b]);
+  }
+}
+
 // Element assembly in gather form: row a of Omega_j sums, over the elements
 // of its dof that belong to Omega_j (ascending element id), the element
 // matrix row.  lK receives Atilde_j, lB receives A_j^o (overlap elements).
+// The local column of an element dof comes from eloc, its slot in row a
+// (columns ascending) by binary search.
 __global__ void k_assemble(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Nlist,
                            const int32_t* __restrict__ sub_elem, const int64_t* __restrict__ de_ptr,
-                           const int32_t* __restrict__ de, const int32_t* __restrict__ elem_dofs,
+                           const int32_t* __restrict__ de, const int32_t* __restrict__ eloc,
                            const double* __restrict__ elem_mats, int ke,
                            const int32_t* __restrict__ e_tau, const int64_t* __restrict__ lrow,
                            const int32_t* __restrict__ lcol, double* __restrict__ lK,
@@ -333,24 +352,28 @@ __global__ void k_assemble(const SubDesc* __restrict__ sub, const int32_t* __res
   for (int a = threadIdx.x; a < d.nN; a += blockDim.x) {
     const int32_t k = Nj[a];
     const int64_t r0 = lrow[d.offN + a], r1 = lrow[d.offN + a + 1];
+    const int rl = (int)(r1 - r0);
+    const int32_t* rc = lcol + r0;
     for (int64_t e = r0; e < r1; ++e) {
       lK[e] = 0.0;
       lB[e] = 0.0;
     }
     for (int64_t t = de_ptr[k]; t < de_ptr[k + 1]; ++t) {
       const int32_t el = de[t];
-      if (find_i32(Ej, d.nE, el) < 0) continue;
-      const int32_t* ed = elem_dofs + (int64_t)el * ke;
+      const int pe = find_i32(Ej, d.nE, el);
+      if (pe < 0) continue;
+      const int32_t* loc = eloc + (d.offE + pe) * (int64_t)ke;
       int ak = 0;
-      while (ak < ke && ed[ak] != k) ++ak;
+      while (ak < ke && loc[ak] != a) ++ak;
+      if (ak == ke) continue;  // cannot happen: dof k of this element is row a
       const double* Krow = elem_mats + ((int64_t)el * ke + ak) * ke;
       const bool ovl = e_tau[el] > 1;
       for (int bq = 0; bq < ke; ++bq) {
-        const int bl = find_i32(Nj, d.nN, ed[bq]);
+        const int bl = loc[bq];
         if (bl < 0) continue;
-        int64_t slot = r0;
-        while (slot < r1 && lcol[slot] != bl) ++slot;
-        if (slot >= r1) continue;  // cannot happen when A holds every element coupling
+        const int sl = lower_bound_i32(rc, rl, bl);
+        if (sl >= rl || rc[sl] != bl) continue;  // cannot happen when A holds every element coupling
+        const int64_t slot = r0 + sl;
         const double v = Krow[bq];
         if (!isfinite(v)) record_error(st, GENEO_ERR_NONFINITE, blockIdx.x, el);
         lK[slot] += v;
@@ -702,7 +725,12 @@ geneo_status_t assemble_local(geneo_handle_s* h, const geneo_problem_t* p, Assem
   // numeric assembly of Atilde_j, A_j^o, then B_j and K_j
   GENEO_TRY(tmp.get(&out.lK, (size_t)out.lnnz));
   GENEO_TRY(tmp.get(&out.lB, (size_t)out.lnnz));
-  k_assemble<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, de_ptr, de, p->elem_dofs,
+  int32_t* eloc = nullptr;
+  int64_t sumE = 0;
+  for (const SubDesc& d : h->hsub) sumE += d.nE;
+  GENEO_TRY(tmp.get(&eloc, (size_t)std::max<int64_t>(sumE * ke, 1)));
+  k_elem_local<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, p->elem_dofs, ke, eloc); note_launch();
+  k_assemble<<<N, kT, 0, s>>>(h->dsub, h->Nlist, p->sub_elem, de_ptr, de, eloc,
                               p->elem_mats, ke, a_out.e_tau, out.lrow, out.lcol, out.lK, out.lB,
                               h->dstat); note_launch();
   k_pencil<<<N, kT, 0, s>>>(h->dsub, h->pu, out.lrow, out.lcol, out.lK, out.lB, h->opt.sigma,
