@@ -2027,7 +2027,8 @@ size_t ring_smem(int max_w, int ring, int hs) {
 template <typename T, typename A = T>
 geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count, int max_w,
                                 double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
-                                const int32_t* skip_dev, DevStatus* st, cudaStream_t s) {
+                                const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int live = 0) {
+  if (live <= 0) live = count;
   if (nrhs == 1) {
     int snb = 16;
     if (solve_smem<T>(max_w, 1, next_pow2(max_w + 32), 16, 2) > kSmemCap) snb = 4;
@@ -2050,7 +2051,7 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
         const int kc = std::min(kmax, nrhs - c0);
         int CT = (((kc + 1) / 2) + 3) & ~3;
         // parts of 8 k columns (CT a multiple of 4)
-        const int units = (kc + 7) / 8, parts = split_parts(count, units);
+        const int units = (kc + 7) / 8, parts = split_parts(live, units);
         int nsplit = 1;
         if (parts > 1) {
           CT = 4 * ((units + parts - 1) / parts);
@@ -2080,7 +2081,7 @@ geneo_status_t band_solve_plain(const T* base, const BandDesc* d_desc, int count
   GENEO_CUDA(allow_smem(kern));
   for (int c0 = 0; c0 < nrhs; c0 += kmax) {
     const int kc = std::min(kmax, nrhs - c0);
-    const int nsplit = split_parts(count, (kc + 3) / 4);  // parts of at least 4 columns
+    const int nsplit = split_parts(live, (kc + 3) / 4);  // parts of at least 4 columns
     kern<<<dim3(count, nsplit), kThreads, smem, s>>>(base, d_desc, xbase, xoff, c0, kc, nrhs_dev, skip_dev, ring,
                                                      st);
     note_launch();
@@ -2093,15 +2094,18 @@ template <typename T, typename A>
 geneo_status_t band_solve_impl(const T* base, const BandDesc* d_desc, int count, int max_w,
                                double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                                const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
-                               int res_stages) {
+                               int res_stages, int active) {
   if (count <= 0 || nrhs <= 0) return GENEO_OK;
   // double-single arithmetic covers the multi-column solves; one right-hand
   // side keeps the FP64 kernels
   if constexpr (!std::is_same_v<A, T>) {
     if (nrhs == 1)
       return band_solve_impl<T, T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, max_n,
-                                   tc_passes, res_stages);
+                                   tc_passes, res_stages, active);
   }
+  // matrices to solve (the others are skipped by their blocks at once): the
+  // column split and the pipeline depth follow this number
+  const int live = active > 0 ? std::min(active, count) : count;
   // One right-hand side (the preconditioner's local solves): two stages and
   // one register slot per warp keep the block small enough for several
   // blocks per SM, which hides the latency of the sequential sweep.
@@ -2156,7 +2160,7 @@ geneo_status_t band_solve_impl(const T* base, const BandDesc* d_desc, int count,
         // column parts of 8 NT columns for small batches
         int nsplit = 1;
         {
-          const int parts = split_parts(count, NT);
+          const int parts = split_parts(live, NT);
           if (parts > 1) {
             NT = (NT + parts - 1) / parts;
             nsplit = (kk + 8 * NT - 1) / (8 * NT);
@@ -2166,7 +2170,7 @@ geneo_status_t band_solve_impl(const T* base, const BandDesc* d_desc, int count,
         // fills more than one wave of single blocks (NT <= 2), else the
         // deepest that fits
         int stages = 4;
-        const size_t cap = (NT <= 2 && count > 152 && mtc_smem(max_w, ring, NT, 2) <= kTwoPerSm) ? kTwoPerSm
+        const size_t cap = (NT <= 2 && live > 152 && mtc_smem(max_w, ring, NT, 2) <= kTwoPerSm) ? kTwoPerSm
                                                                                                 : 227 * 1024;
         while (stages > 2 && mtc_smem(max_w, ring, NT, stages) > cap) --stages;
         GENEO_TRY(launch_mtc(NT, stages, tc_passes, dim3(count, nsplit), mtc_smem(max_w, ring, NT, stages), s,
@@ -2182,13 +2186,13 @@ geneo_status_t band_solve_impl(const T* base, const BandDesc* d_desc, int count,
     const int gx = std::max(1, std::min(64, (max_n > 0 ? max_n : 4096) * nrhs / 256));
     k_band_scale_x<T><<<dim3(gx, count), 256, 0, s>>>(base, d_desc, xbase, xoff, 0, nrhs, nrhs_dev, skip_dev);
     note_launch();
-    GENEO_TRY(band_solve_plain<T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s));
+    GENEO_TRY(band_solve_plain<T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, live));
     k_band_scale_x<T><<<dim3(gx, count), 256, 0, s>>>(base, d_desc, xbase, xoff, 0, nrhs, nrhs_dev, skip_dev);
     note_launch();
     GENEO_CUDA(cudaGetLastError());
     return GENEO_OK;
   } else {
-    return band_solve_plain<T, A>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s);
+    return band_solve_plain<T, A>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, live);
   }
 }
 
@@ -2196,16 +2200,16 @@ template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n, int tc_passes,
-                          int res_stages) {
+                          int res_stages, int active) {
   return band_solve_impl<T, T>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s, max_n,
-                               tc_passes, res_stages);
+                               tc_passes, res_stages, active);
 }
 
 geneo_status_t band_solve_ds(const double* base, const BandDesc* d_desc, int count, int max_w, double* xbase,
                              const int64_t* xoff, int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev,
-                             DevStatus* st, cudaStream_t s, int max_n) {
+                             DevStatus* st, cudaStream_t s, int max_n, int active) {
   return band_solve_impl<double, dsv>(base, d_desc, count, max_w, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, s,
-                                      max_n, 3, 0);
+                                      max_n, 3, 0, active);
 }
 
 template geneo_status_t band_potrf<double>(double*, const BandDesc*, int, int, int, DevStatus*,
@@ -2214,9 +2218,9 @@ template geneo_status_t band_potrf<float>(float*, const BandDesc*, int, int, int
                                           cudaStream_t, bool, int32_t*, float, const Tc5Plan*);
 template geneo_status_t band_solve<double>(const double*, const BandDesc*, int, int, double*,
                                            const int64_t*, int, const int32_t*, const int32_t*,
-                                           DevStatus*, cudaStream_t, int, int, int);
+                                           DevStatus*, cudaStream_t, int, int, int, int);
 template geneo_status_t band_solve<float>(const float*, const BandDesc*, int, int, double*,
                                           const int64_t*, int, const int32_t*, const int32_t*,
-                                          DevStatus*, cudaStream_t, int, int, int);
+                                          DevStatus*, cudaStream_t, int, int, int, int);
 
 }  // namespace geneo

@@ -353,12 +353,14 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
 // several right-hand sides): 3 = each tensor-core product as three TF32
 // passes (about FP32 accuracy), 1 = one TF32 pass.  res_stages (one
 // right-hand side with the vector resident, 2-4; 0 = by shared memory): the
-// pipeline depth of that kernel, as an autotuner picked it.
+// pipeline depth of that kernel, as an autotuner picked it.  active (0 =
+// count): how many of the matrices skip_dev leaves to solve, which sizes the
+// column split of the multi-column kernels.
 template <typename T>
 geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int max_w,
                           double* xbase, const int64_t* xoff, int nrhs, const int32_t* nrhs_dev,
                           const int32_t* skip_dev, DevStatus* st, cudaStream_t s, int max_n = 0,
-                          int tc_passes = 3, int res_stages = 0);
+                          int tc_passes = 3, int res_stages = 0, int active = 0);
 
 // FP64 factors solved in double-single arithmetic on the FP32 pipe (about
 // 46 significant bits) for several right-hand sides: the FP64 fallback
@@ -366,7 +368,7 @@ geneo_status_t band_solve(const T* base, const BandDesc* d_desc, int count, int 
 // sweeps; one right-hand side is solved in FP64.
 geneo_status_t band_solve_ds(const double* base, const BandDesc* d_desc, int count, int max_w, double* xbase,
                              const int64_t* xoff, int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev,
-                             DevStatus* st, cudaStream_t s, int max_n);
+                             DevStatus* st, cudaStream_t s, int max_n, int active = 0);
 
 // solve_set.cu
 // A batch of band factors cut into classes of similar half bandwidth for
@@ -401,9 +403,11 @@ geneo_status_t make_solve_set(const void* base, bool f64, const BandDesc* d_desc
                               const double* base64, const BandDesc* d_desc64, int count64, DevMem& mem,
                               cudaStream_t s, SolveSet* out, bool ds64 = false);
 // band_solve over every class, ordered after the work already on s; the
-// work of every lane is joined back into s before the call returns.
+// work of every lane is joined back into s before the call returns.  active
+// (0 = all): an upper bound of the matrices of any class that skip_dev leaves
+// to solve.
 geneo_status_t solve_set_run(const SolveSet& ss, const SolveStreams& pool, double* xbase, const int64_t* xoff,
                              int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev, DevStatus* st,
-                             cudaStream_t s, int tc_passes = 3, int res_stages = 0);
+                             cudaStream_t s, int tc_passes = 3, int res_stages = 0, int active = 0);
 
 }  // namespace geneo

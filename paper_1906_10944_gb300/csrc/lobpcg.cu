@@ -1282,19 +1282,23 @@ k_resid(const SubDesc* __restrict__ sub, ColRef S, ColRef BX, ColRef KX, ColRef 
   double* sbase = cr_ptr(S, d, j);
   double* w0 = sbase + (int64_t)s * d.nN;
   const int k = na;
+  // S, BX, KX and P are distinct buffers: the loads of later rows may be
+  // issued before the stores of earlier ones
   for (int t = 0; t < k; ++t) {
     const int c = act[t];
     const double nc = nu[c];
-    const double* bc = bx + (int64_t)c * d.nN;
-    const double* kc = kx + (int64_t)c * d.nN;
-    double* o = w0 + (int64_t)t * d.nN;
+    const double* __restrict__ bc = bx + (int64_t)c * d.nN;
+    const double* __restrict__ kc = kx + (int64_t)c * d.nN;
+    double* __restrict__ o = w0 + (int64_t)t * d.nN;
+#pragma unroll 4
     for (int a = threadIdx.x; a < d.nN; a += blockDim.x) o[a] = bc[a] - nc * kc[a];
   }
   const int sp = spj[j];
   const double* pc = cr_ptr(P, d, j);
   for (int t = 0; t < sp; ++t) {
-    double* o = w0 + (int64_t)(k + t) * d.nN;
-    const double* src = pc + (int64_t)t * d.nN;
+    double* __restrict__ o = w0 + (int64_t)(k + t) * d.nN;
+    const double* __restrict__ src = pc + (int64_t)t * d.nN;
+#pragma unroll 4
     for (int a = threadIdx.x; a < d.nN; a += blockDim.x) o[a] = src[a];
   }
 }
@@ -1499,10 +1503,10 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
   SolveSet setK;
   GENEO_TRY(make_solve_set(asmb.bandK, !f32, asmb.dbandK, N, f32 ? asmb.bandK64 : nullptr,
                            f32 ? asmb.dbandK64 : nullptr, f32 ? asmb.nK64 : 0, tmp, st, &setK, true));
-  auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip,
-                        int kmax) -> geneo_status_t {
+  auto solveK_raw = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip, int kmax,
+                        int active) -> geneo_status_t {
     return solve_set_run(setK, h->solve_streams, S, xoff, kmax, ncols, skip, h->dstat, st,
-                         o.eig_solve_tf32 ? 1 : 3);
+                         o.eig_solve_tf32 ? 1 : 3, 0, active);
   };
   // timed with CUDA events; flops from the per-subdomain column counts
   auto solveK = [&](int64_t* xoff, const int32_t* ncols, const int32_t* skip) -> geneo_status_t {
@@ -1512,9 +1516,14 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     GENEO_CUDA(cudaStreamSynchronize(st));
     double fl = 0.0, by = 0.0;
     const double esz = f32 ? 4.0 : 8.0;
-    int kmax = 0;
+    // widest block and subdomains left (in the last iterations few remain,
+    // and their solves are cut into column parts on the idle SMs)
+    int kmax = 0, active = 0;
     for (int j = 0; j < N; ++j)
-      if (!hk[j]) kmax = std::max(kmax, (int)hc[j]);
+      if (!hk[j]) {
+        kmax = std::max(kmax, (int)hc[j]);
+        active += hc[j] > 0;
+      }
     for (int j = 0; j < N; ++j)
       if (!hk[j] && hc[j] > 0) {
         fl += kflops[j] * hc[j];
@@ -1524,7 +1533,7 @@ geneo_status_t local_eigensolve(geneo_handle_s* h, AssemblyOut& asmb, DevMem& tm
     h->eig_flops += fl;
     const int pr = h->prof.begin(GENEO_PROF_EIG_SOLVE, fl, by, st);
     evs.start(st);
-    geneo_status_t r = kmax > 0 ? solveK_raw(xoff, ncols, skip, kmax) : GENEO_OK;
+    geneo_status_t r = kmax > 0 ? solveK_raw(xoff, ncols, skip, kmax, active) : GENEO_OK;
     h->prof.end(pr, st);
     evs.stop();
     h->eig_ms = evs.ms;

@@ -74,15 +74,16 @@ geneo_status_t add_part(const void* base, bool f64, bool ds, const BandDesc* d_d
 
 geneo_status_t run_class(const SolveClass& c, double* xbase, const int64_t* xoff, int nrhs,
                          const int32_t* nrhs_dev, const int32_t* skip_dev, DevStatus* st, cudaStream_t s,
-                         int tc_passes, int res_stages) {
+                         int tc_passes, int res_stages, int active) {
+  const int act = active > 0 ? std::min(active, c.count) : 0;
   if (c.ds && nrhs > 1)
     return band_solve_ds(static_cast<const double*>(c.base), c.d, c.count, c.max_w, xbase, xoff, nrhs, nrhs_dev,
-                         skip_dev, st, s, c.max_n);
+                         skip_dev, st, s, c.max_n, act);
   if (c.f64)
     return band_solve<double>(static_cast<const double*>(c.base), c.d, c.count, c.max_w, xbase, xoff, nrhs,
-                              nrhs_dev, skip_dev, st, s, c.max_n, tc_passes, res_stages);
+                              nrhs_dev, skip_dev, st, s, c.max_n, tc_passes, res_stages, act);
   return band_solve<float>(static_cast<const float*>(c.base), c.d, c.count, c.max_w, xbase, xoff, nrhs,
-                           nrhs_dev, skip_dev, st, s, c.max_n, tc_passes, res_stages);
+                           nrhs_dev, skip_dev, st, s, c.max_n, tc_passes, res_stages, act);
 }
 
 }  // namespace
@@ -115,7 +116,7 @@ geneo_status_t make_solve_set(const void* base, bool f64, const BandDesc* d_desc
 
 geneo_status_t solve_set_run(const SolveSet& ss, const SolveStreams& pool, double* xbase, const int64_t* xoff,
                              int nrhs, const int32_t* nrhs_dev, const int32_t* skip_dev, DevStatus* st,
-                             cudaStream_t s, int tc_passes, int res_stages) {
+                             cudaStream_t s, int tc_passes, int res_stages, int active) {
   if (ss.cls.empty() || nrhs <= 0) return GENEO_OK;
   if (ss.lanes > 1) {
     GENEO_CUDA(cudaEventRecord(pool.fork, s));
@@ -124,7 +125,7 @@ geneo_status_t solve_set_run(const SolveSet& ss, const SolveStreams& pool, doubl
   geneo_status_t rc = GENEO_OK;
   for (const SolveClass& c : ss.cls) {
     const cudaStream_t cs = c.lane == 0 ? s : pool.s[c.lane - 1];
-    rc = run_class(c, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, cs, tc_passes, res_stages);
+    rc = run_class(c, xbase, xoff, nrhs, nrhs_dev, skip_dev, st, cs, tc_passes, res_stages, active);
     if (rc != GENEO_OK) break;
   }
   // join every lane, also after a failed launch, so that no work is left
