@@ -30,21 +30,48 @@ constexpr int kRedBlocks = 1024;
 constexpr int kNoAllocMaxIt = 4095;
 constexpr int kNoAllocScalars = 16;
 
+// u_j = R_j r and c_j = Z_j^T r (the restriction to the coarse space) in one
+// pass over r: each gathered r value serves u and up to kRm coarse products,
+// and the kRm sums share one block reduction (fixed order).
+constexpr int kRm = 8;
 __global__ void __launch_bounds__(kT)
 k_restrict(const SubDesc* __restrict__ sub, const int32_t* __restrict__ Dlist, const double* __restrict__ r,
            const double* __restrict__ Z, double* __restrict__ u, double* __restrict__ c) {
   const int j = blockIdx.x;
   const SubDesc d = sub[j];
-  __shared__ double red[kT / 32];
+  __shared__ double red[kT / 32][kRm];
   const int32_t* Dj = Dlist + d.offN;
   double* uj = u + d.offN;
-  for (int i = threadIdx.x; i < d.nD; i += blockDim.x) uj[i] = r[Dj[i]];
   const double* zj = Z + d.offZ;
-  for (int k = 0; k < d.m; ++k) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < d.nD; i += blockDim.x) s += zj[(int64_t)k * d.nD + i] * r[Dj[i]];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) c[d.offH + k] = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (d.m == 0) {
+    for (int i = threadIdx.x; i < d.nD; i += blockDim.x) uj[i] = r[Dj[i]];
+    return;
+  }
+  for (int k0 = 0; k0 < d.m; k0 += kRm) {
+    const int km = min(kRm, d.m - k0);
+    double acc[kRm];
+#pragma unroll
+    for (int k = 0; k < kRm; ++k) acc[k] = 0.0;
+    for (int i = threadIdx.x; i < d.nD; i += blockDim.x) {
+      const double rv = r[Dj[i]];
+      if (k0 == 0) uj[i] = rv;
+#pragma unroll
+      for (int k = 0; k < kRm; ++k)
+        if (k < km) acc[k] += zj[(int64_t)(k0 + k) * d.nD + i] * rv;
+    }
+#pragma unroll
+    for (int k = 0; k < kRm; ++k) {
+      const double v = warp_sum(acc[k]);
+      if (lane == 0) red[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < km) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w][threadIdx.x];
+      c[d.offH + k0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -430,9 +457,12 @@ double condition_estimate_fixed(const double* a, const double* b, int m, double*
 // band solve with the vector resident in shared memory): each pipeline
 // depth (2, 3, 4 stages; deeper stages take more shared memory and so fewer
 // blocks per SM) is timed on this batch, on a scratch copy of the subdomain
-// vectors (one warm-up and three timed launches each, CUDA events), and the
-// fastest is kept for the process, keyed by (precision, largest band width,
-// largest order, batch size).  Runs once per key at the end of a setup.
+// vectors, and the fastest is kept for the process, keyed by (precision,
+// largest band width, largest order, batch size).  The depths are timed in
+// turn, four rounds after a warm-up launch of each, one launch per CUDA-event
+// pair, and each depth keeps its fastest launch: a single short window per
+// depth is at the mercy of whatever else the GPU does at that moment.  Runs
+// once per key at the end of a setup.
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune;
@@ -457,26 +487,34 @@ geneo_status_t tune_local_solve(geneo_handle_s* h) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GENEO_CUDA(cudaEventCreate(&e0));
   GENEO_CUDA(cudaEventCreate(&e1));
-  int best = 0;
-  float best_ms = 1e30f;
-  for (int stages = 2; stages <= 4; ++stages) {
-    auto run = [&]() -> geneo_status_t {
-      return solve_set_run(h->setA, h->solve_streams, scratch, h->uoff, 1, nullptr, nullptr, h->dstat, s, 3,
-                           stages);
-    };
-    geneo_status_t st = run();
-    if (st != GENEO_OK) break;
-    GENEO_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3 && st == GENEO_OK; ++r) st = run();
-    GENEO_CUDA(cudaEventRecord(e1, s));
-    GENEO_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    GENEO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (st == GENEO_OK && ms < best_ms) {
-      best_ms = ms;
-      best = stages;
-    }
+  auto run = [&](int stages) -> geneo_status_t {
+    return solve_set_run(h->setA, h->solve_streams, scratch, h->uoff, 1, nullptr, nullptr, h->dstat, s, 3, stages);
+  };
+  constexpr int kDepths = 3, kRounds = 4;
+  float best_ms[kDepths];
+  bool ok[kDepths];
+  for (int i = 0; i < kDepths; ++i) {
+    best_ms[i] = 1e30f;
+    ok[i] = run(2 + i) == GENEO_OK;  // warm-up (and the shared-memory attribute)
   }
+  for (int r = 0; r < kRounds; ++r)
+    for (int i = 0; i < kDepths; ++i) {
+      if (!ok[i]) continue;
+      GENEO_CUDA(cudaEventRecord(e0, s));
+      ok[i] = run(2 + i) == GENEO_OK;
+      GENEO_CUDA(cudaEventRecord(e1, s));
+      GENEO_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GENEO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ok[i]) best_ms[i] = std::min(best_ms[i], ms);
+    }
+  int best = 0;
+  float bms = 1e30f;
+  for (int i = 0; i < kDepths; ++i)
+    if (ok[i] && best_ms[i] < bms) {
+      bms = best_ms[i];
+      best = 2 + i;
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   GENEO_CUDA(cudaStreamSynchronize(s));
