@@ -210,75 +210,97 @@ k_band_potrf(T* __restrict__ base, const BandDesc* __restrict__ descs, int phmax
 }
 
 // Right-looking factorisation of one large band over many SMs (the coarse
-// matrix A_H, whose FP64 work is too much for one SM): per panel of NB
-// columns one block factors the diagonal block and solves the panel rows
-// (k_band_panel), then a grid of 64 x 64 tiles applies the rank-NB update to
-// the trailing window (k_band_trail).  Two launches per panel; the stream
-// orders them.
+// matrix A_H, whose FP64 work is too much for one SM).  Per panel of NB
+// columns: one warp factors the diagonal block (k_band_panel_diag), a grid
+// of one-warp blocks solves the panel rows below it, one row per thread
+// (k_band_panel_rows), then a grid of 64 x 64 tiles applies the rank-NB
+// update to the trailing window (k_band_trail).  Three launches per panel;
+// the stream orders them.  GB300 issues FP64 at 2 fused multiply-adds per
+// clock per SM, so the rows' solves (h NB^2 / 2 of them) are spread over
+// h / 32 SMs instead of one.
 template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads)
-k_band_panel(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb, DevStatus* st) {
+__global__ void __launch_bounds__(32)
+k_band_panel_diag(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb, DevStatus* st) {
   const BandDesc d = descs[0];
   const int n = d.n, w = d.w;
   const int64_t ld = d.ld;
   T* L = base + d.off;
   __shared__ T Dk[NB * (NB + 1)];
   constexpr int DS = NB + 1;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = threadIdx.x;
   const int b = min(NB, n - kb);
-  const int h = min(w, n - kb - b);
-  for (int idx = tid; idx < NB * NB; idx += nt) {
+  for (int idx = lane; idx < NB * NB; idx += 32) {
     const int r = idx / NB, c = idx % NB;
     T v = T(0);
     if (r < b && c < b && r >= c && r - c <= w) v = L[bidx(kb + r, kb + c, w, ld)];
     Dk[r * DS + c] = v;
   }
-  __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
-    for (int t = 0; t < b; ++t) {
-      if (lane == t) {
-        T dv = Dk[t * DS + t];
-        if (!finite_pos(dv)) {
-          record_error(st, isfinite(dv) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id, (int64_t)kb + t);
-          dv = T(1);
-        }
-        Dk[t * DS + t] = sqrt(dv);
+  __syncwarp();
+  for (int t = 0; t < b; ++t) {
+    if (lane == t) {
+      T dv = Dk[t * DS + t];
+      if (!finite_pos(dv)) {
+        record_error(st, isfinite(dv) ? GENEO_ERR_NOT_SPD : GENEO_ERR_NONFINITE, d.id, (int64_t)kb + t);
+        dv = T(1);
       }
-      __syncwarp();
-      const T piv = Dk[t * DS + t];
-      if (lane > t && lane < b) Dk[lane * DS + t] /= piv;
-      __syncwarp();
-      if (lane > t && lane < b) {
-        const T lrt = Dk[lane * DS + t];
-        for (int u = t + 1; u <= lane; ++u) Dk[lane * DS + u] -= lrt * Dk[u * DS + t];
-      }
-      __syncwarp();
+      Dk[t * DS + t] = sqrt(dv);
     }
+    __syncwarp();
+    const T piv = Dk[t * DS + t];
+    if (lane > t && lane < b) Dk[lane * DS + t] /= piv;
+    __syncwarp();
+    if (lane > t && lane < b) {
+      const T lrt = Dk[lane * DS + t];
+      for (int u = t + 1; u <= lane; ++u) Dk[lane * DS + u] -= lrt * Dk[u * DS + t];
+    }
+    __syncwarp();
   }
-  __syncthreads();
-  for (int idx = tid; idx < NB * NB; idx += nt) {
+  for (int idx = lane; idx < NB * NB; idx += 32) {
     const int r = idx / NB, c = idx % NB;
     if (r < b && c < b && r >= c && r - c <= w) L[bidx(kb + r, kb + c, w, ld)] = Dk[r * DS + c];
   }
-  for (int i = tid; i < h; i += nt) {
-    const int rr = kb + b + i;
-    T x[NB];
-#pragma unroll
-    for (int t = 0; t < NB; ++t) x[t] = (t < b && rr - (kb + t) <= w) ? L[bidx(rr, kb + t, w, ld)] : T(0);
-#pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      if (t < b) {
-        T v = x[t];
-#pragma unroll
-        for (int u = 0; u < t; ++u) v -= x[u] * Dk[t * DS + u];
-        x[t] = v / Dk[t * DS + t];
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < NB; ++t)
-      if (t < b && rr - (kb + t) <= w) L[bidx(rr, kb + t, w, ld)] = x[t];
+}
+
+// Rows kb + b + 32 blockIdx.x + lane of the panel: x L_kk^T = a (the
+// diagonal block already factored), multiplying by the pivots' reciprocals.
+template <typename T, int NB>
+__global__ void __launch_bounds__(32)
+k_band_panel_rows(T* __restrict__ base, const BandDesc* __restrict__ descs, int kb) {
+  const BandDesc d = descs[0];
+  const int n = d.n, w = d.w;
+  const int64_t ld = d.ld;
+  T* L = base + d.off;
+  __shared__ T Dk[NB * (NB + 1)];
+  __shared__ T rp[NB];
+  constexpr int DS = NB + 1;
+  const int lane = threadIdx.x;
+  const int b = min(NB, n - kb);
+  const int h = min(w, n - kb - b);
+  for (int idx = lane; idx < NB * NB; idx += 32) {
+    const int r = idx / NB, c = idx % NB;
+    Dk[r * DS + c] = (r < b && c < b && r >= c && r - c <= w) ? L[bidx(kb + r, kb + c, w, ld)] : T(0);
   }
+  __syncwarp();
+  for (int t = lane; t < NB; t += 32) rp[t] = t < b ? T(1) / Dk[t * DS + t] : T(0);
+  __syncwarp();
+  const int i = 32 * blockIdx.x + lane;
+  if (i >= h) return;
+  const int rr = kb + b + i;
+  T x[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) x[t] = (t < b && rr - (kb + t) <= w) ? L[bidx(rr, kb + t, w, ld)] : T(0);
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    if (t < b) {
+      T v = x[t];
+#pragma unroll
+      for (int u = 0; u < t; ++u) v -= x[u] * Dk[t * DS + u];
+      x[t] = v * rp[t];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t < b && rr - (kb + t) <= w) L[bidx(rr, kb + t, w, ld)] = x[t];
 }
 
 // Trailing update of panel kb: C(i, i') -= sum_t P(i, t) P(i', t) over the
@@ -1866,10 +1888,11 @@ geneo_status_t band_potrf(T* base, const BandDesc* d_desc, int count, int max_w,
   if (count == 1 && max_n > 256 && max_w >= 128 && !weak) {
     constexpr int PB = 32;
     for (int kb = 0; kb < max_n; kb += PB) {
-      k_band_panel<T, PB><<<1, kThreads, 0, s>>>(base, d_desc, kb, st); note_launch();
+      k_band_panel_diag<T, PB><<<1, 32, 0, s>>>(base, d_desc, kb, st); note_launch();
       const int b = std::min(PB, max_n - kb);
       const int h = std::min(max_w, max_n - kb - b);
       if (h > 0) {
+        k_band_panel_rows<T, PB><<<(h + 31) / 32, 32, 0, s>>>(base, d_desc, kb); note_launch();
         const int T64 = (h + 63) / 64;
         k_band_trail<T, PB><<<T64 * (T64 + 1) / 2, kThreads, 0, s>>>(base, d_desc, kb); note_launch();
       }
