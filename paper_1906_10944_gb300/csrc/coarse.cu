@@ -301,7 +301,13 @@ geneo_status_t build_coarse(geneo_handle_s* h, const AssemblyOut& asmb, const do
     k_identity<<<(unsigned)std::min<int64_t>(((int64_t)dim * dim + kT - 1) / kT, 152 * 16), kT, 0, s>>>(
         h->Hinv, dim); note_launch();
     GENEO_CUDA(cudaGetLastError());
-    GENEO_TRY(band_solve<double>(h->bandH, drep, nc, wH, h->Hinv, dxo, 16, dcnt, nullptr, h->dstat, s, 0));
+    // FP32 mode: the columns of A_H^{-1} in double-single arithmetic on the
+    // FP32 pipe (about 46 bits; GB300 issues FP64 at 1/64 of the FP32 rate),
+    // an error far below the FP32 local solves' beside it in M^{-1}
+    if (h->fp32)
+      GENEO_TRY(band_solve_ds(h->bandH, drep, nc, wH, h->Hinv, dxo, 16, dcnt, nullptr, h->dstat, s, 0));
+    else
+      GENEO_TRY(band_solve<double>(h->bandH, drep, nc, wH, h->Hinv, dxo, 16, dcnt, nullptr, h->dstat, s, 0));
     GENEO_TRY(check_status(h, s));
   }
   *ms_factor = ms_since(t2);
