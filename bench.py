@@ -9,7 +9,8 @@ element layers, kappa = exp(Gaussian field) with 1e6-contrast slabs, at most
 eigensolves, coarse space) + geneo_pcg_solve + geneo_destroy, inputs resident
 in device memory.  value = dofs solved per second over the timed steps.
 The default path is the mixed-precision one (FP32 band factors and local
-solves; FP64 residuals, Rayleigh-Ritz, coarse problem and PCG); `compare`
+solves; FP64 residuals, coarse problem and PCG; double-single eigensolver
+products, Rayleigh-Ritz and coarse inverse); `compare`
 holds one timed step of the FP64 path ("mixed vs FP64").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
@@ -917,7 +918,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": w["desc"],
                        "precision": ("mixed: FP32 band factors and local solves; FP64 residuals, "
-                                     "Rayleigh-Ritz, coarse problem and PCG")
+                                     "coarse problem and PCG; double-single eigensolver products, "
+                                     "Rayleigh-Ritz and coarse inverse")
                                     if args.precision == "mixed" else "fp64",
                        "l2": "inputs larger than L2 (CSR A 0.7 GB, element matrices 1.07 GB); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

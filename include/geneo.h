@@ -72,8 +72,11 @@ typedef enum {
 
 typedef enum {
   GENEO_PREC_FP64 = 0,   /* all factors and local solves in FP64 */
-  GENEO_PREC_FP32 = 1    /* subdomain factors in FP32; Rayleigh-Ritz, residuals,
-                            coarse problem and PCG in FP64 */
+  GENEO_PREC_FP32 = 1    /* subdomain factors in FP32; residuals, coarse
+                            problem and PCG in FP64; the eigensolver's block
+                            products, Gram matrices and Rayleigh-Ritz sweeps
+                            and the columns of the coarse inverse in
+                            double-single arithmetic (about 46 bits) */
 } geneo_precision_t;
 
 /*
@@ -190,9 +193,10 @@ typedef struct {
  *             block solves with K_j (the shift-and-invert operator of
  *             Section 4.4) as one TF32 tensor-core pass per product instead
  *             of three (about 1e-3 relative error in K_j^{-1} R; the
- *             residuals, Rayleigh-Ritz and convergence test stay FP64, so
- *             only the search directions change and the eigenpairs meet the
- *             same tolerance); 0 keeps FP32 accuracy in those solves.
+ *             residuals and the convergence test stay FP64 and Rayleigh-Ritz
+ *             double-single, so only the search directions change and the
+ *             eigenpairs meet the same tolerance); 0 keeps FP32 accuracy in
+ *             those solves.
  *  factor_kernel  GENEO_PREC_FP32 only: 0 (default) factors the bands on the
  *             fifth-generation tensor cores (tcgen05 MMAs, TMEM accumulators,
  *             tensor-map copies) when the batch's half bandwidth fits that

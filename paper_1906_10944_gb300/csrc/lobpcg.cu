@@ -18,8 +18,12 @@
 //   P = Q U_Q, X = S U
 // Stop when every Ritz pair below the threshold tau is converged and the
 // first one at or above tau is converged too (or all nev_max in fixed-count
-// mode).  Rayleigh-Ritz, residuals and orthogonalisation are FP64; the
-// K^{-1} solves use the factor's precision.
+// mode).  Residuals are FP64.  With FP32 factors the first
+// orthogonalisation pass runs in FP32 and the second, the block products,
+// the Gram matrices and the Rayleigh-Ritz sweeps in double-single arithmetic
+// (about 46 bits; the products and Gram matrices of the subdomains whose K_j
+// needed FP64 stay FP64); with FP64 factors all of it is FP64.  The K^{-1} solves use the factor's
+// precision.
 //
 // Dense small problems (at most kMaxW = 104 columns) are solved by parallel
 // cyclic Jacobi in shared memory, one thread block per subdomain.

@@ -208,7 +208,8 @@ def test_wide_bands_mixed_precision():
 
 def test_c1_mixed_precision():
     """FP32 factors (local solves and the eigensolver's shift-invert operator)
-    with FP64 residuals, Rayleigh-Ritz, coarse problem and PCG."""
+    with FP64 residuals, coarse problem and PCG, and double-single eigensolver
+    products, Rayleigh-Ritz and coarse inverse."""
     _full_check(_c1(), name="c1", precision=1, iter_slack=0.1)
 
 
